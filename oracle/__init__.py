@@ -1,0 +1,249 @@
+"""CPU oracle for the SMAT hot path (arXiv 1210.2536) -- TEST INFRASTRUCTURE.
+
+Thin ctypes/numpy front end to ``oracle.c`` (plain C, FP64, no FMA
+contraction).  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package; the library under
+``paper_1210_2536_gb300`` never does, and the two share no code.
+
+Every function restates a definition of the paper:
+  spmv_csr        y = alpha*A*x + beta*y in CSR, fixed ascending order (Sec. 2.1, 3)
+  spmv_csr_threads  the same on T threads, nonzero-balanced row split (Sec. 6)
+  features        Table "Feature parameters of a sparse matrix" (Sec. 4)
+  to_ell/to_dia/to_coo  the four basic storage formats (Sec. 2.1)
+  mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
+Readings taken where the paper is silent are listed in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MLP_IN, MLP_H, MLP_OUT = 12, 64, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (gcc, -O2 -ffp-contract=off: every FP op is one rounding)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-std=gnu11", "-o", tmp, _SRC, "-lm", "-pthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Features(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("m", "n", "nnz", "max_rd", "min_rd", "ndiags", "ntdiags", "empty_rows", "s2_lo", "s2_hi")] + \
+               [(n, ctypes.c_double) for n in
+                ("aver_rd", "var_rd", "er_dia", "er_ell", "ntdiags_ratio", "r")] + [("r_valid", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        vp, i64, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.oracle_spmv_csr.argtypes = [i64, vp, vp, vp, vp, f64, f64, vp]
+        L.oracle_spmv_csr_threads.argtypes = [i64, vp, vp, vp, vp, f64, f64, vp, ctypes.c_int]
+        L.oracle_partition_rows.argtypes = [i64, vp, ctypes.c_int, vp]
+        L.oracle_max_rd.argtypes = [i64, vp]
+        L.oracle_max_rd.restype = i64
+        L.oracle_features.argtypes = [i64, i64, vp, vp, i64, i64, vp, vp, ctypes.POINTER(_Features)]
+        L.oracle_to_ell.argtypes = [i64, vp, vp, vp, i64, i64, i64, vp, vp]
+        L.oracle_dia_offsets.argtypes = [i64, i64, vp, vp, vp]
+        L.oracle_dia_offsets.restype = i64
+        L.oracle_to_dia.argtypes = [i64, vp, vp, vp, i64, vp, i64, i64, vp]
+        L.oracle_to_coo.argtypes = [i64, vp, vp]
+        L.oracle_round_bf16.argtypes = [i64, vp, vp]
+        L.oracle_bf16_to_double.argtypes = [i64, vp, vp]
+        L.oracle_mlp_param_count.restype = i64
+        L.oracle_mlp_forward.argtypes = [vp, i64, vp, vp]
+        L.oracle_mlp_loss_grad.argtypes = [vp, i64, vp, vp, vp]
+        L.oracle_mlp_loss_grad.restype = f64
+        L.oracle_adam.argtypes = [i64, vp, vp, vp, vp, i64, f64, f64, f64, f64]
+        _lib = L
+    return _lib
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# SpMV (Sec. 2.1 / Sec. 3: CSR is the unified interface and default format)
+# ---------------------------------------------------------------------------
+
+def spmv_csr(m, rowptr, colidx, val, x, alpha=1.0, beta=0.0, y=None, threads: int = 1):
+    """y = alpha*A*x + beta*y with FP64 accumulation in ascending storage order.
+    ``val`` and ``x`` are widened to FP64 first (exact for FP32 / BF16 storage).
+    Returns a new array; ``y`` is read only when beta != 0."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v, pv = _c(val, np.float64)
+    xx, px = _c(x, np.float64)
+    out = np.zeros(m, dtype=np.float64) if y is None else np.array(y, dtype=np.float64, copy=True)
+    if threads <= 1:
+        lib().oracle_spmv_csr(m, prp, pci, pv, px, float(alpha), float(beta), out.ctypes.data)
+    else:
+        lib().oracle_spmv_csr_threads(m, prp, pci, pv, px, float(alpha), float(beta), out.ctypes.data,
+                                      int(threads))
+    return out
+
+
+def partition_rows(m, rowptr, nthreads):
+    rp, prp = _c(rowptr, np.int32)
+    b = np.zeros(nthreads + 1, dtype=np.int64)
+    lib().oracle_partition_rows(m, prp, nthreads, b.ctypes.data)
+    return b
+
+
+def spmv_rows_sampled(rowptr, colidx, val, x, rows, alpha=1.0, beta=0.0, y_in=None):
+    """The oracle product for selected rows only (for full-size parity checks):
+    builds the sub-CSR of those rows and runs ``spmv_csr`` on it."""
+    rows = np.asarray(rows, dtype=np.int64)
+    rp = np.asarray(rowptr, dtype=np.int64)
+    starts, ends = rp[rows], rp[rows + 1]
+    lens = ends - starts
+    sub_rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=sub_rp[1:])
+    idx = np.concatenate([np.arange(s, e) for s, e in zip(starts, ends)]) if len(rows) else np.zeros(0, np.int64)
+    yb = None if y_in is None else np.asarray(y_in, dtype=np.float64)[rows]
+    return spmv_csr(len(rows), sub_rp.astype(np.int32), np.asarray(colidx)[idx], np.asarray(val)[idx], x,
+                    alpha, beta, yb)
+
+
+# ---------------------------------------------------------------------------
+# Features (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def features(m, n, rowptr, colidx, tau=(3, 5)):
+    """All feature parameters plus the row-degree histogram and the per-diagonal
+    counts (index d + M - 1 for diagonal d = j - i)."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    mx = int(lib().oracle_max_rd(m, prp)) if m > 0 else 0
+    hist = np.zeros(mx + 1, dtype=np.int64)
+    dcnt = np.zeros(max(m + n - 1, 1), dtype=np.int64)
+    f = _Features()
+    lib().oracle_features(m, n, prp, pci, int(tau[0]), int(tau[1]), hist.ctypes.data, dcnt.ctypes.data,
+                          ctypes.byref(f))
+    d = {name: getattr(f, name) for name, _ in _Features._fields_}
+    d["s2"] = (d.pop("s2_hi") << 64) | (d.pop("s2_lo") & 0xFFFFFFFFFFFFFFFF)
+    d["hist"] = hist
+    d["diag_cnt"] = dcnt[: m + n - 1] if m + n > 0 else dcnt[:0]
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Conversions (Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def pitch(m: int) -> int:
+    """Row pitch of the ELL and DIA arrays: M rounded up to a multiple of 32."""
+    return (m + 31) // 32 * 32
+
+
+def to_ell(m, rowptr, colidx, val, K=None, P=None):
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    if K is None:
+        K = int(np.max(np.diff(rp))) if m > 0 else 0
+    P = pitch(m) if P is None else P
+    col = np.empty(K * P, dtype=np.int32)
+    out = np.empty(K * P, dtype=v.dtype)
+    lib().oracle_to_ell(m, prp, pci, v.ctypes.data, v.itemsize, K, P, col.ctypes.data, out.ctypes.data)
+    return col, out, K, P
+
+
+def dia_offsets(m, n, rowptr, colidx):
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    nd = int(lib().oracle_dia_offsets(m, n, prp, pci, None))
+    off = np.empty(nd, dtype=np.int32)
+    lib().oracle_dia_offsets(m, n, prp, pci, off.ctypes.data)
+    return off
+
+
+def to_dia(m, n, rowptr, colidx, val, P=None):
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    off = dia_offsets(m, n, rp, ci)
+    P = pitch(m) if P is None else P
+    out = np.empty(len(off) * P, dtype=v.dtype)
+    lib().oracle_to_dia(m, prp, pci, v.ctypes.data, v.itemsize, off.ctypes.data, len(off), P, out.ctypes.data)
+    return off, out, P
+
+
+def to_coo(m, rowptr):
+    rp, prp = _c(rowptr, np.int32)
+    nnz = int(rp[-1]) if m > 0 else 0
+    row = np.empty(nnz, dtype=np.int32)
+    lib().oracle_to_coo(m, prp, row.ctypes.data)
+    return row
+
+
+# ---------------------------------------------------------------------------
+# Value storage precision
+# ---------------------------------------------------------------------------
+
+def round_bf16(x) -> np.ndarray:
+    """FP64 -> bfloat16 bit patterns (uint16), round to nearest even."""
+    xx, px = _c(x, np.float64)
+    out = np.empty(xx.shape, dtype=np.uint16)
+    lib().oracle_round_bf16(xx.size, px, out.ctypes.data)
+    return out
+
+
+def bf16_to_double(b) -> np.ndarray:
+    bb, pb = _c(b, np.uint16)
+    out = np.empty(bb.shape, dtype=np.float64)
+    lib().oracle_bf16_to_double(bb.size, pb, out.ctypes.data)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# MLP selector (Sec. 5 replacement) and its optimizer
+# ---------------------------------------------------------------------------
+
+def mlp_param_count() -> int:
+    return int(lib().oracle_mlp_param_count())
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    p, pp = _c(params, np.float64)
+    x, px = _c(X, np.float64)
+    B = x.shape[0]
+    out = np.empty((B, MLP_OUT), dtype=np.float64)
+    lib().oracle_mlp_forward(pp, B, px, out.ctypes.data)
+    return out
+
+
+def mlp_loss_grad(params, X, T):
+    p, pp = _c(params, np.float64)
+    x, px = _c(X, np.float64)
+    t, pt = _c(T, np.float64)
+    g = np.empty_like(p)
+    loss = lib().oracle_mlp_loss_grad(pp, x.shape[0], px, pt, g.ctypes.data)
+    return float(loss), g
+
+
+def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays p, m, v given gradient g."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gg, pg = _c(g, np.float64)
+    lib().oracle_adam(p.size, p.ctypes.data, pg, m.ctypes.data, v.ctypes.data, int(t), lr, b1, b2, eps)
