@@ -1,0 +1,265 @@
+/*
+ * smat.h -- C ABI of libsmat, an input-adaptive sparse matrix-vector multiply
+ * library for NVIDIA GB300 (sm_103a), after SMAT (Li, Zhang, Tan, Chen,
+ * "SMAT: An Input Adaptive Sparse Matrix-Vector Multiplication Auto-Tuner",
+ * arXiv 1210.2536).
+ *
+ * The caller hands in a matrix in CSR only (Sec. 3: the unified CSR interface)
+ * and asks for y = alpha*A*x + beta*y.  The library extracts the matrix's
+ * feature parameters on the GPU (Sec. 4), chooses a storage format and kernel
+ * (Sec. 5-6: a learned classifier with an execute-and-measure fallback),
+ * converts CSR to that format (Sec. 2.1) and runs the product.
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only.  Streams are cudaStream_t passed as void*; NULL is
+ *     the legacy default stream.
+ *   - Every call returns an smat_status_t; no C++ exception crosses the ABI
+ *     and no kernel traps.  Errors detected on the device (invalid CSR) are
+ *     reported through a flag the host reads.
+ *   - Indices are int32 (M, N, NNZ <= 2^31 - 1).  Rows must hold strictly
+ *     increasing column indices (canonical CSR); anything else is
+ *     SMAT_ERR_INVALID_CSR.
+ *   - Value storage: SMAT_F64 computes in FP64 with FP64 x and y.  SMAT_F32 and
+ *     SMAT_BF16 store values in FP32 / bfloat16 and compute with FP32
+ *     accumulation, FP32 x and y, FP32 alpha and beta.
+ *   - alpha and beta are HOST pointers to one scalar of the compute type.
+ *     beta == 0 means y is only written (NaN in y is ignored, as in BLAS).
+ *
+ * Thread safety: calls on different handles are independent.  Calls on one
+ * handle must not overlap: the merge-path and COO kernels keep their carries
+ * in handle-owned scratch, so two products on one handle must be ordered
+ * (same stream, or synchronised).
+ */
+#ifndef SMAT_H
+#define SMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smat_s *smat_handle_t;
+typedef struct smat_batch_s *smat_batch_t;
+
+typedef enum {
+  SMAT_OK = 0,
+  SMAT_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, bad enum          */
+  SMAT_ERR_INVALID_CSR = 2, /* rowptr not monotone / wrong ends, column out of
+                               range, or columns not strictly increasing      */
+  SMAT_ERR_ALLOC = 3,       /* device or host allocation failed               */
+  SMAT_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed           */
+  SMAT_ERR_UNSUPPORTED = 5, /* sizes beyond int32 indexing, format not
+                               admissible for this matrix                      */
+  SMAT_ERR_MODEL = 6,       /* selector model missing or malformed            */
+  SMAT_ERR_NOT_CONVERGED = 7 /* iterative solve stopped before its tolerance  */
+} smat_status_t;
+
+typedef enum { SMAT_F64 = 0, SMAT_F32 = 1, SMAT_BF16 = 2 } smat_dtype_t;
+
+/* Storage formats (Sec. 2.1: the four basic formats). */
+typedef enum { SMAT_FMT_CSR = 0, SMAT_FMT_ELL = 1, SMAT_FMT_DIA = 2, SMAT_FMT_COO = 3 } smat_format_t;
+
+/* Kernel variants the selector chooses among (the paper's kernel library maps
+ * each format to its best implementation, Sec. 3).  On the GPU the CSR format
+ * has five implementations. */
+typedef enum {
+  SMAT_V_CSR_SCALAR = 0, /* one thread per row                              */
+  SMAT_V_CSR_VEC4 = 1,   /* 4 lanes per row, shuffle reduction              */
+  SMAT_V_CSR_VEC8 = 2,   /* 8 lanes per row                                  */
+  SMAT_V_CSR_VEC32 = 3,  /* one warp per row                                 */
+  SMAT_V_CSR_MERGE = 4,  /* merge-path split of rows + nonzeros              */
+  SMAT_V_ELL = 5,        /* column-major ELL, 16-byte vector loads           */
+  SMAT_V_DIA = 6,        /* diagonal-major DIA                               */
+  SMAT_V_COO = 7,        /* COO with segmented reduction                     */
+  SMAT_NUM_VARIANTS = 8
+} smat_variant_t;
+
+/* Feature parameters (Sec. 4, Table "Feature parameters of a sparse matrix").
+ * Integer members are exact.  Each double is computed from exact integers:
+ *   aver_rd = NNZ / M
+ *   var_rd  = (M * S2 - NNZ^2) / M^2, S2 = sum of squared row degrees
+ *             (population variance of the row degree)
+ *   er_dia  = NNZ / (Ndiags * M),  er_ell = NNZ / (max_RD * M)
+ *   ntdiags_ratio = (# diagonals filled above tau) / Ndiags
+ * with each integer operand converted to double once and one division.
+ *   r = -slope of the least-squares line through (ln k, ln h[k]) over row
+ *       degrees k >= 1 with h[k] > 0 (P(k) ~ k^-R); r_valid = 0 and r = 0 when
+ *       fewer than two degrees occur.
+ * Ratios whose denominator is 0 are 0. */
+typedef struct {
+  int64_t m, n, nnz;
+  int64_t max_rd, min_rd, empty_rows;
+  int64_t ndiags, ntdiags;
+  uint64_t s2;
+  double aver_rd, var_rd, er_dia, er_ell, ntdiags_ratio, r;
+  int32_t r_valid;
+  uint32_t admissible; /* bit v set: variant v may be used for this matrix */
+} smat_features_t;
+
+/* Selection modes for smat_tune. */
+typedef enum {
+  SMAT_TUNE_LEARNED = 0,    /* MLP over the features; execute-and-measure when its
+                               confidence is below the threshold (Sec. 6)      */
+  SMAT_TUNE_EXHAUSTIVE = 1, /* time every admissible variant, keep the fastest
+                               (the brute-force search of Sec. 7.3)          */
+  SMAT_TUNE_RULES = 2,      /* the paper's published thresholds (Sec. 4)       */
+  SMAT_TUNE_FIXED = 3       /* use opts.fixed_variant                          */
+} smat_tune_mode_t;
+
+typedef struct {
+  int32_t mode;            /* smat_tune_mode_t                                  */
+  int32_t fixed_variant;   /* for SMAT_TUNE_FIXED                                */
+  float conf_threshold;    /* learned mode: trial when max probability < this  */
+  int32_t fallback_topk;   /* learned mode: variants trialled on fallback (0=all) */
+  int32_t tau_num, tau_den;/* "true" diagonal: > tau_num/tau_den filled (3/5)  */
+  int32_t fill_ratio_max;  /* DIA/ELL admissible while Ndiags, max_RD <= this *
+                              aver_RD (Sec. 2.3: 20, i.e. >= 5% fill)          */
+  double bytes_cap;        /* DIA/ELL admissible while their bytes <= this *
+                              CSR bytes (default 4)                            */
+  int32_t trial_reps;      /* timed repetitions per variant (median)          */
+  int32_t trial_warmup;    /* untimed repetitions per variant                  */
+  double trial_budget_ms;  /* stop trialling further variants past this       */
+  uint32_t allowed;        /* bit mask over smat_variant_t (0 = all)           */
+  int32_t keep_formats;    /* 1: keep every converted format after tuning      */
+} smat_tune_opts_t;
+
+/* Fill *opts with the defaults above. */
+void smat_tune_opts_default(smat_tune_opts_t *opts);
+
+/* Short English text for a status code (static storage). */
+const char *smat_status_string(smat_status_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Matrix handle (Sec. 3: the unified CSR interface)                         */
+/* ------------------------------------------------------------------------ */
+
+/* Create a handle from a CSR matrix with m rows, n columns and nnz stored
+ * entries: rowptr[m+1], colidx[nnz] (int32), vals[nnz] of the storage type.
+ * The three pointers may be host or device memory (detected); they are copied
+ * into library-owned device memory before the call returns, so the caller may
+ * free them afterwards.  The copy is validated on the GPU (rowptr[0] = 0,
+ * rowptr[m] = nnz, monotone rowptr, 0 <= col < n, strictly increasing columns
+ * in each row); a violation returns SMAT_ERR_INVALID_CSR and no handle.  Until
+ * smat_tune runs, the plan is CSR-scalar (Sec. 4: CSR is the default format).
+ * m = 0 or nnz = 0 is allowed.  Errors: INVALID_ARG, INVALID_CSR, ALLOC, CUDA,
+ * UNSUPPORTED (m, n or nnz > 2^31 - 1). */
+smat_status_t smat_create(smat_handle_t *out, int64_t m, int64_t n, int64_t nnz,
+                          const int32_t *rowptr, const int32_t *colidx, const void *vals,
+                          smat_dtype_t dtype);
+
+/* Free the handle and everything it owns.  NULL is a no-op.  The handle must
+ * not be in use on any stream. */
+smat_status_t smat_destroy(smat_handle_t h);
+
+/* Run-time stage of Sec. 6: extract features (Sec. 4) if not done yet, choose
+ * a variant by opts->mode (NULL: learned when a model is loaded, otherwise
+ * exhaustive), convert CSR to its format (Sec. 2.1) and store the plan.  Work
+ * is issued on `stream`; the call returns after synchronising it. */
+smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts, void *stream);
+
+/* y = alpha*A*x + beta*y through the handle's plan.  x[n] and y[m] are DEVICE
+ * pointers of the compute type; alpha and beta HOST pointers.  Asynchronous on
+ * `stream`; only launch errors are reported.  x and y must not overlap. */
+smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const void *beta,
+                        void *y, void *stream);
+
+/* Same product through a chosen variant (its format is built on first use;
+ * SMAT_ERR_UNSUPPORTED if the variant is not admissible and cannot be built). */
+smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *alpha,
+                                const void *x, const void *beta, void *y, void *stream);
+
+/* Same product with x and y in HOST memory (pinned or pageable): x is copied to
+ * a device staging buffer, the product runs through the plan, y is copied
+ * back (and, when beta != 0, copied in first).  Returns after `stream` has
+ * finished, so y is ready on return. */
+smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_host,
+                             const void *beta, void *y_host, void *stream);
+
+/* Feature parameters (computes them on `stream` = NULL if not yet done). */
+smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out);
+
+/* The 12 selector inputs before standardisation: log1p of M, N, NNZ, aver_RD,
+ * max_RD, min_RD, var_RD, Ndiags, then NTdiags_ratio, ER_DIA, ER_ELL and R. */
+smat_status_t smat_get_feature_vector(smat_handle_t h, float out[12]);
+
+/* Current plan: variant, wall time of the last smat_tune in ms, selector
+ * confidence (max softmax probability; -1 when no model was used) and whether
+ * the execute-and-measure fallback ran. */
+smat_status_t smat_get_plan(smat_handle_t h, int32_t *variant, double *tune_ms, float *confidence,
+                            int32_t *trialled);
+
+/* Median trial time per variant in ms from the last smat_tune (-1 = not run). */
+smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_VARIANTS]);
+
+/* Build format `fmt` on the device now (ELL, DIA or COO; CSR is always there).
+ * UNSUPPORTED if the format is not admissible (fill or byte cap). */
+smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream);
+
+/* Layout of a built format:
+ *   ELL: dims = {K = max_RD, P = pitch}, arrays col int32[K*P], val[K*P]
+ *   DIA: dims = {Ndiags, P},             arrays offsets int32[Ndiags], val[Ndiags*P]
+ *   COO: dims = {NNZ, 0},                arrays row int32[NNZ] (col and val are CSR's)
+ * P is M rounded up to a multiple of 32; padding holds column -1 / value +0. */
+smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[2]);
+
+/* Copy a built format to caller memory (host or device, detected):
+ *   ELL: idx <- col, val <- val;  DIA: idx <- offsets, val <- val;
+ *   COO: idx <- row (val unused).  Sizes as in smat_format_dims. */
+smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *idx, void *val);
+
+/* ------------------------------------------------------------------------ */
+/* Learned selector (replaces the ruleset classifier of Sec. 5)             */
+/* MLP 12 -> 64 -> ReLU -> 64 -> ReLU -> 8 over standardised features.       */
+/* Parameters, FP32, row-major out x in:                                     */
+/*   W1[64][12] b1[64] W2[64][64] b2[64] W3[8][64] b3[8]  (5512 floats)      */
+/* ------------------------------------------------------------------------ */
+#define SMAT_MLP_PARAMS 5512
+
+/* Install the process-wide selector: parameters plus the standardisation
+ * mean[12] and std[12] (host pointers, copied).  NULL params uninstalls. */
+smat_status_t smat_set_model(const float *params, const float *mean, const float *std);
+
+/* Load a model file written by the training driver (magic "SMATMLP1",
+ * int32 version 1, mean[12], std[12], params[5512], all little-endian FP32). */
+smat_status_t smat_load_model(const char *path);
+
+/* Forward pass for B samples: X[B][12] (already standardised) -> logits[B][8].
+ * All pointers are DEVICE memory; asynchronous on `stream`. */
+smat_status_t smat_mlp_forward(const float *params, const float *X, int32_t B, float *logits,
+                               void *stream);
+
+/* Mean soft-target cross-entropy L = -(1/B) sum_b sum_c T[b][c] log softmax(z_b)_c
+ * and dL/dparams (backpropagation), for B samples.  Device pointers:
+ * params[5512], X[B][12], T[B][8], grad[5512], loss[1].  `work` is caller
+ * scratch of smat_mlp_work_floats(B) floats.  Deterministic. */
+int64_t smat_mlp_work_floats(int32_t B);
+smat_status_t smat_mlp_loss_grad(const float *params, const float *X, const float *T, int32_t B,
+                                 float *grad, float *loss, float *work, void *stream);
+
+/* One Adam step (Kingma & Ba 2015) on n parameters; t >= 1 is the step count.
+ * Device pointers p, g, m, v. */
+smat_status_t smat_mlp_adam(float *p, const float *g, float *m, float *v, int64_t n, int32_t t,
+                            float lr, float beta1, float beta2, float eps, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Value casts for reduced-precision storage (device arrays, n elements)    */
+/* ------------------------------------------------------------------------ */
+/* FP64 -> FP32, round to nearest even. */
+smat_status_t smat_cast_f64_to_f32(const double *in, float *out, int64_t n, void *stream);
+/* FP64 -> bfloat16 (uint16 bit patterns), round to nearest even, one rounding. */
+smat_status_t smat_cast_f64_to_bf16(const double *in, uint16_t *out, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Testing hook                                                              */
+/* ------------------------------------------------------------------------ */
+/* Make the k-th device allocation from now on fail (k >= 1), as if the GPU
+ * were out of memory; k = 0 disables.  Host-side only: lets tests check that
+ * every entry point returns SMAT_ERR_ALLOC and frees what it had allocated. */
+void smat_test_fail_alloc_after(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMAT_H */

@@ -1,0 +1,374 @@
+"""Input-adaptive SpMV for GB300 after SMAT (arXiv 1210.2536): Python binding.
+
+The functions below carry the names of the C ABI in ``include/smat.h`` and do
+argument marshalling only; every step of the product runs in libsmat's CUDA
+kernels.  PyTorch supplies device memory and streams.  ``SpMatrix`` wraps a
+handle for convenience.
+
+The library is built by ``__graft_entry__.build()`` (or
+``python -m paper_1210_2536_gb300._build``); importing this package without it
+raises, so nothing can silently fall back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsmat.so")
+
+SMAT_OK, SMAT_ERR_INVALID_ARG, SMAT_ERR_INVALID_CSR, SMAT_ERR_ALLOC, SMAT_ERR_CUDA, \
+    SMAT_ERR_UNSUPPORTED, SMAT_ERR_MODEL, SMAT_ERR_NOT_CONVERGED = range(8)
+SMAT_F64, SMAT_F32, SMAT_BF16 = range(3)
+SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO = range(4)
+(SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32, SMAT_V_CSR_MERGE, SMAT_V_ELL,
+ SMAT_V_DIA, SMAT_V_COO) = range(8)
+SMAT_NUM_VARIANTS = 8
+VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo"]
+SMAT_TUNE_LEARNED, SMAT_TUNE_EXHAUSTIVE, SMAT_TUNE_RULES, SMAT_TUNE_FIXED = range(4)
+SMAT_MLP_PARAMS = 5512
+DTYPES = {"f64": SMAT_F64, "f32": SMAT_F32, "bf16": SMAT_BF16}
+
+
+class SmatError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {smat_status_string(status)} (status {status})")
+
+
+class smat_features_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("m", "n", "nnz", "max_rd", "min_rd", "empty_rows", "ndiags",
+                                              "ntdiags")] + \
+               [("s2", ctypes.c_uint64)] + \
+               [(n, ctypes.c_double) for n in ("aver_rd", "var_rd", "er_dia", "er_ell", "ntdiags_ratio", "r")] + \
+               [("r_valid", ctypes.c_int32), ("admissible", ctypes.c_uint32)]
+
+
+class smat_tune_opts_t(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("fixed_variant", ctypes.c_int32), ("conf_threshold", ctypes.c_float),
+                ("fallback_topk", ctypes.c_int32), ("tau_num", ctypes.c_int32), ("tau_den", ctypes.c_int32),
+                ("fill_ratio_max", ctypes.c_int32), ("bytes_cap", ctypes.c_double), ("trial_reps", ctypes.c_int32),
+                ("trial_warmup", ctypes.c_int32), ("trial_budget_ms", ctypes.c_double),
+                ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32)]
+
+
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_SIGS = {
+    "smat_tune_opts_default": (None, [ctypes.POINTER(smat_tune_opts_t)]),
+    "smat_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "smat_test_fail_alloc_after": (None, [_I32]),
+    "smat_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int]),
+    "smat_destroy": (ctypes.c_int, [_VP]),
+    "smat_tune": (ctypes.c_int, [_VP, ctypes.POINTER(smat_tune_opts_t), _VP]),
+    "smat_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
+    "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
+    "smat_get_plan": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "smat_get_timings": (ctypes.c_int, [_VP, _VP]),
+    "smat_convert": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "smat_format_dims": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "smat_export_format": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "smat_set_model": (ctypes.c_int, [_VP, _VP, _VP]),
+    "smat_load_model": (ctypes.c_int, [ctypes.c_char_p]),
+    "smat_mlp_forward": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
+    "smat_mlp_work_floats": (_I64, [_I32]),
+    "smat_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP]),
+    "smat_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _I32, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, _VP]),
+    "smat_cast_f64_to_f32": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "smat_cast_f64_to_bf16": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libsmat (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != SMAT_OK:
+        raise SmatError(status, where)
+    return status
+
+
+def smat_status_string(s: int) -> str:
+    try:
+        return lib().smat_status_string(int(s)).decode()
+    except RuntimeError:
+        return f"status {s}"
+
+
+def smat_tune_opts_default() -> smat_tune_opts_t:
+    o = smat_tune_opts_t()
+    lib().smat_tune_opts_default(ctypes.byref(o))
+    return o
+
+
+# -- raw entry points: integers are pointers (tensor.data_ptr() / ndarray.ctypes.data) --
+
+def smat_create(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dtype):
+    h = _VP()
+    st = lib().smat_create(ctypes.byref(h), m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dtype)
+    return st, h.value
+
+
+def smat_destroy(h):
+    return lib().smat_destroy(h)
+
+
+def smat_tune(h, opts: smat_tune_opts_t | None, stream=0):
+    return lib().smat_tune(h, ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def smat_spmv(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
+    return lib().smat_spmv(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_spmv_variant(h, v, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
+    return lib().smat_spmv_variant(h, v, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
+    return lib().smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_get_features(h) -> smat_features_t:
+    f = smat_features_t()
+    _check(lib().smat_get_features(h, ctypes.byref(f)), "smat_get_features")
+    return f
+
+
+def smat_get_feature_vector(h) -> np.ndarray:
+    out = np.zeros(12, dtype=np.float32)
+    _check(lib().smat_get_feature_vector(h, out.ctypes.data), "smat_get_feature_vector")
+    return out
+
+
+def smat_get_plan(h):
+    v, ms, conf, tr = ctypes.c_int32(), ctypes.c_double(), ctypes.c_float(), ctypes.c_int32()
+    _check(lib().smat_get_plan(h, ctypes.byref(v), ctypes.byref(ms), ctypes.byref(conf), ctypes.byref(tr)),
+           "smat_get_plan")
+    return v.value, ms.value, conf.value, tr.value
+
+
+def smat_get_timings(h) -> np.ndarray:
+    out = np.zeros(SMAT_NUM_VARIANTS, dtype=np.float32)
+    _check(lib().smat_get_timings(h, out.ctypes.data), "smat_get_timings")
+    return out
+
+
+def smat_convert(h, fmt, stream=0):
+    return lib().smat_convert(h, fmt, stream)
+
+
+def smat_format_dims(h, fmt):
+    d = np.zeros(2, dtype=np.int64)
+    st = lib().smat_format_dims(h, fmt, d.ctypes.data)
+    return st, int(d[0]), int(d[1])
+
+
+def smat_export_format(h, fmt, idx_ptr, val_ptr):
+    return lib().smat_export_format(h, fmt, idx_ptr, val_ptr)
+
+
+def smat_set_model(params, mean, std):
+    if params is None:
+        return lib().smat_set_model(None, None, None)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    sd = np.ascontiguousarray(std, dtype=np.float32)
+    assert p.size == SMAT_MLP_PARAMS and mu.size == 12 and sd.size == 12
+    return lib().smat_set_model(p.ctypes.data, mu.ctypes.data, sd.ctypes.data)
+
+
+def smat_load_model(path: str):
+    return lib().smat_load_model(os.fsencode(path))
+
+
+def smat_mlp_forward(params_ptr, x_ptr, B, logits_ptr, stream=0):
+    return lib().smat_mlp_forward(params_ptr, x_ptr, B, logits_ptr, stream)
+
+
+def smat_mlp_work_floats(B) -> int:
+    return int(lib().smat_mlp_work_floats(B))
+
+
+def smat_mlp_loss_grad(params_ptr, x_ptr, t_ptr, B, grad_ptr, loss_ptr, work_ptr, stream=0):
+    return lib().smat_mlp_loss_grad(params_ptr, x_ptr, t_ptr, B, grad_ptr, loss_ptr, work_ptr, stream)
+
+
+def smat_mlp_adam(p_ptr, g_ptr, m_ptr, v_ptr, n, t, lr, b1, b2, eps, stream=0):
+    return lib().smat_mlp_adam(p_ptr, g_ptr, m_ptr, v_ptr, n, t, lr, b1, b2, eps, stream)
+
+
+def smat_cast_f64_to_f32(in_ptr, out_ptr, n, stream=0):
+    return lib().smat_cast_f64_to_f32(in_ptr, out_ptr, n, stream)
+
+
+def smat_cast_f64_to_bf16(in_ptr, out_ptr, n, stream=0):
+    return lib().smat_cast_f64_to_bf16(in_ptr, out_ptr, n, stream)
+
+
+def write_model(path, params, mean, std):
+    """Model file read by smat_load_model: b"SMATMLP1", int32 1, mean[12], std[12], params[5512] (FP32 LE)."""
+    with open(path, "wb") as f:
+        f.write(b"SMATMLP1")
+        f.write(struct.pack("<i", 1))
+        for a in (mean, std, params):
+            f.write(np.ascontiguousarray(a, dtype="<f4").tobytes())
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper over torch tensors (marshalling only)
+# ---------------------------------------------------------------------------
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class SpMatrix:
+    """A CSR matrix handed to libsmat (Sec. 3: the unified CSR interface).
+
+    ``rowptr``/``colidx``/``vals`` may be torch tensors (CPU or CUDA) or numpy
+    arrays; they are copied into library-owned device memory.  ``dtype`` is the
+    value storage: "f64", "f32" or "bf16" (bf16 values are passed as 16-bit
+    patterns in a uint16/int16 array or as a torch.bfloat16 tensor)."""
+
+    def __init__(self, m, n, rowptr, colidx, vals, dtype="f64"):
+        self.m, self.n = int(m), int(n)
+        self.dtype = dtype
+        self._keep = [rowptr, colidx, vals]
+        rp, ci, vv = (_ptr(a) for a in (rowptr, colidx, vals))
+        self.nnz = int(_len(colidx))
+        st, h = smat_create(self.m, self.n, self.nnz, rp, ci, vv, DTYPES[dtype])
+        self._keep = None
+        _check(st, "smat_create")
+        self.h = h
+
+    @property
+    def compute_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == "f64" else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            smat_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, mode="exhaustive", variant=None, stream=None, **kw):
+        o = smat_tune_opts_default()
+        o.mode = {"learned": SMAT_TUNE_LEARNED, "exhaustive": SMAT_TUNE_EXHAUSTIVE, "rules": SMAT_TUNE_RULES,
+                  "fixed": SMAT_TUNE_FIXED}[mode]
+        if variant is not None:
+            o.fixed_variant = int(variant)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        _check(smat_tune(self.h, o, _stream_ptr(stream)), "smat_tune")
+        return self
+
+    def _scalars(self, alpha, beta):
+        if self.dtype == "f64":
+            a, b = ctypes.c_double(alpha), ctypes.c_double(beta)
+        else:
+            a, b = ctypes.c_float(alpha), ctypes.c_float(beta)
+        return a, b
+
+    def spmv(self, x, y=None, alpha=1.0, beta=0.0, variant=None, stream=None):
+        """y = alpha*A*x + beta*y on the device; returns y (a CUDA tensor)."""
+        import torch
+        if y is None:
+            y = torch.empty(self.m, dtype=self.compute_dtype, device=x.device)
+        assert x.dtype == self.compute_dtype and y.dtype == self.compute_dtype and x.is_cuda and y.is_cuda
+        assert x.is_contiguous() and y.is_contiguous()
+        a, b = self._scalars(alpha, beta)
+        s = _stream_ptr(stream)
+        if variant is None:
+            st = smat_spmv(self.h, ctypes.addressof(a), x.data_ptr(), ctypes.addressof(b), y.data_ptr(), s)
+        else:
+            st = smat_spmv_variant(self.h, int(variant), ctypes.addressof(a), x.data_ptr(), ctypes.addressof(b),
+                                   y.data_ptr(), s)
+        _check(st, "smat_spmv")
+        return y
+
+    def spmv_host(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        """Same product with host (CPU tensor / ndarray) x and y; y holds the result on return."""
+        a, b = self._scalars(alpha, beta)
+        _check(smat_spmv_host(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
+                              _stream_ptr(stream)), "smat_spmv_host")
+        return y
+
+    def features(self) -> dict:
+        f = smat_get_features(self.h)
+        return {n: getattr(f, n) for n, _ in smat_features_t._fields_}
+
+    def feature_vector(self) -> np.ndarray:
+        return smat_get_feature_vector(self.h)
+
+    def plan(self) -> dict:
+        v, ms, conf, tr = smat_get_plan(self.h)
+        return {"variant": v, "name": VARIANT_NAMES[v], "tune_ms": ms, "confidence": conf, "trialled": tr}
+
+    def timings(self) -> np.ndarray:
+        return smat_get_timings(self.h)
+
+    def convert(self, fmt, stream=None):
+        _check(smat_convert(self.h, fmt, _stream_ptr(stream)), "smat_convert")
+
+    def export(self, fmt):
+        """Copy a built format to host numpy arrays (see smat_format_dims)."""
+        st, d0, d1 = smat_format_dims(self.h, fmt)
+        _check(st, "smat_format_dims")
+        vdt = {"f64": np.float64, "f32": np.float32, "bf16": np.uint16}[self.dtype]
+        if fmt == SMAT_FMT_ELL:
+            idx, val = np.empty(d0 * d1, np.int32), np.empty(d0 * d1, vdt)
+        elif fmt == SMAT_FMT_DIA:
+            idx, val = np.empty(d0, np.int32), np.empty(d0 * d1, vdt)
+        else:
+            idx, val = np.empty(d0, np.int32), None
+        _check(smat_export_format(self.h, fmt, idx.ctypes.data, None if val is None else val.ctypes.data),
+               "smat_export_format")
+        return idx, val, d0, d1
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr() if a.numel() else None
+    a = np.asarray(a)
+    assert a.flags.c_contiguous
+    return a.ctypes.data if a.size else None
+
+
+def _len(a):
+    return a.numel() if hasattr(a, "numel") else np.asarray(a).size

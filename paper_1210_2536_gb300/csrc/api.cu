@@ -1,0 +1,736 @@
+// C ABI of libsmat: the unified CSR interface (arXiv 1210.2536, Sec. 3) and
+// the run-time stage (Sec. 6): feature extraction -> format search ->
+// confidence check -> execute & measure -> convert -> SpMV.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "smat_internal.h"
+
+namespace smat {
+
+// ---------------------------------------------------------------------------
+// Allocation with a test hook (error-path tests inject a failure on the host).
+// ---------------------------------------------------------------------------
+static std::atomic<long> g_alloc_fail_at{0};
+static std::atomic<long> g_alloc_count{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  long k = ++g_alloc_count;
+  long f = g_alloc_fail_at.load();
+  if (f > 0 && k == f) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+void dev_free(void *p) {
+  if (p) cudaFree(p);
+}
+
+Model &model() {
+  static Model m;
+  return m;
+}
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() { dev_free(p); }
+  cudaError_t alloc(size_t bytes) { return dev_alloc(&p, bytes); }
+  template <typename T> T *as() const { return (T *)p; }
+};
+
+smat_status_t st_of(cudaError_t e) {
+  if (e == cudaSuccess) return SMAT_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SMAT_ERR_ALLOC;
+  }
+  return SMAT_ERR_CUDA;
+}
+
+#define TRY(call)                               \
+  do {                                          \
+    smat_status_t _s = st_of(call);             \
+    if (_s != SMAT_OK) return _s;               \
+  } while (0)
+#define TRYS(call)                              \
+  do {                                          \
+    smat_status_t _s = (call);                  \
+    if (_s != SMAT_OK) return _s;               \
+  } while (0)
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int tsize(const smat_s *h) { return h->dtype == SMAT_F64 ? 8 : 4; }
+
+int variant_format(int v) {
+  if (v == SMAT_V_ELL) return SMAT_FMT_ELL;
+  if (v == SMAT_V_DIA) return SMAT_FMT_DIA;
+  if (v == SMAT_V_COO) return SMAT_FMT_COO;
+  return SMAT_FMT_CSR;
+}
+
+double csr_bytes(const smat_s *h) { return (double)(h->esz + 4) * h->nnz + 4.0 * (h->m + 1); }
+double ell_bytes(const smat_s *h) { return (double)(h->esz + 4) * h->f.max_rd * h->P; }
+double dia_bytes(const smat_s *h) { return (double)h->esz * h->f.ndiags * h->P + 4.0 * h->f.ndiags; }
+
+// ---------------------------------------------------------------------------
+// Feature extraction (Sec. 4): integer passes on the GPU, then the doubles
+// from exact integers, each operand converted once and one division.
+// ---------------------------------------------------------------------------
+void power_law_fit(const std::vector<int64_t> &hist, double *R, int32_t *valid) {
+  double cnt = 0.0, sum_x = 0.0, sum_y = 0.0, sum_xx = 0.0, sum_xy = 0.0;
+  for (size_t k = 1; k < hist.size(); ++k) {
+    if (hist[k] <= 0) continue;
+    const double lk = std::log((double)k), lh = std::log((double)hist[k]);
+    cnt = cnt + 1.0;
+    sum_x = sum_x + lk;
+    sum_y = sum_y + lh;
+    sum_xx = sum_xx + lk * lk;
+    sum_xy = sum_xy + lk * lh;
+  }
+  if (cnt < 2.0) {
+    *R = 0.0;
+    *valid = 0;
+    return;
+  }
+  const double slope_num = cnt * sum_xy - sum_x * sum_y;
+  const double slope_den = cnt * sum_xx - sum_x * sum_x;
+  *R = -(slope_num / slope_den);
+  *valid = 1;
+}
+
+void update_admissible(smat_s *h) {
+  smat_features_t &f = h->f;
+  uint32_t mask = (1u << SMAT_V_CSR_SCALAR) | (1u << SMAT_V_CSR_VEC4) | (1u << SMAT_V_CSR_VEC8) |
+                  (1u << SMAT_V_CSR_VEC32) | (1u << SMAT_V_CSR_MERGE) | (1u << SMAT_V_COO);
+  const double cap = h->bytes_cap * std::max(csr_bytes(h), 1.0);
+  // Sec. 2.3: DIA / ELL only while Ndiags (max_RD) <= 20 x aver_RD, i.e.
+  // at least 5% of the stored slots are nonzeros; plus a hard byte cap.
+  const __int128 lim = (__int128)h->fill_ratio_max * f.nnz;
+  if (f.m > 0 && f.max_rd > 0 && (__int128)f.max_rd * f.m <= lim && ell_bytes(h) <= cap) mask |= 1u << SMAT_V_ELL;
+  // the DIA kernel stages its offsets in shared memory: at most 8192 of them
+  if (f.m > 0 && f.ndiags > 0 && f.ndiags <= 8192 && h->dia_offsets_complete && (__int128)f.ndiags * f.m <= lim &&
+      dia_bytes(h) <= cap)
+    mask |= 1u << SMAT_V_DIA;
+  f.admissible = mask;
+}
+
+smat_status_t compute_features(smat_s *h, cudaStream_t s) {
+  smat_features_t f{};
+  f.m = h->m;
+  f.n = h->n;
+  f.nnz = h->nnz;
+  RowStats st{0ull, 0, h->m > 0 ? INT_MAX : 0, 0, 0};
+  if (h->m > 0) {
+    DevBuf d_st;
+    TRY(d_st.alloc(sizeof(RowStats)));
+    TRY(cudaMemcpyAsync(d_st.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    TRY(launch_row_stats(h->rowptr, h->m, d_st.as<RowStats>(), s));
+    TRY(cudaMemcpyAsync(&st, d_st.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+  }
+  f.max_rd = st.max_rd;
+  f.min_rd = st.min_rd;
+  f.empty_rows = st.empty_rows;
+  f.s2 = st.s2;
+  const int64_t hist_len = f.max_rd + 1;
+  h->hist.assign((size_t)hist_len, 0);
+  h->dia_offsets.clear();
+  h->dia_offsets_complete = false;
+  const int64_t nd_all = h->m + h->n - 1;
+  if (h->m > 0 && h->n > 0) {
+    DevBuf d_hist, d_cnt, d_counts, d_off;
+    TRY(d_hist.alloc((size_t)hist_len * sizeof(int)));
+    TRY(d_cnt.alloc((size_t)nd_all * sizeof(int)));
+    TRY(cudaMemsetAsync(d_hist.p, 0, (size_t)hist_len * sizeof(int), s));
+    TRY(cudaMemsetAsync(d_cnt.p, 0, (size_t)nd_all * sizeof(int), s));
+    TRY(launch_hist_diag(h->rowptr, h->colidx, h->m, d_hist.as<int>(), hist_len, d_cnt.as<int>(), s));
+    // offsets are kept while DIA can still be admissible (Ndiags <= 20 aver_RD)
+    int64_t cap = (int64_t)((__int128)h->fill_ratio_max * h->nnz / h->m) + 1;
+    cap = std::max<int64_t>(cap, 64);
+    cap = std::min<int64_t>(cap, nd_all);
+    TRY(d_counts.alloc(3 * sizeof(unsigned long long)));
+    TRY(d_off.alloc((size_t)cap * sizeof(int32_t)));
+    TRY(cudaMemsetAsync(d_counts.p, 0, 3 * sizeof(unsigned long long), s));
+    TRY(launch_diag_reduce(d_cnt.as<int>(), h->m, h->n, h->tau_num, h->tau_den,
+                           d_counts.as<unsigned long long>(), d_off.as<int32_t>(), cap, s));
+    unsigned long long counts[3];
+    std::vector<int> hist32((size_t)hist_len);
+    TRY(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, s));
+    TRY(cudaMemcpyAsync(hist32.data(), d_hist.p, (size_t)hist_len * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    for (int64_t k = 0; k < hist_len; ++k) h->hist[(size_t)k] = hist32[(size_t)k];
+    f.ndiags = (int64_t)counts[0];
+    f.ntdiags = (int64_t)counts[1];
+    if ((int64_t)counts[2] <= cap) {
+      h->dia_offsets.resize((size_t)counts[2]);
+      TRY(cudaMemcpy(h->dia_offsets.data(), d_off.p, (size_t)counts[2] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      std::sort(h->dia_offsets.begin(), h->dia_offsets.end());
+      h->dia_offsets_complete = true;
+    }
+  } else if (h->m > 0) {
+    h->hist[0] = h->m;  // no columns: every row is empty
+  }
+  if (h->m > 0) {
+    const double M = (double)h->m;
+    f.aver_rd = (double)h->nnz / M;
+    const __int128 var_num = (__int128)h->m * (__int128)f.s2 - (__int128)h->nnz * (__int128)h->nnz;
+    const __int128 var_den = (__int128)h->m * (__int128)h->m;
+    f.var_rd = (double)var_num / (double)var_den;
+    f.er_dia = f.ndiags > 0 ? (double)h->nnz / (double)(f.ndiags * h->m) : 0.0;
+    f.er_ell = f.max_rd > 0 ? (double)h->nnz / (double)(f.max_rd * h->m) : 0.0;
+  }
+  f.ntdiags_ratio = f.ndiags > 0 ? (double)f.ntdiags / (double)f.ndiags : 0.0;
+  power_law_fit(h->hist, &f.r, &f.r_valid);
+  h->f = f;
+  h->have_features = true;
+  update_admissible(h);
+  return SMAT_OK;
+}
+
+void feature_vector(const smat_features_t &f, float out[12]) {
+  out[0] = (float)std::log1p((double)f.m);
+  out[1] = (float)std::log1p((double)f.n);
+  out[2] = (float)std::log1p((double)f.nnz);
+  out[3] = (float)std::log1p(f.aver_rd);
+  out[4] = (float)std::log1p((double)f.max_rd);
+  out[5] = (float)std::log1p((double)f.min_rd);
+  out[6] = (float)std::log1p(f.var_rd);
+  out[7] = (float)std::log1p((double)f.ndiags);
+  out[8] = (float)f.ntdiags_ratio;
+  out[9] = (float)f.er_dia;
+  out[10] = (float)f.er_ell;
+  out[11] = (float)(f.r_valid ? std::max(-100.0, std::min(100.0, f.r)) : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Format construction (Sec. 2.1).
+// ---------------------------------------------------------------------------
+void free_format(smat_s *h, int fmt) {
+  if (fmt == SMAT_FMT_ELL) {
+    dev_free(h->ell_col); dev_free(h->ell_val);
+    h->ell_col = nullptr; h->ell_val = nullptr; h->ell_K = 0;
+  } else if (fmt == SMAT_FMT_DIA) {
+    dev_free(h->dia_off); dev_free(h->dia_val);
+    h->dia_off = nullptr; h->dia_val = nullptr; h->dia_nd = 0;
+  } else if (fmt == SMAT_FMT_COO) {
+    dev_free(h->coo_row); dev_free(h->coo_empty);
+    h->coo_row = nullptr; h->coo_empty = nullptr; h->coo_nempty = 0;
+  }
+}
+
+smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
+  if (fmt == SMAT_FMT_CSR) return SMAT_OK;
+  if (!h->have_features) TRYS(compute_features(h, s));
+  if (fmt == SMAT_FMT_ELL) {
+    if (h->ell_val) return SMAT_OK;
+    if (!(h->f.admissible & (1u << SMAT_V_ELL))) return SMAT_ERR_UNSUPPORTED;
+    const int64_t K = h->f.max_rd;
+    if (K == 0) return SMAT_ERR_UNSUPPORTED;
+    void *c = nullptr, *v = nullptr;
+    TRY(dev_alloc(&c, (size_t)(K * h->P) * 4));
+    cudaError_t e = dev_alloc(&v, (size_t)(K * h->P) * h->esz);
+    if (e != cudaSuccess) { dev_free(c); return st_of(e); }
+    h->ell_col = (int32_t *)c; h->ell_val = v; h->ell_K = K;
+    TRY(launch_to_ell(h, K, h->ell_col, h->ell_val, s));
+    return SMAT_OK;
+  }
+  if (fmt == SMAT_FMT_DIA) {
+    if (h->dia_val) return SMAT_OK;
+    if (!(h->f.admissible & (1u << SMAT_V_DIA))) return SMAT_ERR_UNSUPPORTED;
+    const int64_t nd = (int64_t)h->dia_offsets.size();
+    void *o = nullptr, *v = nullptr;
+    TRY(dev_alloc(&o, (size_t)nd * 4));
+    cudaError_t e = dev_alloc(&v, (size_t)(nd * h->P) * h->esz);
+    if (e != cudaSuccess) { dev_free(o); return st_of(e); }
+    h->dia_off = (int32_t *)o; h->dia_val = v; h->dia_nd = nd;
+    TRY(cudaMemcpyAsync(h->dia_off, h->dia_offsets.data(), (size_t)nd * 4, cudaMemcpyHostToDevice, s));
+    TRY(launch_to_dia(h, h->dia_off, nd, h->dia_val, s));
+    TRY(cudaStreamSynchronize(s));  // the host offsets buffer must outlive the copy
+    return SMAT_OK;
+  }
+  if (fmt == SMAT_FMT_COO) {
+    if (h->coo_row || h->coo_empty) return SMAT_OK;
+    void *r = nullptr;
+    if (h->nnz > 0) {
+      TRY(dev_alloc(&r, (size_t)h->nnz * 4));
+      h->coo_row = (int32_t *)r;
+      TRY(launch_to_coo(h, h->coo_row, s));
+    }
+    if (h->f.empty_rows > 0) {
+      void *l = nullptr;
+      DevBuf cnt;
+      TRY(dev_alloc(&l, (size_t)h->f.empty_rows * 4));
+      h->coo_empty = (int32_t *)l;
+      h->coo_nempty = h->f.empty_rows;
+      TRY(cnt.alloc(sizeof(int)));
+      TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int), s));
+      TRY(launch_empty_rows(h, h->coo_empty, cnt.as<int>(), s));
+      TRY(cudaStreamSynchronize(s));
+    }
+    return SMAT_OK;
+  }
+  return SMAT_ERR_INVALID_ARG;
+}
+
+smat_status_t ensure_scratch(smat_s *h, int variant) {
+  size_t need = carry_bytes_needed(h, variant);
+  if (need <= h->carry_bytes) return SMAT_OK;
+  void *p = nullptr;
+  TRY(dev_alloc(&p, need));
+  dev_free(h->carry);
+  h->carry = p;
+  h->carry_bytes = need;
+  return SMAT_OK;
+}
+
+bool variant_ready(const smat_s *h, int v) {
+  int fmt = variant_format(v);
+  if (fmt == SMAT_FMT_ELL && !h->ell_val) return false;
+  if (fmt == SMAT_FMT_DIA && !h->dia_val) return false;
+  if (fmt == SMAT_FMT_COO && !h->coo_row && !(h->nnz == 0)) return false;
+  if (fmt == SMAT_FMT_COO && h->f.empty_rows > 0 && !h->coo_empty) return false;
+  if (carry_bytes_needed(h, v) > h->carry_bytes) return false;
+  return true;
+}
+
+smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
+  if (v < 0 || v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  int fmt = variant_format(v);
+  if (fmt != SMAT_FMT_CSR && !h->have_features) TRYS(compute_features(h, s));
+  TRYS(build_format(h, fmt, s));
+  TRYS(ensure_scratch(h, v));
+  return SMAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Execute & measure (Sec. 6) / brute-force search (Sec. 7.3): median of timed
+// repetitions per candidate, on zero vectors.
+// ---------------------------------------------------------------------------
+smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_opts_t &o, cudaStream_t s,
+                    int *best) {
+  DevBuf x, y;
+  TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * tsize(h)));
+  TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * tsize(h)));
+  TRY(cudaMemsetAsync(x.p, 0, (size_t)std::max<int64_t>(h->n, 1) * tsize(h), s));
+  TRY(cudaMemsetAsync(y.p, 0, (size_t)std::max<int64_t>(h->m, 1) * tsize(h), s));
+  const double one = 1.0, zero = 0.0;
+  const float onef = 1.0f, zerof = 0.0f;
+  const void *a = h->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
+  const void *b = h->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
+  const int reps = std::max(1, o.trial_reps);
+  std::vector<cudaEvent_t> ev((size_t)reps * 2);
+  for (auto &e : ev) TRY(cudaEventCreate(&e));
+  struct EvGuard {
+    std::vector<cudaEvent_t> &v;
+    ~EvGuard() { for (auto e : v) if (e) cudaEventDestroy(e); }
+  } guard{ev};
+  const double t_start = now_ms();
+  float best_ms = 1e30f;
+  *best = -1;
+  for (int v : cands) {
+    if (*best >= 0 && now_ms() - t_start > o.trial_budget_ms) break;
+    smat_status_t ps = prepare_variant(h, v, s);
+    if (ps == SMAT_ERR_UNSUPPORTED || ps == SMAT_ERR_ALLOC) continue;  // skip, keep searching
+    TRYS(ps);
+    for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s));
+    for (int r = 0; r < reps; ++r) {
+      TRY(cudaEventRecord(ev[2 * r], s));
+      TRY(launch_spmv(h, v, a, x.p, b, y.p, s));
+      TRY(cudaEventRecord(ev[2 * r + 1], s));
+    }
+    TRY(cudaStreamSynchronize(s));
+    std::vector<float> ms((size_t)reps);
+    for (int r = 0; r < reps; ++r) TRY(cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]));
+    std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
+    float med = ms[(size_t)reps / 2];
+    h->timings[v] = med;
+    if (med < best_ms) {
+      best_ms = med;
+      *best = v;
+    }
+    if (!o.keep_formats) {
+      // drop a trialled format right away unless it is the best so far
+      for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_COO; ++fmt)
+        if (fmt != variant_format(*best)) free_format(h, fmt);
+    }
+  }
+  if (*best < 0) *best = SMAT_V_CSR_SCALAR;
+  return SMAT_OK;
+}
+
+// The paper's observations (Sec. 4) as an ordered rule set: DIA, ELL, CSR, COO
+// (Sec. 6 gives this order).  CSR maps to the CSR-vector width that fits the
+// mean row length.
+int rules_select(const smat_features_t &f, uint32_t ok) {
+  if ((ok >> SMAT_V_DIA) & 1u) {
+    if (f.ndiags <= 500 && (f.ndiags < 25 || f.er_dia > 0.6 || f.ntdiags_ratio > 0.4)) return SMAT_V_DIA;
+  }
+  if ((ok >> SMAT_V_ELL) & 1u) {
+    if ((f.max_rd < 5 || f.er_ell > 0.9) && f.var_rd < 0.5) return SMAT_V_ELL;
+  }
+  int csr = f.aver_rd < 8.0 ? SMAT_V_CSR_VEC4 : (f.aver_rd < 24.0 ? SMAT_V_CSR_VEC8 : SMAT_V_CSR_VEC32);
+  bool small_world = f.r_valid && f.r >= 1.0 && f.r < 4.0;
+  if (small_world && ((ok >> SMAT_V_COO) & 1u)) return SMAT_V_COO;
+  if ((ok >> csr) & 1u) return csr;
+  for (int v = 0; v < SMAT_NUM_VARIANTS; ++v)
+    if ((ok >> v) & 1u) return v;
+  return SMAT_V_CSR_SCALAR;
+}
+
+smat_status_t mlp_probs(const smat_s *h, float probs[SMAT_NUM_VARIANTS], cudaStream_t s) {
+  const Model &M = model();
+  float v[12];
+  feature_vector(h->f, v);
+  for (int i = 0; i < 12; ++i) v[i] = (v[i] - M.mean[i]) / (M.stdv[i] > 0 ? M.stdv[i] : 1.0f);
+  DevBuf d;
+  const size_t np = SMAT_MLP_PARAMS;
+  TRY(d.alloc((np + 12 + 8) * sizeof(float)));
+  float *dp = d.as<float>(), *dx = dp + np, *dz = dx + 12;
+  TRY(cudaMemcpyAsync(dp, M.params, np * sizeof(float), cudaMemcpyHostToDevice, s));
+  TRY(cudaMemcpyAsync(dx, v, 12 * sizeof(float), cudaMemcpyHostToDevice, s));
+  TRY(launch_mlp_forward(dp, dx, 1, dz, s));
+  float z[8];
+  TRY(cudaMemcpyAsync(z, dz, sizeof(z), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  float zmax = -INFINITY;
+  for (int c = 0; c < 8; ++c)
+    if ((h->f.admissible >> c) & 1u) zmax = std::max(zmax, z[c]);
+  double se = 0.0;
+  for (int c = 0; c < 8; ++c) se += ((h->f.admissible >> c) & 1u) ? std::exp((double)(z[c] - zmax)) : 0.0;
+  for (int c = 0; c < 8; ++c)
+    probs[c] = ((h->f.admissible >> c) & 1u) ? (float)(std::exp((double)(z[c] - zmax)) / se) : 0.0f;
+  return SMAT_OK;
+}
+
+smat_status_t check_handle(const smat_s *h) { return h ? SMAT_OK : SMAT_ERR_INVALID_ARG; }
+
+}  // namespace
+}  // namespace smat
+
+using namespace smat;
+
+extern "C" {
+
+void smat_tune_opts_default(smat_tune_opts_t *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = SMAT_TUNE_LEARNED;
+  o->fixed_variant = SMAT_V_CSR_SCALAR;
+  o->conf_threshold = 0.6f;
+  o->fallback_topk = 3;
+  o->tau_num = 3;
+  o->tau_den = 5;
+  o->fill_ratio_max = 20;
+  o->bytes_cap = 4.0;
+  o->trial_reps = 10;
+  o->trial_warmup = 2;
+  o->trial_budget_ms = 2000.0;
+  o->allowed = 0;
+  o->keep_formats = 0;
+}
+
+const char *smat_status_string(smat_status_t s) {
+  switch (s) {
+    case SMAT_OK: return "ok";
+    case SMAT_ERR_INVALID_ARG: return "invalid argument";
+    case SMAT_ERR_INVALID_CSR: return "invalid CSR structure";
+    case SMAT_ERR_ALLOC: return "allocation failed";
+    case SMAT_ERR_CUDA: return "CUDA error";
+    case SMAT_ERR_UNSUPPORTED: return "unsupported (size or format not admissible)";
+    case SMAT_ERR_MODEL: return "selector model missing or malformed";
+    case SMAT_ERR_NOT_CONVERGED: return "not converged";
+  }
+  return "unknown status";
+}
+
+void smat_test_fail_alloc_after(int32_t k) {
+  g_alloc_count = 0;
+  g_alloc_fail_at = k;
+}
+
+smat_status_t smat_create(smat_handle_t *out, int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                          const int32_t *colidx, const void *vals, smat_dtype_t dtype) {
+  if (!out) return SMAT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (m < 0 || n < 0 || nnz < 0 || !rowptr) return SMAT_ERR_INVALID_ARG;
+  if (dtype != SMAT_F64 && dtype != SMAT_F32 && dtype != SMAT_BF16) return SMAT_ERR_INVALID_ARG;
+  if (nnz > 0 && (!colidx || !vals)) return SMAT_ERR_INVALID_ARG;
+  if (m > INT32_MAX - 1 || n > INT32_MAX || nnz > INT32_MAX || m + n > (int64_t)INT32_MAX * 2)
+    return SMAT_ERR_UNSUPPORTED;
+  smat_s *h = new (std::nothrow) smat_s();
+  if (!h) return SMAT_ERR_ALLOC;
+  h->m = m; h->n = n; h->nnz = nnz; h->dtype = dtype; h->esz = elem_size(dtype); h->P = pitch_of(m);
+  for (auto &t : h->timings) t = -1.0f;
+  auto fail = [&](smat_status_t s) { smat_destroy(h); return s; };
+  void *p = nullptr;
+  cudaError_t e = dev_alloc(&p, (size_t)(m + 1) * 4);
+  if (e != cudaSuccess) return fail(st_of(e));
+  h->rowptr = (int32_t *)p;
+  if (nnz > 0) {
+    if ((e = dev_alloc(&p, (size_t)nnz * 4)) != cudaSuccess) return fail(st_of(e));
+    h->colidx = (int32_t *)p;
+    if ((e = dev_alloc(&p, (size_t)nnz * h->esz)) != cudaSuccess) return fail(st_of(e));
+    h->val = p;
+  }
+  if ((e = cudaMemcpy(h->rowptr, rowptr, (size_t)(m + 1) * 4, cudaMemcpyDefault)) != cudaSuccess) return fail(st_of(e));
+  if (nnz > 0) {
+    if ((e = cudaMemcpy(h->colidx, colidx, (size_t)nnz * 4, cudaMemcpyDefault)) != cudaSuccess) return fail(st_of(e));
+    if ((e = cudaMemcpy(h->val, vals, (size_t)nnz * h->esz, cudaMemcpyDefault)) != cudaSuccess) return fail(st_of(e));
+  }
+  // K1: structural validation on the device, reported through a flag.
+  void *flag = nullptr;
+  if ((e = dev_alloc(&flag, sizeof(int))) != cudaSuccess) return fail(st_of(e));
+  int hf = 0;
+  e = cudaMemset(flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_validate(h, (int *)flag, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  dev_free(flag);
+  if (e != cudaSuccess) return fail(st_of(e));
+  if (hf) return fail(SMAT_ERR_INVALID_CSR);
+  *out = h;
+  return SMAT_OK;
+}
+
+smat_status_t smat_destroy(smat_handle_t h) {
+  if (!h) return SMAT_OK;
+  dev_free(h->rowptr); dev_free(h->colidx); dev_free(h->val);
+  free_format(h, SMAT_FMT_ELL); free_format(h, SMAT_FMT_DIA); free_format(h, SMAT_FMT_COO);
+  dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y);
+  delete h;
+  return SMAT_OK;
+}
+
+smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *stream) {
+  TRYS(check_handle(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  smat_tune_opts_t o;
+  if (opts_in) o = *opts_in; else { smat_tune_opts_default(&o); if (!model().loaded) o.mode = SMAT_TUNE_EXHAUSTIVE; }
+  if (o.mode < SMAT_TUNE_LEARNED || o.mode > SMAT_TUNE_FIXED) return SMAT_ERR_INVALID_ARG;
+  if (o.tau_den <= 0 || o.tau_num < 0 || o.fill_ratio_max <= 0) return SMAT_ERR_INVALID_ARG;
+  const double t0 = now_ms();
+  if (!h->have_features || o.tau_num != h->tau_num || o.tau_den != h->tau_den ||
+      o.fill_ratio_max != h->fill_ratio_max) {
+    h->tau_num = o.tau_num; h->tau_den = o.tau_den; h->fill_ratio_max = o.fill_ratio_max;
+    h->bytes_cap = o.bytes_cap > 0 ? o.bytes_cap : 4.0;
+    TRYS(compute_features(h, s));
+  } else if (o.bytes_cap > 0 && o.bytes_cap != h->bytes_cap) {
+    h->bytes_cap = o.bytes_cap;
+    update_admissible(h);
+  }
+  for (auto &t : h->timings) t = -1.0f;
+  const uint32_t allowed = o.allowed ? o.allowed : 0xFFu;
+  const uint32_t ok = h->f.admissible & allowed;
+  if (!ok) return SMAT_ERR_UNSUPPORTED;
+  int v = SMAT_V_CSR_SCALAR;
+  h->confidence = -1.0f;
+  h->trialled = 0;
+  std::vector<int> cands;
+  for (int c : {SMAT_V_DIA, SMAT_V_ELL, SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32,
+                SMAT_V_CSR_MERGE, SMAT_V_COO})
+    if ((ok >> c) & 1u) cands.push_back(c);
+  switch (o.mode) {
+    case SMAT_TUNE_FIXED:
+      if (o.fixed_variant < 0 || o.fixed_variant >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+      if (!((ok >> o.fixed_variant) & 1u)) return SMAT_ERR_UNSUPPORTED;
+      v = o.fixed_variant;
+      break;
+    case SMAT_TUNE_RULES:
+      v = rules_select(h->f, ok);
+      break;
+    case SMAT_TUNE_EXHAUSTIVE:
+      TRYS(trial(h, cands, o, s, &v));
+      h->trialled = 1;
+      break;
+    case SMAT_TUNE_LEARNED: {
+      if (!model().loaded) return SMAT_ERR_MODEL;
+      float p[SMAT_NUM_VARIANTS];
+      TRYS(mlp_probs(h, p, s));
+      int arg = -1;
+      for (int c = 0; c < SMAT_NUM_VARIANTS; ++c)
+        if (((ok >> c) & 1u) && (arg < 0 || p[c] > p[arg])) arg = c;
+      v = arg;
+      h->confidence = p[arg];
+      if (p[arg] < o.conf_threshold) {
+        std::vector<int> top(cands);
+        std::sort(top.begin(), top.end(), [&](int a, int b) { return p[a] > p[b]; });
+        if (o.fallback_topk > 0 && (int)top.size() > o.fallback_topk) top.resize((size_t)o.fallback_topk);
+        TRYS(trial(h, top, o, s, &v));
+        h->trialled = 1;
+      }
+    } break;
+  }
+  TRYS(prepare_variant(h, v, s));
+  if (!o.keep_formats)
+    for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_COO; ++fmt)
+      if (fmt != variant_format(v)) free_format(h, fmt);
+  TRY(cudaStreamSynchronize(s));
+  h->variant = v;
+  h->tune_ms = now_ms() - t0;
+  return SMAT_OK;
+}
+
+smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const void *beta, void *y,
+                        void *stream) {
+  TRYS(check_handle(h));
+  if (!alpha || !beta || (h->m > 0 && !y) || (h->n > 0 && !x)) return SMAT_ERR_INVALID_ARG;
+  if (!variant_ready(h, h->variant)) return SMAT_ERR_UNSUPPORTED;
+  TRY(launch_spmv(h, h->variant, alpha, x, beta, y, (cudaStream_t)stream));
+  return SMAT_OK;
+}
+
+smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *alpha, const void *x,
+                                const void *beta, void *y, void *stream) {
+  TRYS(check_handle(h));
+  if (!alpha || !beta || (h->m > 0 && !y) || (h->n > 0 && !x)) return SMAT_ERR_INVALID_ARG;
+  if ((int)v < 0 || (int)v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  if (!variant_ready(h, v)) {
+    TRYS(prepare_variant(h, v, (cudaStream_t)stream));
+    if (!variant_ready(h, v)) return SMAT_ERR_UNSUPPORTED;
+  }
+  TRY(launch_spmv(h, v, alpha, x, beta, y, (cudaStream_t)stream));
+  return SMAT_OK;
+}
+
+smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
+                             void *y_host, void *stream) {
+  TRYS(check_handle(h));
+  if (!alpha || !beta || (h->m > 0 && !y_host) || (h->n > 0 && !x_host)) return SMAT_ERR_INVALID_ARG;
+  if (!variant_ready(h, h->variant)) return SMAT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ts = (size_t)tsize(h);
+  if (!h->stage_x && h->n > 0) TRY(dev_alloc(&h->stage_x, (size_t)h->n * ts));
+  if (!h->stage_y && h->m > 0) TRY(dev_alloc(&h->stage_y, (size_t)h->m * ts));
+  const bool beta_zero = h->dtype == SMAT_F64 ? *(const double *)beta == 0.0 : *(const float *)beta == 0.0f;
+  if (h->n > 0) TRY(cudaMemcpyAsync(h->stage_x, x_host, (size_t)h->n * ts, cudaMemcpyHostToDevice, s));
+  if (!beta_zero && h->m > 0)
+    TRY(cudaMemcpyAsync(h->stage_y, y_host, (size_t)h->m * ts, cudaMemcpyHostToDevice, s));
+  TRY(launch_spmv(h, h->variant, alpha, h->stage_x, beta, h->stage_y, s));
+  if (h->m > 0) TRY(cudaMemcpyAsync(y_host, h->stage_y, (size_t)h->m * ts, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  return SMAT_OK;
+}
+
+smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out) {
+  TRYS(check_handle(h));
+  if (!out) return SMAT_ERR_INVALID_ARG;
+  if (!h->have_features) TRYS(compute_features(h, 0));
+  *out = h->f;
+  return SMAT_OK;
+}
+
+smat_status_t smat_get_feature_vector(smat_handle_t h, float out[12]) {
+  TRYS(check_handle(h));
+  if (!out) return SMAT_ERR_INVALID_ARG;
+  if (!h->have_features) TRYS(compute_features(h, 0));
+  feature_vector(h->f, out);
+  return SMAT_OK;
+}
+
+smat_status_t smat_get_plan(smat_handle_t h, int32_t *variant, double *tune_ms, float *confidence,
+                            int32_t *trialled) {
+  TRYS(check_handle(h));
+  if (variant) *variant = h->variant;
+  if (tune_ms) *tune_ms = h->tune_ms;
+  if (confidence) *confidence = h->confidence;
+  if (trialled) *trialled = h->trialled;
+  return SMAT_OK;
+}
+
+smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_VARIANTS]) {
+  TRYS(check_handle(h));
+  if (!ms) return SMAT_ERR_INVALID_ARG;
+  for (int v = 0; v < SMAT_NUM_VARIANTS; ++v) ms[v] = h->timings[v];
+  return SMAT_OK;
+}
+
+smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream) {
+  TRYS(check_handle(h));
+  if (fmt < SMAT_FMT_CSR || fmt > SMAT_FMT_COO) return SMAT_ERR_INVALID_ARG;
+  TRYS(build_format(h, fmt, (cudaStream_t)stream));
+  TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return SMAT_OK;
+}
+
+smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[2]) {
+  TRYS(check_handle(h));
+  if (!dims) return SMAT_ERR_INVALID_ARG;
+  switch (fmt) {
+    case SMAT_FMT_ELL: if (!h->ell_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->ell_K; dims[1] = h->P; break;
+    case SMAT_FMT_DIA: if (!h->dia_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->dia_nd; dims[1] = h->P; break;
+    case SMAT_FMT_COO: if (!h->coo_row && h->nnz > 0) return SMAT_ERR_UNSUPPORTED; dims[0] = h->nnz; dims[1] = 0; break;
+    case SMAT_FMT_CSR: dims[0] = h->m; dims[1] = h->nnz; break;
+    default: return SMAT_ERR_INVALID_ARG;
+  }
+  return SMAT_OK;
+}
+
+smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *idx, void *val) {
+  TRYS(check_handle(h));
+  int64_t d[2];
+  TRYS(smat_format_dims(h, fmt, d));
+  switch (fmt) {
+    case SMAT_FMT_ELL:
+      if (!idx || !val) return SMAT_ERR_INVALID_ARG;
+      TRY(cudaMemcpy(idx, h->ell_col, (size_t)(d[0] * d[1]) * 4, cudaMemcpyDefault));
+      TRY(cudaMemcpy(val, h->ell_val, (size_t)(d[0] * d[1]) * h->esz, cudaMemcpyDefault));
+      break;
+    case SMAT_FMT_DIA:
+      if (!idx || !val) return SMAT_ERR_INVALID_ARG;
+      TRY(cudaMemcpy(idx, h->dia_off, (size_t)d[0] * 4, cudaMemcpyDefault));
+      TRY(cudaMemcpy(val, h->dia_val, (size_t)(d[0] * d[1]) * h->esz, cudaMemcpyDefault));
+      break;
+    case SMAT_FMT_COO:
+      if (!idx) return SMAT_ERR_INVALID_ARG;
+      if (h->nnz > 0) TRY(cudaMemcpy(idx, h->coo_row, (size_t)h->nnz * 4, cudaMemcpyDefault));
+      break;
+    default:
+      return SMAT_ERR_INVALID_ARG;
+  }
+  return SMAT_OK;
+}
+
+smat_status_t smat_set_model(const float *params, const float *mean, const float *stdv) {
+  Model &M = model();
+  if (!params) {
+    M.loaded = false;
+    return SMAT_OK;
+  }
+  if (!mean || !stdv) return SMAT_ERR_INVALID_ARG;
+  std::memcpy(M.params, params, sizeof(M.params));
+  std::memcpy(M.mean, mean, sizeof(M.mean));
+  std::memcpy(M.stdv, stdv, sizeof(M.stdv));
+  M.loaded = true;
+  return SMAT_OK;
+}
+
+smat_status_t smat_load_model(const char *path) {
+  if (!path) return SMAT_ERR_INVALID_ARG;
+  FILE *fp = std::fopen(path, "rb");
+  if (!fp) return SMAT_ERR_MODEL;
+  char magic[8];
+  int32_t ver = 0;
+  std::vector<float> buf(12 + 12 + SMAT_MLP_PARAMS);
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "SMATMLP1", 8) == 0 &&
+            std::fread(&ver, 4, 1, fp) == 1 && ver == 1 &&
+            std::fread(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+  std::fclose(fp);
+  if (!ok) return SMAT_ERR_MODEL;
+  for (float v : buf)
+    if (!std::isfinite(v)) return SMAT_ERR_MODEL;
+  return smat_set_model(buf.data() + 24, buf.data(), buf.data() + 12);
+}
+
+}  // extern "C"

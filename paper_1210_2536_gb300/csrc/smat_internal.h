@@ -1,0 +1,125 @@
+// Internal declarations shared by the libsmat translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "smat.h"
+
+namespace smat {
+
+// Storage element size per dtype.
+inline int elem_size(smat_dtype_t t) { return t == SMAT_F64 ? 8 : (t == SMAT_F32 ? 4 : 2); }
+inline int64_t pitch_of(int64_t m) { return (m + 31) / 32 * 32; }
+
+// Device allocation with a host-side failure hook: SMAT_TEST_FAIL_ALLOC_AFTER=k
+// makes the k-th allocation of the process (1-based) fail, for error-path tests.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+
+// Device-side error flags set by validation kernels (never trap).
+enum : int {
+  ERRF_ROWPTR = 1,     // rowptr[0] != 0, rowptr[m] != nnz or decreasing
+  ERRF_COL_RANGE = 2,  // column outside [0, n)
+  ERRF_COL_ORDER = 4,  // columns not strictly increasing in a row
+};
+
+// Integer statistics of the row degrees (one pass over rowptr).
+struct RowStats {
+  unsigned long long s2;  // sum of rd^2
+  int max_rd;
+  int min_rd;
+  int empty_rows;
+  int pad;
+};
+
+// Selector model (process-wide).
+struct Model {
+  bool loaded = false;
+  float mean[12], stdv[12];
+  float params[SMAT_MLP_PARAMS];
+};
+Model &model();
+
+}  // namespace smat
+
+// The handle.
+struct smat_s {
+  int64_t m = 0, n = 0, nnz = 0;
+  smat_dtype_t dtype = SMAT_F64;
+  int esz = 8;
+  int64_t P = 0;  // pitch of ELL / DIA arrays
+
+  // CSR (always present)
+  int32_t *rowptr = nullptr, *colidx = nullptr;
+  void *val = nullptr;
+
+  // features
+  bool have_features = false;
+  smat_features_t f{};
+  std::vector<int64_t> hist;         // row-degree histogram
+  std::vector<int32_t> dia_offsets;  // occupied diagonals, ascending (when counted)
+  bool dia_offsets_complete = false;
+  int32_t tau_num = 3, tau_den = 5;
+  int32_t fill_ratio_max = 20;
+  double bytes_cap = 4.0;
+
+  // ELL
+  int64_t ell_K = 0;
+  int32_t *ell_col = nullptr;
+  void *ell_val = nullptr;
+  // DIA
+  int64_t dia_nd = 0;
+  int32_t *dia_off = nullptr;
+  void *dia_val = nullptr;
+  // COO
+  int32_t *coo_row = nullptr;
+  int32_t *coo_empty = nullptr;  // list of empty rows (y = beta*y there)
+  int64_t coo_nempty = 0;
+
+  // scratch for merge-path and COO carries
+  void *carry = nullptr;
+  size_t carry_bytes = 0;
+
+  // host-buffer staging for smat_spmv_host
+  void *stage_x = nullptr, *stage_y = nullptr;
+
+  // plan
+  int32_t variant = SMAT_V_CSR_SCALAR;
+  double tune_ms = 0.0;
+  float confidence = -1.0f;
+  int32_t trialled = 0;
+  float timings[SMAT_NUM_VARIANTS];
+};
+
+namespace smat {
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_validate(const smat_s *h, int *d_flag, cudaStream_t s);
+cudaError_t launch_row_stats(const int32_t *rowptr, int64_t m, RowStats *d_stats, cudaStream_t s);
+cudaError_t launch_hist_diag(const int32_t *rowptr, const int32_t *colidx, int64_t m,
+                             int *d_hist, int64_t hist_len, int *d_diag_cnt, cudaStream_t s);
+cudaError_t launch_diag_reduce(const int *d_diag_cnt, int64_t m, int64_t n, int tau_num,
+                               int tau_den, unsigned long long *d_counts, int32_t *d_offsets,
+                               int64_t offsets_cap, cudaStream_t s);
+
+cudaError_t launch_to_coo(const smat_s *h, int32_t *row, cudaStream_t s);
+cudaError_t launch_empty_rows(const smat_s *h, int32_t *list, int *d_count, cudaStream_t s);
+cudaError_t launch_to_ell(const smat_s *h, int64_t K, int32_t *col, void *val, cudaStream_t s);
+cudaError_t launch_to_dia(const smat_s *h, const int32_t *d_off, int64_t nd, void *val,
+                          cudaStream_t s);
+
+// Size in bytes of the carry scratch a variant needs (0 if none).
+size_t carry_bytes_needed(const smat_s *h, int variant);
+// SpMV through one variant; alpha/beta are host scalars of the compute type.
+cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,
+                        const void *beta, void *y, cudaStream_t s);
+
+// MLP forward over standardised inputs (device), used by the selector.
+cudaError_t launch_mlp_forward(const float *params, const float *X, int B, float *logits,
+                               cudaStream_t s);
+
+}  // namespace smat

@@ -1,0 +1,528 @@
+// SpMV kernels y = alpha*A*x + beta*y for the four basic formats
+// (arXiv 1210.2536, Sec. 2.1; the paper's kernel library maps each format to
+// its best implementation, Sec. 3).  GPU implementations of CSR follow Bell &
+// Garland (2008, cited by the paper: scalar and vector kernels) and Merrill &
+// Garland (2016: merge-path); COO uses a tiled segmented reduction.
+//
+// All kernels are bound by HBM bandwidth: they stream the format's index and
+// value arrays once with coalesced (ELL, DIA: 16-byte vector) loads, gather x
+// through L1/L2, and write y once.  The alpha/beta epilogue is fused:
+//   y_i = alpha*acc            if beta == 0 (y is not read)
+//   y_i = alpha*acc + beta*y_i otherwise, each product rounded separately.
+// Storage V in {double, float, bf16}; compute T = double for V = double,
+// float otherwise.  For V = double the CSR-scalar, ELL and DIA kernels add
+// products one at a time in ascending column order with separately rounded
+// multiply and add, i.e. the same operations as the CSR definition.
+#include <cuda_bf16.h>
+
+#include "smat_internal.h"
+
+namespace smat {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename V> struct Compute { typedef float T; };
+template <> struct Compute<double> { typedef double T; };
+
+__device__ __forceinline__ double ld_val(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_val(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// acc + v*x: separately rounded for FP64 storage (matches the CSR definition
+// operation for operation), fused multiply-add for FP32 accumulation.
+__device__ __forceinline__ double madd(double acc, double v, double x) { return __dadd_rn(acc, __dmul_rn(v, x)); }
+__device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf(v, x, acc); }
+
+// acc + v*x with one rounding (kernels that reorder the sum anyway).
+__device__ __forceinline__ double fused(double acc, double v, double x) { return fma(v, x, acc); }
+__device__ __forceinline__ float fused(float acc, float v, float x) { return fmaf(v, x, acc); }
+
+template <typename T>
+__device__ __forceinline__ T epilogue(T acc, T alpha, T beta, const T *y, long long i) {
+  T ax = mul_rn(alpha, acc);
+  if (beta == (T)0) return ax;
+  return add_rn(ax, mul_rn(beta, y[i]));
+}
+
+// ---------------------------------------------------------------------------
+// K7: CSR-scalar, one thread per row.
+// ---------------------------------------------------------------------------
+template <typename V, typename T>
+__global__ void __launch_bounds__(256) csr_scalar_kernel(const int32_t *__restrict__ rowptr,
+                                                         const int32_t *__restrict__ col,
+                                                         const V *__restrict__ val, const T *__restrict__ x,
+                                                         T alpha, T beta, T *__restrict__ y, long long m) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    int s = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+    T acc = 0;
+    for (int k = s; k < e; ++k) acc = madd(acc, (T)ld_val(val + k), __ldg(x + __ldg(col + k)));
+    y[i] = epilogue(acc, alpha, beta, y, i);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K8: CSR-vector, W lanes per row, lane-strided loads, shuffle reduction.
+// ---------------------------------------------------------------------------
+template <typename V, typename T, int W>
+__global__ void __launch_bounds__(256) csr_vector_kernel(const int32_t *__restrict__ rowptr,
+                                                         const int32_t *__restrict__ col,
+                                                         const V *__restrict__ val, const T *__restrict__ x,
+                                                         T alpha, T beta, T *__restrict__ y, long long m) {
+  constexpr int RPW = 32 / W;  // rows per warp per step
+  const int lane = threadIdx.x & 31, sub = lane % W;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r0 = warp * RPW; r0 < m; r0 += nwarps * RPW) {
+    long long row = r0 + lane / W;
+    T acc = 0;
+    if (row < m) {
+      int s = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+#pragma unroll 4
+      for (int k = s + sub; k < e; k += W) acc = fused(acc, (T)ld_val(val + k), __ldg(x + __ldg(col + k)));
+    }
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o, W);
+    if (sub == 0 && row < m) y[row] = epilogue(acc, alpha, beta, y, row);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled segmented reduction shared by merge-path CSR (K9) and COO (K12).
+// A CTA consumes a tile of NT*IPT items; each thread walks IPT consecutive
+// items, finishing the rows whose last nonzero it sees.  Partial sums that
+// cross thread boundaries are combined by a deterministic block-wide
+// segmented scan; the partial sum of the row still open at the end of the
+// tile is written to a per-tile carry and added by a fix-up kernel.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct SegPair {
+  int h;  // this range finished at least one row
+  T v;    // partial sum of the row open at the end of the range
+};
+
+template <typename T>
+__device__ __forceinline__ SegPair<T> seg_combine(SegPair<T> a, SegPair<T> b) {
+  SegPair<T> r;
+  r.h = a.h | b.h;
+  r.v = b.h ? b.v : a.v + b.v;
+  return r;
+}
+
+// Exclusive block scan of (h, v) pairs in thread order.  Returns the exclusive
+// prefix for this thread and writes the block total to *total.
+template <typename T, int NT>
+__device__ __forceinline__ SegPair<T> block_seg_scan(SegPair<T> x, SegPair<T> *total) {
+  __shared__ int sh_h[NT / 32];
+  __shared__ T sh_v[NT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  SegPair<T> inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int ph = __shfl_up_sync(FULL, inc.h, o);
+    T pv = __shfl_up_sync(FULL, inc.v, o);
+    if (lane >= o) {
+      SegPair<T> p{ph, pv};
+      inc = seg_combine(p, inc);
+    }
+  }
+  SegPair<T> exc;
+  exc.h = __shfl_up_sync(FULL, inc.h, 1);
+  exc.v = __shfl_up_sync(FULL, inc.v, 1);
+  if (lane == 0) { exc.h = 0; exc.v = (T)0; }
+  if (lane == 31) { sh_h[w] = inc.h; sh_v[w] = inc.v; }
+  __syncthreads();
+  if (w == 0) {
+    SegPair<T> wv;
+    wv.h = lane < NT / 32 ? sh_h[lane] : 0;
+    wv.v = lane < NT / 32 ? sh_v[lane] : (T)0;
+    SegPair<T> wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int ph = __shfl_up_sync(FULL, wi.h, o);
+      T pv = __shfl_up_sync(FULL, wi.v, o);
+      if (lane >= o) {
+        SegPair<T> p{ph, pv};
+        wi = seg_combine(p, wi);
+      }
+    }
+    // exclusive prefix of warp totals
+    int eh = __shfl_up_sync(FULL, wi.h, 1);
+    T ev = __shfl_up_sync(FULL, wi.v, 1);
+    if (lane == 0) { eh = 0; ev = (T)0; }
+    if (lane < NT / 32) { sh_h[lane] = eh; sh_v[lane] = ev; }
+    if (lane == NT / 32 - 1) { total->h = wi.h; total->v = wi.v; }
+  }
+  __syncthreads();
+  SegPair<T> wp{sh_h[w], sh_v[w]};
+  return seg_combine(wp, exc);
+}
+
+// Merge-path coordinate: number of row ends a among the first d merge items
+// of (rowptr[1..m]) and (0..nnz-1), row ends first on ties.
+__device__ __forceinline__ void merge_search(const int32_t *__restrict__ rowptr, long long m, long long nnz,
+                                             long long d, long long *a, long long *b) {
+  long long lo = d - nnz > 0 ? d - nnz : 0, hi = d < m ? d : m;
+  while (lo < hi) {
+    long long mid = (lo + hi) >> 1;
+    if ((long long)__ldg(rowptr + mid + 1) <= d - mid - 1) lo = mid + 1; else hi = mid;
+  }
+  *a = lo;
+  *b = d - lo;
+}
+
+template <typename V, typename T, int NT, int IPT>
+__global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ col,
+                                                       const V *__restrict__ val, const T *__restrict__ x,
+                                                       T alpha, T beta, T *__restrict__ y, long long m,
+                                                       long long nnz, int32_t *carry_row, T *carry_val) {
+  constexpr int TILE = NT * IPT;
+  __shared__ int32_t s_rowend[TILE + 1];
+  __shared__ T s_prod[TILE];
+  __shared__ long long s_coord[4];
+  __shared__ SegPair<T> s_total;
+  const long long total = m + nnz;
+  const long long d0 = (long long)blockIdx.x * TILE;
+  const long long d1 = d0 + TILE < total ? d0 + TILE : total;
+  if (threadIdx.x < 2) {
+    long long a, b;
+    merge_search(rowptr, m, nnz, threadIdx.x == 0 ? d0 : d1, &a, &b);
+    s_coord[2 * threadIdx.x] = a;
+    s_coord[2 * threadIdx.x + 1] = b;
+  }
+  __syncthreads();
+  const long long a0 = s_coord[0], b0 = s_coord[1], a1 = s_coord[2], b1 = s_coord[3];
+  const int nrows = (int)(a1 - a0), nnzs = (int)(b1 - b0);
+  for (int i = threadIdx.x; i < nrows; i += NT) s_rowend[i] = __ldg(rowptr + a0 + 1 + i);
+  for (int j = threadIdx.x; j < nnzs; j += NT) {
+    long long k = b0 + j;
+    s_prod[j] = mul_rn((T)ld_val(val + k), __ldg(x + __ldg(col + k)));
+  }
+  __syncthreads();
+  // this thread's start on the tile's merge path
+  const int items = (int)(d1 - d0);
+  const int dt = min((int)threadIdx.x * IPT, items);
+  int lo = dt - nnzs > 0 ? dt - nnzs : 0, hi = dt < nrows ? dt : nrows;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((long long)s_rowend[mid] <= b0 + (dt - mid - 1)) lo = mid + 1; else hi = mid;
+  }
+  int a = lo;
+  long long b = b0 + (dt - lo);
+  const int dend = min(dt + IPT, items);
+  T acc = 0, first_acc = 0;
+  int first_row = -1;
+  for (int it = dt; it < dend; ++it) {
+    if (a < nrows && (long long)s_rowend[a] <= b) {
+      if (first_row < 0) {
+        first_row = a;
+        first_acc = acc;
+      } else {
+        long long r = a0 + a;
+        y[r] = epilogue(acc, alpha, beta, y, r);
+      }
+      acc = 0;
+      ++a;
+    } else {
+      acc = add_rn(acc, s_prod[b - b0]);
+      ++b;
+    }
+  }
+  SegPair<T> mine{first_row >= 0 ? 1 : 0, acc};
+  SegPair<T> incoming = block_seg_scan<T, NT>(mine, &s_total);
+  if (first_row >= 0) {
+    long long r = a0 + first_row;
+    y[r] = epilogue(add_rn(incoming.v, first_acc), alpha, beta, y, r);
+  }
+  if (threadIdx.x == 0) {
+    bool open = a1 < m && b1 > b0;
+    carry_row[blockIdx.x] = open ? (int32_t)a1 : -1;
+    carry_val[blockIdx.x] = open ? s_total.v : (T)0;
+  }
+}
+
+template <typename V, typename T, int NT, int IPT>
+__global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row,
+                                                 const int32_t *__restrict__ col,
+                                                 const V *__restrict__ val, const T *__restrict__ x,
+                                                 T alpha, T beta, T *__restrict__ y, long long nnz,
+                                                 int32_t *carry_row, T *carry_val) {
+  constexpr int TILE = NT * IPT;
+  __shared__ int32_t s_row[TILE + 1];
+  __shared__ T s_prod[TILE];
+  __shared__ SegPair<T> s_total;
+  const long long b0 = (long long)blockIdx.x * TILE;
+  const int cnt = (int)(nnz - b0 < TILE ? nnz - b0 : TILE);
+  for (int j = threadIdx.x; j < cnt; j += NT) {
+    long long k = b0 + j;
+    s_row[j] = __ldg(row + k);
+    s_prod[j] = mul_rn((T)ld_val(val + k), __ldg(x + __ldg(col + k)));
+  }
+  if (threadIdx.x == 0) s_row[cnt] = (b0 + cnt < nnz) ? __ldg(row + b0 + cnt) : -1;
+  __syncthreads();
+  const int j0 = min((int)threadIdx.x * IPT, cnt), j1 = min(j0 + IPT, cnt);
+  T acc = 0, first_acc = 0;
+  int first_row = -1;
+  for (int j = j0; j < j1; ++j) {
+    acc = add_rn(acc, s_prod[j]);
+    int r = s_row[j];
+    if (s_row[j + 1] != r) {  // last stored entry of row r
+      if (first_row < 0) {
+        first_row = r;
+        first_acc = acc;
+      } else {
+        y[r] = epilogue(acc, alpha, beta, y, (long long)r);
+      }
+      acc = 0;
+    }
+  }
+  SegPair<T> mine{first_row >= 0 ? 1 : 0, acc};
+  SegPair<T> incoming = block_seg_scan<T, NT>(mine, &s_total);
+  if (first_row >= 0) y[first_row] = epilogue(add_rn(incoming.v, first_acc), alpha, beta, y, (long long)first_row);
+  if (threadIdx.x == 0) {
+    bool open = cnt > 0 && s_row[cnt] == s_row[cnt - 1];
+    carry_row[blockIdx.x] = open ? s_row[cnt - 1] : -1;
+    carry_val[blockIdx.x] = open ? s_total.v : (T)0;
+  }
+}
+
+// Fix-up: y[r] += alpha * (sum of the carries of row r), runs of equal rows
+// summed in tile order by the run's first entry.
+template <typename T>
+__global__ void carry_fixup_kernel(const int32_t *__restrict__ carry_row, const T *__restrict__ carry_val,
+                                   long long ntiles, T alpha, T *__restrict__ y) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ntiles;
+       c += (long long)gridDim.x * blockDim.x) {
+    int r = carry_row[c];
+    if (r < 0 || (c > 0 && carry_row[c - 1] == r)) continue;
+    T s = carry_val[c];
+    for (long long q = c + 1; q < ntiles && carry_row[q] == r; ++q) s = add_rn(s, carry_val[q]);
+    y[r] = add_rn(y[r], mul_rn(alpha, s));
+  }
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long count, T beta, T *__restrict__ y) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < count;
+       c += (long long)gridDim.x * blockDim.x) {
+    int r = rows[c];
+    y[r] = beta == (T)0 ? (T)0 : mul_rn(beta, y[r]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K10: ELL, column-major, R consecutive rows per thread so that every slot is
+// one 16-byte load of values (and 4R bytes of columns).
+// ---------------------------------------------------------------------------
+template <typename V, int R> struct VecOf;
+template <> struct VecOf<double, 2> { typedef double2 T; };
+template <> struct VecOf<float, 4> { typedef float4 T; };
+template <> struct VecOf<__nv_bfloat16, 8> { typedef uint4 T; };
+
+template <typename V, int R>
+__device__ __forceinline__ void load_vals(const V *p, typename Compute<V>::T (&out)[R]);
+template <>
+__device__ __forceinline__ void load_vals<double, 2>(const double *p, double (&out)[2]) {
+  double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  out[0] = v.x; out[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load_vals<float, 4>(const float *p, float (&out)[4]) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_vals<__nv_bfloat16, 8>(const __nv_bfloat16 *p, float (&out)[8]) {
+  uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+  unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    out[2 * q] = __uint_as_float(w[q] << 16);
+    out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_cols(const int32_t *p, int (&c)[R]) {
+  if constexpr (R == 2) {
+    int2 v = __ldg(reinterpret_cast<const int2 *>(p));
+    c[0] = v.x; c[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      int4 v = __ldg(reinterpret_cast<const int4 *>(p) + q);
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+  }
+}
+
+template <typename V, int R>
+__global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
+                                                  long long P, long long K,
+                                                  const typename Compute<V>::T *__restrict__ x,
+                                                  typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                                  typename Compute<V>::T *__restrict__ y, long long m) {
+  typedef typename Compute<V>::T T;
+  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
+  if (i0 >= m) return;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 4
+  for (long long q = 0; q < K; ++q) {
+    T v[R];
+    int c[R];
+    load_vals<V, R>(eval + q * P + i0, v);
+    load_cols<R>(ecol + q * P + i0, c);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (c[r] >= 0) acc[r] = madd(acc[r], v[r], __ldg(x + c[r]));
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+}
+
+// ---------------------------------------------------------------------------
+// K11: DIA, diagonal-major, R consecutive rows per thread, offsets staged in
+// shared memory.  Fill zeros are multiplied like stored values (Table
+// "Performance features of the four formats": extra computation decided by
+// zero filling).
+// ---------------------------------------------------------------------------
+template <typename V, int R>
+__global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ off, int nd,
+                                                  const V *__restrict__ dval, long long P,
+                                                  const typename Compute<V>::T *__restrict__ x,
+                                                  typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                                  typename Compute<V>::T *__restrict__ y, long long m,
+                                                  long long n) {
+  typedef typename Compute<V>::T T;
+  extern __shared__ int32_t s_off[];
+  for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
+  __syncthreads();
+  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
+  if (i0 >= m) return;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+#pragma unroll 4
+  for (int t = 0; t < nd; ++t) {
+    const long long o = s_off[t];
+    T v[R];
+    load_vals<V, R>(dval + (long long)t * P + i0, v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      long long j = i0 + r + o;
+      if (j >= 0 && j < n) acc[r] = madd(acc[r], v[r], __ldg(x + j));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+}
+
+int grid_for(long long work, int block, int max_blocks) {
+  long long g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+constexpr int MERGE_NT = 256, MERGE_IPT = 8;
+constexpr int COO_NT = 256, COO_IPT = 8;
+
+template <typename V>
+cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p,
+                       const void *beta_p, void *y_p, cudaStream_t s) {
+  typedef typename Compute<V>::T T;
+  const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
+  const T *x = (const T *)x_p;
+  T *y = (T *)y_p;
+  const V *val = (const V *)h->val;
+  const long long m = h->m;
+  if (m == 0) return cudaSuccess;
+  switch (variant) {
+    case SMAT_V_CSR_SCALAR:
+      csr_scalar_kernel<V, T><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      break;
+    case SMAT_V_CSR_VEC4:
+      csr_vector_kernel<V, T, 4><<<grid_for(m * 4, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      break;
+    case SMAT_V_CSR_VEC8:
+      csr_vector_kernel<V, T, 8><<<grid_for(m * 8, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      break;
+    case SMAT_V_CSR_VEC32:
+      csr_vector_kernel<V, T, 32><<<grid_for(m * 32, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      break;
+    case SMAT_V_CSR_MERGE: {
+      long long tiles = (m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+      int32_t *crow = (int32_t *)h->carry;
+      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+      csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
+          h->rowptr, h->colidx, val, x, alpha, beta, y, m, h->nnz, crow, cval);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (tiles > 1)
+        carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, y);
+    } break;
+    case SMAT_V_ELL: {
+      constexpr int R = 16 / (int)sizeof(V);
+      ell_kernel<V, R><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
+          h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, alpha, beta, y, m);
+    } break;
+    case SMAT_V_DIA: {
+      constexpr int R = 16 / (int)sizeof(V);
+      dia_kernel<V, R><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
+          h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, alpha, beta, y, m, h->n);
+    } break;
+    case SMAT_V_COO: {
+      if (h->coo_nempty > 0) {
+        scale_rows_kernel<T><<<grid_for(h->coo_nempty, 256, 152 * 8), 256, 0, s>>>(h->coo_empty, h->coo_nempty, beta, y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      if (h->nnz == 0) break;
+      long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+      int32_t *crow = (int32_t *)h->carry;
+      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+      coo_kernel<V, T, COO_NT, COO_IPT><<<(unsigned)tiles, COO_NT, 0, s>>>(
+          h->coo_row, h->colidx, val, x, alpha, beta, y, h->nnz, crow, cval);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (tiles > 1)
+        carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, y);
+    } break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t carry_bytes_needed(const smat_s *h, int variant) {
+  long long tiles = 0;
+  if (variant == SMAT_V_CSR_MERGE) tiles = (h->m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+  else if (variant == SMAT_V_COO) tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  else return 0;
+  size_t tsz = h->dtype == SMAT_F64 ? 8 : 4;
+  return (size_t)((tiles * 4 + 15) / 16) * 16 + (size_t)tiles * tsz;
+}
+
+cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
+                        void *y, cudaStream_t s) {
+  switch (h->dtype) {
+    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s);
+    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s);
+    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s);
+  }
+}
+
+}  // namespace smat
