@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""SpMV benchmark: GFLOP/s and HBM % of peak of the tuned pick vs plain CSR.
+
+Workload (the paper's structure classes at full size, synthetic, seeded):
+3-D 7-point Laplacian 128^3; uniform random n = 1e6 with Poisson(16) rows;
+power-law n = 2e6 with Zipf(1.8) rows capped at 1e4; 8x8 block diagonal
+n = 1e6.  Each matrix is stored in FP64 and in FP32 (FP32 accumulation), so a
+step is eight products y = A x through each handle's tuned plan.  Tuning
+(feature extraction, selection, conversion) happens once per handle before the
+timed region and is reported as overhead in units of one CSR-scalar product.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GFLOP/s, HBM % of peak: tuned/learned pick vs plain CSR at stated error"
+UNIT = "GFLOP/s"
+WORKLOAD = "structures_suite: stencil3d7 128^3, uniform 1e6 Poisson(16), powerlaw 2e6 Zipf(1.8) cap 1e4, " \
+           "blockdiag 1e6 b=8; FP64 and FP32 storage"
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=float, default=1.0, help="row-count scale of the workload (1 = full size)")
+    p.add_argument("--select", default="auto", choices=["auto", "learned", "exhaustive", "rules"])
+    p.add_argument("--dtypes", default="f64,f32")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--e2e-steps", type=int, default=100)
+    return p.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(scale):
+    from paper_1210_2536_gb300 import synth
+    mats = synth.structures_suite(scale)
+    xs = [synth.uniform(0, 1, A.n) for A in mats]
+    return mats, xs
+
+
+def stored(A, dtype):
+    if dtype == "f64":
+        return A.val, A.val
+    v = A.val.astype(np.float32)
+    return v, v.astype(np.float64)
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "100"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def dram_traffic_record(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_1210_2536_gb300", "csrc", "spmv.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel_key and cells[3] == h:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+def cpu_baseline(mats, xs, dtypes, seconds):
+    """The oracle (threaded, nonzero-balanced rows, FP64 accumulation) timed
+    on this host's cores over passes of the same products."""
+    import oracle
+    threads = os.cpu_count() or 1
+    prods = []
+    for A, x in zip(mats, xs):
+        for dt in dtypes:
+            _, v64 = stored(A, dt)
+            xx = x if dt == "f64" else x.astype(np.float32).astype(np.float64)
+            prods.append((A, np.ascontiguousarray(v64), np.ascontiguousarray(xx), np.zeros(A.m)))
+    flops = sum(2.0 * A.nnz for A, _, _, _ in prods)
+    t0 = time.perf_counter()
+    passes = 0
+    while True:
+        for A, v, x, y in prods:
+            oracle.spmv_csr_rows(A.rowptr, A.colidx, v, x, 0, A.m, 1.0, 0.0, y, threads)
+        passes += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(flops * passes / dt / 1e9, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{passes} full passes over the {len(prods)} products (all rows), FP64 accumulation, "
+                      f"{threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    dtypes = args.dtypes.split(",")
+    mats, xs = workload(args.scale)
+    threads = os.cpu_count() or 1
+    prods = []
+    for A, x in zip(mats, xs):
+        for dt in dtypes:
+            _, v64 = stored(A, dt)
+            xx = x if dt == "f64" else x.astype(np.float32).astype(np.float64)
+            prods.append([A, np.ascontiguousarray(v64), np.ascontiguousarray(xx), np.zeros(A.m), 0])
+    # each step: the same fraction of every product's rows, sized so that the
+    # whole run stays within about two minutes
+    budget_s = 120.0 / max(1, args.steps + args.warmup)
+    t0 = time.perf_counter()
+    for A, v, x, y, _ in prods:
+        r1 = max(1, A.m // 64)
+        oracle.spmv_csr_rows(A.rowptr, A.colidx, v, x, 0, r1, 1.0, 0.0, y, threads)
+    probe = time.perf_counter() - t0
+    frac = min(1.0, max(1e-6, budget_s / max(probe * 64, 1e-9)))
+
+    def step():
+        flops = 0.0
+        for p in prods:
+            A, v, x, y, off = p
+            rows = max(1, int(A.m * frac))
+            r0 = off if off + rows <= A.m else 0
+            oracle.spmv_csr_rows(A.rowptr, A.colidx, v, x, r0, r0 + rows, 1.0, 0.0, y, threads)
+            flops += 2.0 * (int(A.rowptr[r0 + rows]) - int(A.rowptr[r0]))
+            p[4] = (r0 + rows) % A.m
+        return flops
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    total = 0.0
+    for _ in range(args.steps):
+        total += step()
+    dt = time.perf_counter() - t0
+    value = total / dt / 1e9
+    sample = f"{frac * 100:.3g}% of each product's rows per step ({len(prods)} products), {threads} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(1, args.steps), 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "scale": args.scale},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1210_2536_gb300 as smat
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dtypes = args.dtypes.split(",")
+    mats, xs = workload(args.scale)
+
+    select = args.select
+    model_path = os.path.join(ROOT, "paper_1210_2536_gb300", "selector_mlp.bin")
+    if select == "auto":
+        select = "learned" if os.path.exists(model_path) else "exhaustive"
+    if select == "learned":
+        if smat.smat_load_model(model_path) != 0:
+            raise RuntimeError("selector model did not load")
+
+    prods = []
+    for A, x in zip(mats, xs):
+        for dt in dtypes:
+            vals, v64 = stored(A, dt)
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            t0 = time.perf_counter()
+            M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                              torch.from_numpy(np.ascontiguousarray(vals)).to(dev), dt)
+            torch.cuda.synchronize()
+            create_ms = (time.perf_counter() - t0) * 1e3
+            M.tune(select, keep_formats=0)
+            plan = M.plan()
+            xd = torch.from_numpy(x).to(dev).to(tdt)
+            yd = torch.zeros(A.m, dtype=tdt, device=dev)
+            prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
+                              f=M.features(), launches=M.launches()))
+
+    # parity of every tuned product against the oracle (outside the timed region)
+    import oracle
+    worst = {}
+    for p in prods:
+        A = p["A"]
+        p["M"].spmv(p["x"], p["y"])
+        torch.cuda.synchronize()
+        x64 = p["x"].double().cpu().numpy()
+        ref = oracle.spmv_csr(A.m, A.rowptr, A.colidx, p["v64"], x64, threads=os.cpu_count() or 1)
+        scale = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(p["v64"]), np.abs(x64),
+                                threads=os.cpu_count() or 1)
+        err = np.abs(p["y"].double().cpu().numpy() - ref) / np.maximum(scale, 1e-300)
+        p["max_err"] = float(err.max()) if A.m else 0.0
+        worst[p["dt"]] = max(worst.get(p["dt"], 0.0), p["max_err"])
+    parity_ok = all(worst[d] <= TOL[d] for d in worst)
+
+    # plain CSR-scalar and tuned pick, each timed alone (median of 20)
+    def time_variant(p, v, reps=20):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for _ in range(3):
+            p["M"].spmv(p["x"], p["y"], variant=v)
+        for s, e in ev:
+            s.record()
+            p["M"].spmv(p["x"], p["y"], variant=v)
+            e.record()
+        torch.cuda.synchronize()
+        return statistics.median(s.elapsed_time(e) for s, e in ev)
+
+    for p in prods:
+        p["csr_ms"] = time_variant(p, smat.SMAT_V_CSR_SCALAR)
+        p["pick_ms"] = time_variant(p, p["plan"]["variant"])
+
+    # ---- timed region: K steps of all products through their plans ----
+    K, W = args.steps, args.warmup
+    stride = max(1, K // 200)
+    sampled = list(range(0, K, stride))
+    kev = {i: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in prods] for i in sampled}
+    for _ in range(W):
+        for p in prods:
+            p["M"].spmv(p["x"], p["y"])
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = Clocks(vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device()))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    t_start.record()
+    for k in range(K):
+        evs = kev.get(k)
+        for j, p in enumerate(prods):
+            if evs:
+                evs[j][0].record()
+            p["M"].spmv(p["x"], p["y"])
+            if evs:
+                evs[j][1].record()
+    t_end.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops_step = sum(2.0 * p["A"].nnz for p in prods)
+    value = world * flops_step * K / (ms / 1e3) / 1e9
+    launches_per_step = sum(p["launches"] for p in prods)
+
+    peak, peak_kind = measured_peak()
+    per = []
+    for j, p in enumerate(prods):
+        d = statistics.mean(kev[i][j][0].elapsed_time(kev[i][j][1]) for i in sampled)
+        byts = algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"])
+        csr_bytes = algorithmic_bytes(p["f"], smat.SMAT_V_CSR_SCALAR, p["dt"])
+        per.append({"matrix": p["A"].name, "dtype": p["dt"], "nnz": p["A"].nnz, "variant": p["plan"]["name"],
+                    "confidence": round(p["plan"]["confidence"], 3), "trialled": p["plan"]["trialled"],
+                    "ms_in_step": round(d, 5), "gflops": round(2 * p["A"].nnz / d / 1e6, 2),
+                    "hbm_frac": round(byts / (d / 1e3) / 1e9 / peak, 4),
+                    "pick_ms_alone": round(p["pick_ms"], 5), "csr_scalar_ms_alone": round(p["csr_ms"], 5),
+                    "csr_scalar_gflops": round(2 * p["A"].nnz / p["csr_ms"] / 1e6, 2),
+                    "csr_scalar_hbm_frac": round(csr_bytes / (p["csr_ms"] / 1e3) / 1e9 / peak, 4),
+                    "speedup_vs_csr_scalar": round(p["csr_ms"] / p["pick_ms"], 3),
+                    "tune_ms": round(p["plan"]["tune_ms"], 2),
+                    "tune_overhead_csr_spmvs": round(p["plan"]["tune_ms"] / p["csr_ms"], 1),
+                    "break_even_calls": (round(p["plan"]["tune_ms"] / (p["csr_ms"] - p["pick_ms"]), 1)
+                                         if p["csr_ms"] > p["pick_ms"] else None),
+                    "max_err_normalized": p["max_err"], "alg_bytes": byts, "_d": d})
+    dom = max(per, key=lambda r: r["_d"])
+    dom_key = f"{dom['variant']}:{dom['dtype']}:{dom['matrix']}"
+    dom_bytes = dom["alg_bytes"]
+    achieved = dom_bytes / (dom["_d"] / 1e3) / 1e9
+    traffic = dram_traffic_record(dom_key)
+    for r in per:
+        r.pop("_d")
+        r.pop("alg_bytes")
+
+    # ---- end to end through the C ABI with host buffers ----
+    pinned = []
+    for p in prods:
+        xh = p["x"].cpu().pin_memory()
+        yh = torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory()
+        pinned.append((xh, yh))
+    h2d = sum(xh.numel() * xh.element_size() for xh, _ in pinned)
+    d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
+    for p, (xh, yh) in zip(prods, pinned):
+        p["M"].spmv_host(xh, yh)
+    E = max(1, args.e2e_steps)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        for p, (xh, yh) in zip(prods, pinned):
+            p["M"].spmv_host(xh, yh)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * flops_step * E / e2e_s / 1e9
+
+    if rank == 0:
+        cpu = cpu_baseline(mats, xs, dtypes, args.cpu_seconds) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "+".join(dtypes), "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scale": args.scale, "selector": select,
+                       "l2": "inputs larger than L2: the step streams "
+                             f"{sum(algorithmic_bytes(p['f'], p['plan']['variant'], p['dt']) for p in prods) / 1e6:.0f}"
+                             " MB and each matrix is evicted by the other products between its launches",
+                       "parallelism": f"replicas x{world}"},
+            "parity": {"ok": parity_ok, "max_err_normalized": worst, "bound": TOL},
+            "roofline": {"bound": "hbm", "kernel": dom_key, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "alg_bytes_per_launch": dom_bytes},
+            "step_hbm_frac": round(sum(algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"]) for p in prods)
+                                   / (ms / K / 1e3) / 1e9 / peak, 4),
+            "gpu_launches": launches_per_step * K,
+            "clocks": ck,
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": E},
+            "cpu_baseline": cpu,
+            "per_matrix": per,
+        }
+        print(json.dumps(line), flush=True)
+    for p in prods:
+        p["M"].close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

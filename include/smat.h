@@ -177,6 +177,11 @@ smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *a
 smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_host,
                              const void *beta, void *y_host, void *stream);
 
+/* Number of kernel launches one product through variant v issues on this
+ * handle (merge-path and COO add a carry fix-up launch when they span more
+ * than one tile; COO adds one for empty rows).  Writes 0 for v not built. */
+smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *launches);
+
 /* Feature parameters (computes them on `stream` = NULL if not yet done). */
 smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out);
 

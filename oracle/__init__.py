@@ -102,6 +102,24 @@ def spmv_csr(m, rowptr, colidx, val, x, alpha=1.0, beta=0.0, y=None, threads: in
     return out
 
 
+def spmv_csr_rows(rowptr, colidx, val, x, r0, r1, alpha, beta, y, threads: int = 1):
+    """Rows [r0, r1) of y = alpha*A*x + beta*y, written into ``y`` in place.
+    All arrays must already be contiguous (int32 indices, float64 values)."""
+    for a, t in ((rowptr, np.int32), (colidx, np.int32), (val, np.float64), (x, np.float64), (y, np.float64)):
+        assert a.dtype == t and a.flags.c_contiguous
+    m = int(r1 - r0)
+    if m <= 0:
+        return
+    prp = rowptr.ctypes.data + 4 * int(r0)
+    py = y.ctypes.data + 8 * int(r0)
+    if threads <= 1:
+        lib().oracle_spmv_csr(m, prp, colidx.ctypes.data, val.ctypes.data, x.ctypes.data, float(alpha),
+                              float(beta), py)
+    else:
+        lib().oracle_spmv_csr_threads(m, prp, colidx.ctypes.data, val.ctypes.data, x.ctypes.data, float(alpha),
+                                      float(beta), py, int(threads))
+
+
 def partition_rows(m, rowptr, nthreads):
     rp, prp = _c(rowptr, np.int32)
     b = np.zeros(nthreads + 1, dtype=np.int64)

@@ -84,10 +84,10 @@ static int64_t first_row_at_or_after(const int32_t *rowptr, int64_t m, int64_t t
 }
 
 void oracle_partition_rows(int64_t m, const int32_t *rowptr, int nthreads, int64_t *bounds) {
-  int64_t nnz = rowptr[m];
+  int64_t base = rowptr[0], nnz = (int64_t)rowptr[m] - base;
   bounds[0] = 0;
   for (int t = 1; t < nthreads; ++t) {
-    int64_t target = nnz * t / nthreads;
+    int64_t target = base + nnz * t / nthreads;
     int64_t r = first_row_at_or_after(rowptr, m, target);
     if (r < bounds[t - 1]) r = bounds[t - 1];
     bounds[t] = r;

@@ -66,6 +66,7 @@ _SIGS = {
     "smat_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_launches": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
     "smat_get_plan": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -150,6 +151,12 @@ def smat_spmv_variant(h, v, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
 
 def smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
     return lib().smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_spmv_launches(h, v) -> int:
+    n = ctypes.c_int32()
+    _check(lib().smat_spmv_launches(h, v, ctypes.byref(n)), "smat_spmv_launches")
+    return n.value
 
 
 def smat_get_features(h) -> smat_features_t:
@@ -336,6 +343,10 @@ class SpMatrix:
     def plan(self) -> dict:
         v, ms, conf, tr = smat_get_plan(self.h)
         return {"variant": v, "name": VARIANT_NAMES[v], "tune_ms": ms, "confidence": conf, "trialled": tr}
+
+    def launches(self, variant=None) -> int:
+        """Kernel launches of one product (through the plan, or `variant`)."""
+        return smat_spmv_launches(self.h, self.plan()["variant"] if variant is None else int(variant))
 
     def timings(self) -> np.ndarray:
         return smat_get_timings(self.h)

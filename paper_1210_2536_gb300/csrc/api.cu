@@ -623,6 +623,13 @@ smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_h
   return SMAT_OK;
 }
 
+smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *launches) {
+  TRYS(check_handle(h));
+  if (!launches || (int)v < 0 || (int)v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  *launches = variant_ready(h, v) ? spmv_launch_count(h, v) : 0;
+  return SMAT_OK;
+}
+
 smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out) {
   TRYS(check_handle(h));
   if (!out) return SMAT_ERR_INVALID_ARG;

@@ -114,6 +114,8 @@ cudaError_t launch_to_dia(const smat_s *h, const int32_t *d_off, int64_t nd, voi
 
 // Size in bytes of the carry scratch a variant needs (0 if none).
 size_t carry_bytes_needed(const smat_s *h, int variant);
+// Kernel launches one product through `variant` issues.
+int spmv_launch_count(const smat_s *h, int variant);
 // SpMV through one variant; alpha/beta are host scalars of the compute type.
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,
                         const void *beta, void *y, cudaStream_t s);

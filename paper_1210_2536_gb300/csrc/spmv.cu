@@ -516,6 +516,19 @@ size_t carry_bytes_needed(const smat_s *h, int variant) {
   return (size_t)((tiles * 4 + 15) / 16) * 16 + (size_t)tiles * tsz;
 }
 
+int spmv_launch_count(const smat_s *h, int variant) {
+  if (h->m == 0) return 0;
+  if (variant == SMAT_V_CSR_MERGE) {
+    long long tiles = (h->m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+    return 1 + (tiles > 1);
+  }
+  if (variant == SMAT_V_COO) {
+    long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    return (h->coo_nempty > 0) + (h->nnz > 0) + (tiles > 1);
+  }
+  return 1;
+}
+
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
                         void *y, cudaStream_t s) {
   switch (h->dtype) {
