@@ -73,7 +73,13 @@ typedef enum {
   SMAT_V_ELL = 5,        /* column-major ELL, 16-byte vector loads           */
   SMAT_V_DIA = 6,        /* diagonal-major DIA                               */
   SMAT_V_COO = 7,        /* COO with segmented reduction                     */
-  SMAT_NUM_VARIANTS = 8
+  SMAT_NUM_VARIANTS = 8,
+  /* Not a selector class: CSR-scalar that rounds every product and every
+   * sum separately, in ascending column order -- the operations of the CSR
+   * definition.  In FP64 its result is bitwise reproducible against a plain
+   * sequential implementation; it costs two FP64 operations per nonzero
+   * instead of one.  Only smat_spmv_variant runs it. */
+  SMAT_V_CSR_SCALAR_EXACT = 8
 } smat_variant_t;
 
 /* Feature parameters (Sec. 4, Table "Feature parameters of a sparse matrix").

@@ -27,7 +27,9 @@ SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO = range(4)
 (SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32, SMAT_V_CSR_MERGE, SMAT_V_ELL,
  SMAT_V_DIA, SMAT_V_COO) = range(8)
 SMAT_NUM_VARIANTS = 8
-VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo"]
+SMAT_V_CSR_SCALAR_EXACT = 8
+VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo",
+                 "csr_scalar_exact"]
 SMAT_TUNE_LEARNED, SMAT_TUNE_EXHAUSTIVE, SMAT_TUNE_RULES, SMAT_TUNE_FIXED = range(4)
 SMAT_MLP_PARAMS = 5512
 DTYPES = {"f64": SMAT_F64, "f32": SMAT_F32, "bf16": SMAT_BF16}

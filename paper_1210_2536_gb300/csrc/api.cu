@@ -307,7 +307,7 @@ bool variant_ready(const smat_s *h, int v) {
 }
 
 smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
-  if (v < 0 || v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  if (v < 0 || v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
   int fmt = variant_format(v);
   if (fmt != SMAT_FMT_CSR && !h->have_features) TRYS(compute_features(h, s));
   TRYS(build_format(h, fmt, s));
@@ -595,7 +595,7 @@ smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *a
                                 const void *beta, void *y, void *stream) {
   TRYS(check_handle(h));
   if (!alpha || !beta || (h->m > 0 && !y) || (h->n > 0 && !x)) return SMAT_ERR_INVALID_ARG;
-  if ((int)v < 0 || (int)v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  if ((int)v < 0 || (int)v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
   if (!variant_ready(h, v)) {
     TRYS(prepare_variant(h, v, (cudaStream_t)stream));
     if (!variant_ready(h, v)) return SMAT_ERR_UNSUPPORTED;
@@ -625,7 +625,7 @@ smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_h
 
 smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *launches) {
   TRYS(check_handle(h));
-  if (!launches || (int)v < 0 || (int)v >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  if (!launches || (int)v < 0 || (int)v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
   *launches = variant_ready(h, v) ? spmv_launch_count(h, v) : 0;
   return SMAT_OK;
 }

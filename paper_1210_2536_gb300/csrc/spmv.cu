@@ -25,45 +25,118 @@ constexpr unsigned FULL = 0xffffffffu;
 template <typename V> struct Compute { typedef float T; };
 template <> struct Compute<double> { typedef double T; };
 
-__device__ __forceinline__ double ld_val(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_val(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+// Matrix arrays are read once per product: load them with the streaming
+// (evict-first) policy so that x, which every product gathers from, stays in L2.
+__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) {
+  return __uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short *>(p)) << 16);
+}
+__device__ __forceinline__ int ld_idx(const int32_t *p) { return __ldcs(p); }
 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
-// acc + v*x: separately rounded for FP64 storage (matches the CSR definition
-// operation for operation), fused multiply-add for FP32 accumulation.
-__device__ __forceinline__ double madd(double acc, double v, double x) { return __dadd_rn(acc, __dmul_rn(v, x)); }
-__device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf(v, x, acc); }
-
-// acc + v*x with one rounding (kernels that reorder the sum anyway).
+// acc + v*x.  GB300 executes FP64 arithmetic at about 2 operations per clock
+// per SM, so FP64 SpMV is bound by the FP64 pipe about as much as by HBM:
+// every kernel spends exactly one fused multiply-add per stored product.
+// The EXACT flavour (CSR-scalar only) instead rounds the product and the sum
+// separately, in ascending column order -- the CSR definition operation for
+// operation -- at twice the FP64 cost.
 __device__ __forceinline__ double fused(double acc, double v, double x) { return fma(v, x, acc); }
 __device__ __forceinline__ float fused(float acc, float v, float x) { return fmaf(v, x, acc); }
+template <bool EXACT>
+__device__ __forceinline__ double madd(double acc, double v, double x) {
+  return EXACT ? __dadd_rn(acc, __dmul_rn(v, x)) : fma(v, x, acc);
+}
+template <bool EXACT>
+__device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf(v, x, acc); }
 
-template <typename T>
+// y_i = alpha*acc (+ beta*y_i).  alpha == 1 skips the multiply (exact);
+// beta != 0 folds beta*y_i into one fused multiply-add unless EXACT.
+template <typename T, bool EXACT = false>
 __device__ __forceinline__ T epilogue(T acc, T alpha, T beta, const T *y, long long i) {
-  T ax = mul_rn(alpha, acc);
+  const T ax = alpha == (T)1 ? acc : mul_rn(alpha, acc);
   if (beta == (T)0) return ax;
-  return add_rn(ax, mul_rn(beta, y[i]));
+  if (EXACT) return add_rn(ax, mul_rn(beta, y[i]));
+  return fused(ax, beta, y[i]);
+}
+
+// 16-byte vector loads of R consecutive values (R * sizeof(V) == 16) and of
+// R consecutive column indices.
+template <typename V, int R> struct VecOf;
+template <> struct VecOf<double, 2> { typedef double2 T; };
+template <> struct VecOf<float, 4> { typedef float4 T; };
+template <> struct VecOf<__nv_bfloat16, 8> { typedef uint4 T; };
+
+template <typename V, int R>
+__device__ __forceinline__ void load_vals(const V *p, typename Compute<V>::T (&out)[R]);
+template <>
+__device__ __forceinline__ void load_vals<double, 2>(const double *p, double (&out)[2]) {
+  double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
+  out[0] = v.x; out[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load_vals<float, 4>(const float *p, float (&out)[4]) {
+  float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_vals<__nv_bfloat16, 8>(const __nv_bfloat16 *p, float (&out)[8]) {
+  uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
+  unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    out[2 * q] = __uint_as_float(w[q] << 16);
+    out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_cols(const int32_t *p, int (&c)[R]) {
+  if constexpr (R == 2) {
+    int2 v = __ldcs(reinterpret_cast<const int2 *>(p));
+    c[0] = v.x; c[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      int4 v = __ldcs(reinterpret_cast<const int4 *>(p) + q);
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // K7: CSR-scalar, one thread per row.
 // ---------------------------------------------------------------------------
-template <typename V, typename T>
+template <typename V, typename T, bool EXACT>
 __global__ void __launch_bounds__(256) csr_scalar_kernel(const int32_t *__restrict__ rowptr,
                                                          const int32_t *__restrict__ col,
                                                          const V *__restrict__ val, const T *__restrict__ x,
                                                          T alpha, T beta, T *__restrict__ y, long long m) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
-    int s = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+    const int s = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
     T acc = 0;
-    for (int k = s; k < e; ++k) acc = madd(acc, (T)ld_val(val + k), __ldg(x + __ldg(col + k)));
-    y[i] = epilogue(acc, alpha, beta, y, i);
+    // eight entries per step, predicated: every index and value load, then
+    // the gathers, then the in-order accumulation
+    for (int k = s; k < e; k += 8) {
+      int c[8];
+      T v[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = k + u < e ? ld_idx(col + k + u) : 0;
+        v[u] = k + u < e ? (T)ld_val(val + k + u) : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = k + u < e ? __ldg(x + c[u]) : (T)0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k + u < e) acc = madd<EXACT>(acc, v[u], xv[u]);
+    }
+    y[i] = epilogue<T, EXACT>(acc, alpha, beta, y, i);
   }
 }
 
@@ -83,9 +156,21 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(const int32_t *__restri
     long long row = r0 + lane / W;
     T acc = 0;
     if (row < m) {
-      int s = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
-#pragma unroll 4
-      for (int k = s + sub; k < e; k += W) acc = fused(acc, (T)ld_val(val + k), __ldg(x + __ldg(col + k)));
+      const int s = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+      for (int k = s + sub; k < e; k += 4 * W) {
+        int c[4];
+        T v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c[u] = k + u * W < e ? ld_idx(col + k + u * W) : 0;
+          v[u] = k + u * W < e ? (T)ld_val(val + k + u * W) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = k + u * W < e ? __ldg(x + c[u]) : (T)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + u * W < e) acc = fused(acc, v[u], xv[u]);
+      }
     }
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o, W);
@@ -177,6 +262,31 @@ __device__ __forceinline__ void merge_search(const int32_t *__restrict__ rowptr,
   *b = d - lo;
 }
 
+// s_v[j] = val[b0 + j], s_x[j] = x[col[b0 + j]] for j < cnt: IPT coalesced
+// items per thread, every index and value load issued before the gathers.
+template <typename V, typename T, int NT, int IPT>
+__device__ __forceinline__ void stage_pairs(const int32_t *__restrict__ col, const V *__restrict__ val,
+                                            const T *__restrict__ x, long long b0, int cnt, T *s_v, T *s_x) {
+  int c[IPT];
+  T v[IPT], xv[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int j = threadIdx.x + q * NT;
+    c[q] = j < cnt ? ld_idx(col + b0 + j) : 0;
+    v[q] = j < cnt ? (T)ld_val(val + b0 + j) : (T)0;
+  }
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) xv[q] = (threadIdx.x + q * NT) < cnt ? __ldg(x + c[q]) : (T)0;
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int j = threadIdx.x + q * NT;
+    if (j < cnt) {
+      s_v[j] = v[q];
+      s_x[j] = xv[q];
+    }
+  }
+}
+
 template <typename V, typename T, int NT, int IPT>
 __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict__ rowptr,
                                                        const int32_t *__restrict__ col,
@@ -185,7 +295,7 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
                                                        long long nnz, int32_t *carry_row, T *carry_val) {
   constexpr int TILE = NT * IPT;
   __shared__ int32_t s_rowend[TILE + 1];
-  __shared__ T s_prod[TILE];
+  __shared__ T s_v[TILE], s_x[TILE];
   __shared__ long long s_coord[4];
   __shared__ SegPair<T> s_total;
   const long long total = m + nnz;
@@ -201,10 +311,7 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
   const long long a0 = s_coord[0], b0 = s_coord[1], a1 = s_coord[2], b1 = s_coord[3];
   const int nrows = (int)(a1 - a0), nnzs = (int)(b1 - b0);
   for (int i = threadIdx.x; i < nrows; i += NT) s_rowend[i] = __ldg(rowptr + a0 + 1 + i);
-  for (int j = threadIdx.x; j < nnzs; j += NT) {
-    long long k = b0 + j;
-    s_prod[j] = mul_rn((T)ld_val(val + k), __ldg(x + __ldg(col + k)));
-  }
+  stage_pairs<V, T, NT, IPT>(col, val, x, b0, nnzs, s_v, s_x);
   __syncthreads();
   // this thread's start on the tile's merge path
   const int items = (int)(d1 - d0);
@@ -231,7 +338,7 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
       acc = 0;
       ++a;
     } else {
-      acc = add_rn(acc, s_prod[b - b0]);
+      acc = fused(acc, s_v[b - b0], s_x[b - b0]);
       ++b;
     }
   }
@@ -248,6 +355,43 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
   }
 }
 
+// IPT consecutive int32 from p (16-byte aligned when `full`).
+template <int IPT>
+__device__ __forceinline__ void load_i32_run(const int32_t *__restrict__ p, bool full, int valid, int (&o)[IPT],
+                                             int fill) {
+  if (full) {
+#pragma unroll
+    for (int q = 0; q < IPT / 4; ++q) {
+      int4 v = __ldcs(reinterpret_cast<const int4 *>(p) + q);
+      o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) o[q] = q < valid ? ld_idx(p + q) : fill;
+  }
+}
+
+template <typename V, int IPT>
+__device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full, int valid,
+                                             typename Compute<V>::T (&o)[IPT]) {
+  constexpr int R = 16 / (int)sizeof(V);
+  if (full) {
+#pragma unroll
+    for (int q = 0; q < IPT / R; ++q) {
+      typename Compute<V>::T t[R];
+      load_vals<V, R>(p + q * R, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r) o[q * R + r] = t[r];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) o[q] = q < valid ? (typename Compute<V>::T)ld_val(p + q) : 0;
+  }
+}
+
+// K12: COO.  A CTA owns NT*IPT consecutive stored entries; thread t owns IPT
+// consecutive ones, read with 16-byte vector loads, and accumulates them with
+// one fused multiply-add each.  A row ends at entry k when row[k+1] differs.
 template <typename V, typename T, int NT, int IPT>
 __global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row,
                                                  const int32_t *__restrict__ col,
@@ -255,40 +399,46 @@ __global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row
                                                  T alpha, T beta, T *__restrict__ y, long long nnz,
                                                  int32_t *carry_row, T *carry_val) {
   constexpr int TILE = NT * IPT;
-  __shared__ int32_t s_row[TILE + 1];
-  __shared__ T s_prod[TILE];
+  static_assert(IPT % 8 == 0, "vector loads need 8 entries per thread");
   __shared__ SegPair<T> s_total;
   const long long b0 = (long long)blockIdx.x * TILE;
-  const int cnt = (int)(nnz - b0 < TILE ? nnz - b0 : TILE);
-  for (int j = threadIdx.x; j < cnt; j += NT) {
-    long long k = b0 + j;
-    s_row[j] = __ldg(row + k);
-    s_prod[j] = mul_rn((T)ld_val(val + k), __ldg(x + __ldg(col + k)));
-  }
-  if (threadIdx.x == 0) s_row[cnt] = (b0 + cnt < nnz) ? __ldg(row + b0 + cnt) : -1;
-  __syncthreads();
-  const int j0 = min((int)threadIdx.x * IPT, cnt), j1 = min(j0 + IPT, cnt);
+  const long long k0 = b0 + (long long)threadIdx.x * IPT;
+  const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
+  const bool full = valid == IPT;
+  int r[IPT], c[IPT];
+  T v[IPT], xv[IPT];
+  load_i32_run<IPT>(row + k0, full, valid, r, -1);
+  load_i32_run<IPT>(col + k0, full, valid, c, 0);
+  load_val_run<V, IPT>(val + k0, full, valid, v);
+  const int r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) xv[q] = q < valid ? __ldg(x + c[q]) : (T)0;
   T acc = 0, first_acc = 0;
   int first_row = -1;
-  for (int j = j0; j < j1; ++j) {
-    acc = add_rn(acc, s_prod[j]);
-    int r = s_row[j];
-    if (s_row[j + 1] != r) {  // last stored entry of row r
-      if (first_row < 0) {
-        first_row = r;
-        first_acc = acc;
-      } else {
-        y[r] = epilogue(acc, alpha, beta, y, (long long)r);
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    if (q < valid) {
+      acc = fused(acc, v[q], xv[q]);
+      const int rn = q + 1 < IPT ? r[q + 1] : r_next;
+      if (rn != r[q]) {  // last stored entry of row r[q]
+        if (first_row < 0) {
+          first_row = r[q];
+          first_acc = acc;
+        } else {
+          y[r[q]] = epilogue(acc, alpha, beta, y, (long long)r[q]);
+        }
+        acc = 0;
       }
-      acc = 0;
     }
   }
   SegPair<T> mine{first_row >= 0 ? 1 : 0, acc};
   SegPair<T> incoming = block_seg_scan<T, NT>(mine, &s_total);
   if (first_row >= 0) y[first_row] = epilogue(add_rn(incoming.v, first_acc), alpha, beta, y, (long long)first_row);
-  if (threadIdx.x == 0) {
-    bool open = cnt > 0 && s_row[cnt] == s_row[cnt - 1];
-    carry_row[blockIdx.x] = open ? s_row[cnt - 1] : -1;
+  if (threadIdx.x == NT - 1) {
+    // the row open at the end of the tile continues into the next tile
+    const long long kl = min(b0 + TILE, nnz) - 1;
+    const bool open = kl + 1 < nnz && __ldg(row + kl + 1) == __ldg(row + kl);
+    carry_row[blockIdx.x] = open ? __ldg(row + kl) : -1;
     carry_val[blockIdx.x] = open ? s_total.v : (T)0;
   }
 }
@@ -317,52 +467,56 @@ __global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long co
   }
 }
 
-// ---------------------------------------------------------------------------
-// K10: ELL, column-major, R consecutive rows per thread so that every slot is
-// one 16-byte load of values (and 4R bytes of columns).
-// ---------------------------------------------------------------------------
-template <typename V, int R> struct VecOf;
-template <> struct VecOf<double, 2> { typedef double2 T; };
-template <> struct VecOf<float, 4> { typedef float4 T; };
-template <> struct VecOf<__nv_bfloat16, 8> { typedef uint4 T; };
-
-template <typename V, int R>
-__device__ __forceinline__ void load_vals(const V *p, typename Compute<V>::T (&out)[R]);
-template <>
-__device__ __forceinline__ void load_vals<double, 2>(const double *p, double (&out)[2]) {
-  double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-  out[0] = v.x; out[1] = v.y;
-}
-template <>
-__device__ __forceinline__ void load_vals<float, 4>(const float *p, float (&out)[4]) {
-  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-}
-template <>
-__device__ __forceinline__ void load_vals<__nv_bfloat16, 8>(const __nv_bfloat16 *p, float (&out)[8]) {
-  uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-  unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    out[2 * q] = __uint_as_float(w[q] << 16);
-    out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+// y[i0 .. i0+R) from R accumulators: one vector store (and load when beta != 0)
+// for full groups, scalar at the tail.
+template <typename T, int R> struct YVec;
+template <> struct YVec<double, 2> {
+  static __device__ __forceinline__ void ld(const double *p, double (&o)[2]) { double2 v = *reinterpret_cast<const double2 *>(p); o[0] = v.x; o[1] = v.y; }
+  static __device__ __forceinline__ void st(double *p, const double (&o)[2]) { *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]); }
+};
+template <> struct YVec<float, 4> {
+  static __device__ __forceinline__ void ld(const float *p, float (&o)[4]) { float4 v = *reinterpret_cast<const float4 *>(p); o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  static __device__ __forceinline__ void st(float *p, const float (&o)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct YVec<float, 8> {
+  static __device__ __forceinline__ void ld(const float *p, float (&o)[8]) {
+    float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
   }
-}
+  static __device__ __forceinline__ void st(float *p, const float (&o)[8]) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
+  }
+};
 
-template <int R>
-__device__ __forceinline__ void load_cols(const int32_t *p, int (&c)[R]) {
-  if constexpr (R == 2) {
-    int2 v = __ldg(reinterpret_cast<const int2 *>(p));
-    c[0] = v.x; c[1] = v.y;
+template <typename T, int R>
+__device__ __forceinline__ void write_rows(T *__restrict__ y, long long i0, long long m, const T (&acc)[R], T alpha,
+                                           T beta) {
+  if (i0 + R <= m) {
+    T out[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = alpha == (T)1 ? acc[r] : mul_rn(alpha, acc[r]);
+    if (beta != (T)0) {
+      T yo[R];
+      YVec<T, R>::ld(y + i0, yo);
+#pragma unroll
+      for (int r = 0; r < R; ++r) out[r] = fused(out[r], beta, yo[r]);
+    }
+    YVec<T, R>::st(y + i0, out);
   } else {
 #pragma unroll
-    for (int q = 0; q < R / 4; ++q) {
-      int4 v = __ldg(reinterpret_cast<const int4 *>(p) + q);
-      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
-    }
+    for (int r = 0; r < R; ++r)
+      if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
   }
 }
 
+// ---------------------------------------------------------------------------
+// K10: ELL, column-major, R consecutive rows per thread so that every slot is
+// one 16-byte load of values (and 4R bytes of columns).  U slots are loaded
+// before their gathers are issued (U*R = 8 gathers in flight per thread);
+// padding (column -1) gathers x[0] and is dropped by a select, so no load
+// sits behind a branch.
+// ---------------------------------------------------------------------------
 template <typename V, int R>
 __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
                                                   long long P, long long K,
@@ -370,31 +524,44 @@ __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ec
                                                   typename Compute<V>::T alpha, typename Compute<V>::T beta,
                                                   typename Compute<V>::T *__restrict__ y, long long m) {
   typedef typename Compute<V>::T T;
+  constexpr int U = 16 / R;
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
   if (i0 >= m) return;
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0;
-#pragma unroll 4
-  for (long long q = 0; q < K; ++q) {
-    T v[R];
-    int c[R];
-    load_vals<V, R>(eval + q * P + i0, v);
-    load_cols<R>(ecol + q * P + i0, c);
+  for (long long q = 0; q < K; q += U) {
+    T v[U][R], xv[U][R];
+    int c[U][R];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (c[r] >= 0) acc[r] = madd(acc[r], v[r], __ldg(x + c[r]));
+    for (int u = 0; u < U; ++u) {
+      if (q + u < K) {
+        load_vals<V, R>(eval + (q + u) * P + i0, v[u]);
+        load_cols<R>(ecol + (q + u) * P + i0, c[u]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) { v[u][r] = 0; c[u][r] = -1; }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) xv[u][r] = c[u][r] >= 0 ? __ldg(x + c[u][r]) : (T)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (c[u][r] >= 0) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
   }
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+  write_rows<T, R>(y, i0, m, acc, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------
 // K11: DIA, diagonal-major, R consecutive rows per thread, offsets staged in
-// shared memory.  Fill zeros are multiplied like stored values (Table
-// "Performance features of the four formats": extra computation decided by
-// zero filling).
+// shared memory, U diagonals loaded per step.  Fill zeros are multiplied like
+// stored values (Table "Performance features of the four formats": extra
+// computation decided by zero filling); positions whose column falls outside
+// the matrix gather x[0] and are dropped by a select.
 // ---------------------------------------------------------------------------
 template <typename V, int R>
 __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ off, int nd,
@@ -404,6 +571,7 @@ __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ of
                                                   typename Compute<V>::T *__restrict__ y, long long m,
                                                   long long n) {
   typedef typename Compute<V>::T T;
+  constexpr int U = 16 / R;
   extern __shared__ int32_t s_off[];
   for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
   __syncthreads();
@@ -412,20 +580,33 @@ __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ of
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0;
-#pragma unroll 4
-  for (int t = 0; t < nd; ++t) {
-    const long long o = s_off[t];
-    T v[R];
-    load_vals<V, R>(dval + (long long)t * P + i0, v);
+  for (int t = 0; t < nd; t += U) {
+    T v[U][R], xv[U][R];
+    bool in[U][R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      long long j = i0 + r + o;
-      if (j >= 0 && j < n) acc[r] = madd(acc[r], v[r], __ldg(x + j));
+    for (int u = 0; u < U; ++u) {
+      const bool live = t + u < nd;
+      const long long o = live ? s_off[t + u] : 0;
+      if (live) {
+        load_vals<V, R>(dval + (long long)(t + u) * P + i0, v[u]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u][r] = 0;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long j = i0 + r + o;
+        in[u][r] = live && j >= 0 && j < n;
+        xv[u][r] = in[u][r] ? __ldg(x + j) : (T)0;
+      }
     }
-  }
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (in[u][r]) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+  }
+  write_rows<T, R>(y, i0, m, acc, alpha, beta);
 }
 
 int grid_for(long long work, int block, int max_blocks) {
@@ -450,7 +631,10 @@ cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const 
   if (m == 0) return cudaSuccess;
   switch (variant) {
     case SMAT_V_CSR_SCALAR:
-      csr_scalar_kernel<V, T><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_scalar_kernel<V, T, false><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      break;
+    case SMAT_V_CSR_SCALAR_EXACT:
+      csr_scalar_kernel<V, T, true><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
       break;
     case SMAT_V_CSR_VEC4:
       csr_vector_kernel<V, T, 4><<<grid_for(m * 4, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);

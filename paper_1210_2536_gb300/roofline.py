@@ -12,6 +12,10 @@ y written once (plus read when beta != 0):
   every variant                  + s_x N + s_y M (1 + [beta != 0])
 
 GFLOP/s counts 2 NNZ flops per product (true nonzeros only).
+
+GB300 runs FP64 arithmetic at about 2 operations per clock per SM, so an
+FP64 product that spends one fused multiply-add per stored slot can be bound
+by the FP64 pipe instead of HBM; ``bound`` picks whichever roof binds.
 """
 from __future__ import annotations
 
@@ -39,3 +43,40 @@ def algorithmic_bytes(f: dict, variant: int, dtype: str, beta_nonzero: bool = Fa
 
 def flops(f: dict) -> float:
     return 2.0 * f["nnz"]
+
+
+# FP64 arithmetic on GB300: 152 SMs x 2 FP64 operations per clock x 2.07 GHz
+# (one fused multiply-add counts as one operation, i.e. 2 flops):
+# 629.3 G operations/s = 1.2586 TFLOP/s.  FP32 units are 64x wider, so only
+# FP64 kernels can be bound by arithmetic.
+SMS, FP64_OPS_PER_CLK_PER_SM, SM_CLOCK_GHZ = 152, 2, 2.07
+FP64_PEAK_TFLOPS = SMS * FP64_OPS_PER_CLK_PER_SM * 2 * SM_CLOCK_GHZ / 1e3
+
+
+def fp64_ops(f: dict, variant: int) -> float:
+    """FP64 fused multiply-adds one product needs in this format: one per
+    stored slot the kernel multiplies (fill and padding included)."""
+    if variant == V_ELL:
+        return float(f["max_rd"] * f["m"])
+    if variant == V_DIA:
+        return float(f["ndiags"] * f["m"])
+    return float(f["nnz"])
+
+
+def bound(f: dict, variant: int, dtype: str, seconds: float, hbm_gbs: float) -> dict:
+    """The binding roofline of one launch: HBM bytes, or (FP64 storage) FP64
+    arithmetic, whichever needs more time at peak; achieved/peak for it."""
+    byts = algorithmic_bytes(f, variant, dtype)
+    t_hbm = byts / (hbm_gbs * 1e9)
+    out = {"bound": "hbm", "achieved": byts / seconds / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+           "alg_bytes": byts}
+    if dtype == "f64":
+        ops = fp64_ops(f, variant)
+        t_alu = 2.0 * ops / (FP64_PEAK_TFLOPS * 1e12)
+        out["fp64_frac"] = t_alu / seconds
+        if t_alu > t_hbm:
+            out.update(bound="alu", achieved=2.0 * ops / seconds / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                       alg_fp64_fma=ops)
+    out["hbm_frac"] = t_hbm / seconds
+    out["frac"] = out["achieved"] / out["peak"]
+    return out

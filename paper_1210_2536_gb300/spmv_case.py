@@ -1,0 +1,94 @@
+"""Run one synthetic matrix through chosen SpMV variants and report time,
+GFLOP/s and the fraction of HBM bandwidth each reaches (algorithmic bytes,
+see roofline.py).  Used for kernel studies and profiler captures:
+
+  python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --dtype f64 --variant all
+  python -m paper_1210_2536_gb300.spmv_case --matrix powerlaw:2000000 --variant coo --reps 3
+
+Matrices: stencil2d5:<m>, stencil3d7:<m>, stencil3d27:<m>, uniform:<n>[:lambda],
+powerlaw:<n>[:alpha], blockdiag:<n>[:b].
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+
+import numpy as np
+
+
+def make_matrix(spec: str):
+    from . import synth
+    kind, *args = spec.split(":")
+    a = [float(v) for v in args]
+    if kind == "stencil2d5":
+        return synth.stencil2d5(int(a[0]))
+    if kind == "stencil3d7":
+        return synth.stencil3d7(int(a[0]))
+    if kind == "stencil3d27":
+        return synth.stencil3d27(int(a[0]))
+    if kind == "uniform":
+        return synth.uniform_random(int(a[0]), a[1] if len(a) > 1 else 16.0, 0)
+    if kind == "powerlaw":
+        return synth.powerlaw(int(a[0]), a[1] if len(a) > 1 else 1.8, 10000, 0)
+    if kind == "blockdiag":
+        return synth.blockdiag(int(a[0]), int(a[1]) if len(a) > 1 else 8, 0)
+    raise ValueError(spec)
+
+
+def main():
+    import torch
+
+    import paper_1210_2536_gb300 as smat
+    from .roofline import algorithmic_bytes
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--matrix", default="stencil3d7:128")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--variant", default="all")
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args()
+    A = make_matrix(a.matrix)
+    from . import synth
+    dev = torch.device("cuda:0")
+    if a.dtype == "f64":
+        vals = A.val
+    elif a.dtype == "f32":
+        vals = A.val.astype(np.float32)
+    else:
+        vals = torch.from_numpy(A.val).to(torch.bfloat16).view(torch.int16).numpy()
+    M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                      torch.from_numpy(np.ascontiguousarray(vals)).to(dev), a.dtype)
+    f = M.features()
+    tdt = torch.float64 if a.dtype == "f64" else torch.float32
+    x = torch.from_numpy(synth.uniform(0, 1, A.n)).to(dev).to(tdt)
+    y = torch.zeros(A.m, dtype=tdt, device=dev)
+    peak = 6800.0
+    try:
+        peak = float(json.load(open(os.path.join(os.path.dirname(os.path.dirname(__file__)),
+                                                 "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    names = smat.VARIANT_NAMES
+    vs = [v for v in range(8) if (f["admissible"] >> v) & 1] if a.variant == "all" else [names.index(a.variant)]
+    out = {"matrix": A.name, "m": A.m, "nnz": A.nnz, "dtype": a.dtype, "variants": {}}
+    for v in vs:
+        for _ in range(a.warmup):
+            M.spmv(x, y, variant=v)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
+        for s, e in ev:
+            s.record()
+            M.spmv(x, y, variant=v)
+            e.record()
+        torch.cuda.synchronize()
+        ms = statistics.median(s.elapsed_time(e) for s, e in ev)
+        b = algorithmic_bytes(f, v, a.dtype)
+        out["variants"][names[v]] = {"ms": round(ms, 5), "gflops": round(2 * A.nnz / ms / 1e6, 1),
+                                     "gbs": round(b / ms / 1e6, 1), "hbm_frac": round(b / ms / 1e6 / peak, 4)}
+    print(json.dumps(out))
+    M.close()
+
+
+if __name__ == "__main__":
+    main()

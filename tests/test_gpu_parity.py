@@ -120,7 +120,7 @@ def test_conversions_bit_exact(case, dtype):
     M.close()
 
 
-EXACT_F64 = {smat.SMAT_V_CSR_SCALAR, smat.SMAT_V_ELL, smat.SMAT_V_DIA}
+EXACT_F64 = {smat.SMAT_V_CSR_SCALAR_EXACT}
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
@@ -134,8 +134,8 @@ def test_spmv_every_variant(case, dtype, ab):
     ref, scale = reference(A, vals64, x, alpha, beta, y0 if beta != 0 else None)
     adm = M.features()["admissible"]
     xd = torch.from_numpy(x).to(DEV)
-    for v in range(smat.SMAT_NUM_VARIANTS):
-        if not (adm >> v) & 1:
+    for v in range(smat.SMAT_NUM_VARIANTS + 1):
+        if v < smat.SMAT_NUM_VARIANTS and not (adm >> v) & 1:
             continue
         y = torch.from_numpy(y0.copy()).to(DEV)
         if beta == 0:
