@@ -263,6 +263,33 @@ smat_status_t smat_cast_f64_to_f32(const double *in, float *out, int64_t n, void
 smat_status_t smat_cast_f64_to_bf16(const double *in, uint16_t *out, int64_t n, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free product (the paper has no counterpart to this entry point) */
+/* ------------------------------------------------------------------------ */
+/* y = alpha*A*x + beta*y by merge-path CSR for callers that cannot allocate
+ * device memory: a solver whose memory manager owns every device byte, code
+ * that must not synchronise the device the way cudaMalloc/cudaFree may, or a
+ * host that forbids allocation once its time-critical loop runs.  No handle
+ * and no allocation: the caller passes the CSR arrays (rowptr[m+1],
+ * colidx[nnz], vals[nnz] of the storage type), x[n] and y[m], all DEVICE
+ * pointers, and alpha/beta as HOST pointers to one scalar of the compute type
+ * (FP64 for SMAT_F64, FP32 otherwise).  The input must be canonical CSR; it is
+ * not validated.
+ * The kernel's only scratch, one carry per tile of 2048 merge items, lives in
+ * a fixed 768 KiB array in the library's device memory, held by every GPU
+ * that loads the library until the process exits.  Limit: ceil((m + nnz) /
+ * 2048) <= 65536, i.e. m + nnz <= 134,217,728; larger inputs return
+ * SMAT_ERR_UNSUPPORTED without launching anything.  The first call on each
+ * device looks up the array's address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call shares the array, so calls
+ * whose kernels overlap on the GPU race: order them on one stream or
+ * synchronise between them.  Asynchronous on `stream`; only launch errors are
+ * reported. */
+smat_status_t smat_spmv_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                                          const int32_t *colidx, const void *vals, smat_dtype_t dtype,
+                                          const void *alpha, const void *x, const void *beta, void *y,
+                                          void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Testing hook                                                              */
 /* ------------------------------------------------------------------------ */
 /* Make the k-th device allocation from now on fail (k >= 1), as if the GPU

@@ -83,6 +83,8 @@ _SIGS = {
     "smat_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP]),
     "smat_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _I32, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, _VP]),
+    "smat_spmv_csr_merge_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP,
+                                                   _VP, _VP]),
     "smat_cast_f64_to_f32": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "smat_cast_f64_to_bf16": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
 }
@@ -228,6 +230,13 @@ def smat_mlp_loss_grad(params_ptr, x_ptr, t_ptr, B, grad_ptr, loss_ptr, work_ptr
 
 def smat_mlp_adam(p_ptr, g_ptr, m_ptr, v_ptr, n, t, lr, b1, b2, eps, stream=0):
     return lib().smat_mlp_adam(p_ptr, g_ptr, m_ptr, v_ptr, n, t, lr, b1, b2, eps, stream)
+
+
+def smat_spmv_csr_merge_noalloc(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dtype, alpha_ptr, x_ptr, beta_ptr,
+                                y_ptr, stream=0):
+    """Merge-path CSR product with no allocation (see include/smat.h)."""
+    return lib().smat_spmv_csr_merge_noalloc(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dtype, alpha_ptr, x_ptr,
+                                             beta_ptr, y_ptr, stream)
 
 
 def smat_cast_f64_to_f32(in_ptr, out_ptr, n, stream=0):

@@ -723,3 +723,96 @@ cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const v
 }
 
 }  // namespace smat
+
+// ---------------------------------------------------------------------------
+// Merge-path CSR SpMV that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a solver that runs under a memory
+// manager owning every device byte, code that must not synchronise the device
+// (cudaMalloc/cudaFree may), or a host whose allocation calls are forbidden
+// once its time-critical loop has started.  For them this entry point keeps
+// the only scratch the kernel needs -- one carry (row, partial sum) per tile
+// -- in a fixed array in the library's own device memory.  Every GPU that
+// loads the library holds that array (768 KiB) until the process exits.
+// The array's address is looked up once per device, on the first call made
+// with that device current; make that first call before any stream capture.
+// All calls share the array, so calls whose kernels overlap on the GPU race:
+// order them on one stream, or synchronise between them.  Nothing in the
+// array has to start at zero: each call writes every carry it later reads.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace smat {
+namespace {
+
+constexpr long long NOALLOC_MAX_TILES = 65536;
+// per tile: an int32 row (256 KiB in all) and a value of up to 8 bytes (512 KiB)
+constexpr size_t NOALLOC_ROW_BYTES = NOALLOC_MAX_TILES * 4;
+constexpr size_t NOALLOC_BYTES = NOALLOC_ROW_BYTES + NOALLOC_MAX_TILES * 8;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array for the current device (looked up once).
+cudaError_t noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename V>
+cudaError_t merge_noalloc_typed(long long m, long long nnz, const int32_t *rowptr, const int32_t *colidx,
+                                const void *vals, const void *alpha_p, const void *x_p, const void *beta_p,
+                                void *y_p, unsigned char *scratch, cudaStream_t s) {
+  typedef typename Compute<V>::T T;
+  const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
+  const long long tiles = (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+  int32_t *crow = (int32_t *)scratch;
+  T *cval = (T *)(scratch + NOALLOC_ROW_BYTES);
+  csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
+      rowptr, colidx, (const V *)vals, (const T *)x_p, alpha, beta, (T *)y_p, m, nnz, crow, cval);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || tiles <= 1) return e;
+  carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, (T *)y_p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace smat
+
+extern "C" smat_status_t smat_spmv_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                                                     const int32_t *colidx, const void *vals, smat_dtype_t dtype,
+                                                     const void *alpha, const void *x, const void *beta, void *y,
+                                                     void *stream) {
+  using namespace smat;
+  if (m < 0 || n < 0 || nnz < 0 || !alpha || !beta) return SMAT_ERR_INVALID_ARG;
+  if (dtype != SMAT_F64 && dtype != SMAT_F32 && dtype != SMAT_BF16) return SMAT_ERR_INVALID_ARG;
+  if (m == 0) return SMAT_OK;
+  if (!rowptr || !y || (nnz > 0 && (!colidx || !vals || !x))) return SMAT_ERR_INVALID_ARG;
+  if (m > INT32_MAX - 1 || n > INT32_MAX || nnz > INT32_MAX) return SMAT_ERR_UNSUPPORTED;
+  const long long tiles = (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+  if (tiles > NOALLOC_MAX_TILES) return SMAT_ERR_UNSUPPORTED;  // beyond the fixed scratch
+  void *scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return SMAT_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *sc = (unsigned char *)scratch;
+  switch (dtype) {
+    case SMAT_F64: e = merge_noalloc_typed<double>(m, nnz, rowptr, colidx, vals, alpha, x, beta, y, sc, s); break;
+    case SMAT_F32: e = merge_noalloc_typed<float>(m, nnz, rowptr, colidx, vals, alpha, x, beta, y, sc, s); break;
+    default: e = merge_noalloc_typed<__nv_bfloat16>(m, nnz, rowptr, colidx, vals, alpha, x, beta, y, sc, s); break;
+  }
+  return e == cudaSuccess ? SMAT_OK : SMAT_ERR_CUDA;
+}
