@@ -255,6 +255,47 @@ smat_status_t smat_mlp_adam(float *p, const float *g, float *m, float *v, int64_
                             float lr, float beta1, float beta2, float eps, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Mixed-precision conjugate gradients (iterative refinement)               */
+/* The paper measures SpMV in single and double precision (Sec. 7.2) and     */
+/* motivates the library by solvers that call it hundreds of times (Sec. 1,  */
+/* Sec. 7.3, Eq. "num_iter").                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double rtol;             /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64 residual) */
+  int32_t max_outer;       /* refinement steps                                  */
+  int32_t max_inner;       /* inner CG iterations per refinement step          */
+  float inner_rtol;        /* inner CG stops when ||res|| <= inner_rtol ||res_0|| */
+  int32_t max_total_inner; /* cap on all inner iterations together (0 = none)  */
+  int32_t check_every;     /* inner iterations between host convergence checks */
+  int32_t use_graph;       /* replay chunks of inner iterations from a CUDA graph */
+} smat_cg_opts_t;
+
+typedef struct {
+  int32_t outer;        /* refinement steps taken                                */
+  int32_t inner_total;  /* inner CG iterations taken                             */
+  double relres;        /* final ||b - A x||_2 / ||b||_2, computed in FP64       */
+  double seconds;       /* wall time of the call                                 */
+  int32_t converged;    /* relres <= rtol                                        */
+} smat_cg_info_t;
+
+/* rtol 1e-10, max_outer 50, max_inner 500, inner_rtol 1e-4, no total cap,
+ * check_every 10, use_graph 1. */
+void smat_cg_opts_default(smat_cg_opts_t *opts);
+
+/* Solve A x = b for symmetric positive definite A.  a64 is an SMAT_F64 handle
+ * of A (its plan forms the residual r = b - A x in FP64); a32 is an SMAT_F32
+ * or SMAT_BF16 handle of the same matrix (its plan runs the inner FP32 CG on
+ * A d = r / ||r||); both should be tuned.  Each refinement step updates
+ * x += ||r|| d in FP64.  b[n] and x[n] are DEVICE FP64 arrays; x holds the
+ * initial guess on entry and the solution on return.  opts may be NULL.
+ * Work runs on a private stream ordered after `stream`; the call returns
+ * when the solve has finished.  Returns SMAT_ERR_NOT_CONVERGED (with *info
+ * filled) when a limit stops it first; INVALID_ARG for a non-square matrix or
+ * wrong handle dtypes.  Workspace: 8n + 16n bytes, allocated per call. */
+smat_status_t smat_cg_mixed(smat_handle_t a64, smat_handle_t a32, const double *b, double *x,
+                            const smat_cg_opts_t *opts, smat_cg_info_t *info, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Value casts for reduced-precision storage (device arrays, n elements)    */
 /* ------------------------------------------------------------------------ */
 /* FP64 -> FP32, round to nearest even. */

@@ -57,6 +57,17 @@ class smat_tune_opts_t(ctypes.Structure):
                 ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32)]
 
 
+class smat_cg_opts_t(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_float), ("max_total_inner", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class smat_cg_info_t(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("inner_total", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("converged", ctypes.c_int32)]
+
+
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 _SIGS = {
     "smat_tune_opts_default": (None, [ctypes.POINTER(smat_tune_opts_t)]),
@@ -85,6 +96,9 @@ _SIGS = {
                                      ctypes.c_float, ctypes.c_float, _VP]),
     "smat_spmv_csr_merge_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP,
                                                    _VP, _VP]),
+    "smat_cg_opts_default": (None, [ctypes.POINTER(smat_cg_opts_t)]),
+    "smat_cg_mixed": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(smat_cg_opts_t),
+                                     ctypes.POINTER(smat_cg_info_t), _VP]),
     "smat_cast_f64_to_f32": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "smat_cast_f64_to_bf16": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
 }
@@ -239,6 +253,32 @@ def smat_spmv_csr_merge_noalloc(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dty
                                              beta_ptr, y_ptr, stream)
 
 
+def smat_cg_opts_default() -> smat_cg_opts_t:
+    o = smat_cg_opts_t()
+    lib().smat_cg_opts_default(ctypes.byref(o))
+    return o
+
+
+def smat_cg_mixed(a64, a32, b_ptr, x_ptr, opts: smat_cg_opts_t | None = None, stream=0):
+    """Returns (status, smat_cg_info_t)."""
+    info = smat_cg_info_t()
+    st = lib().smat_cg_mixed(a64, a32, b_ptr, x_ptr, ctypes.byref(opts) if opts is not None else None,
+                             ctypes.byref(info), stream)
+    return st, info
+
+
+def cg_mixed(A64: "SpMatrix", A32: "SpMatrix", b, x, stream=None, **opts):
+    """Mixed-precision CG on device FP64 tensors b and x (x: initial guess, overwritten)."""
+    o = smat_cg_opts_default()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    st, info = smat_cg_mixed(A64.h, A32.h, b.data_ptr(), x.data_ptr(), o, _stream_ptr(stream))
+    if st not in (SMAT_OK, SMAT_ERR_NOT_CONVERGED):
+        _check(st, "smat_cg_mixed")
+    return {"status": st, "outer": info.outer, "inner_total": info.inner_total, "relres": info.relres,
+            "seconds": info.seconds, "converged": bool(info.converged)}
+
+
 def smat_cast_f64_to_f32(in_ptr, out_ptr, n, stream=0):
     return lib().smat_cast_f64_to_f32(in_ptr, out_ptr, n, stream)
 
@@ -254,6 +294,19 @@ def write_model(path, params, mean, std):
         f.write(struct.pack("<i", 1))
         for a in (mean, std, params):
             f.write(np.ascontiguousarray(a, dtype="<f4").tobytes())
+
+
+def read_model(path):
+    """(params[5512], mean[12], std[12]) from a model file (see write_model)."""
+    with open(path, "rb") as f:
+        assert f.read(8) == b"SMATMLP1" and struct.unpack("<i", f.read(4))[0] == 1
+        a = np.frombuffer(f.read(), dtype="<f4")
+    assert a.size == 24 + SMAT_MLP_PARAMS
+    return a[24:].copy(), a[:12].copy(), a[12:24].copy()
+
+
+MODEL_PATH = os.path.join(_PKG, "selector_mlp.bin")
+DATASET_PATH = os.path.join(_PKG, "selector_dataset.jsonl")
 
 
 # ---------------------------------------------------------------------------
