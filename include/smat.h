@@ -255,6 +255,49 @@ smat_status_t smat_mlp_adam(float *p, const float *g, float *m, float *v, int64_
                             float lr, float beta1, float beta2, float eps, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched products: many matrices in one persistent launch                  */
+/* The paper motivates adaptivity with algebraic multigrid, whose levels are */
+/* different matrices used in turn, so one format does not fit them all     */
+/* (Sec. 1).                                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t tile_scale;   /* tile size multiplier; 0 = autotune over {1,2,4,8}     */
+  int32_t ctas_per_sm;  /* resident CTAs per SM; 0 = autotune over {2,4,8}       */
+  int32_t trial_reps;   /* timed graph launches per autotuning candidate       */
+} smat_batch_opts_t;
+
+typedef struct {
+  int32_t count, tiles, grid, tile_scale, ctas_per_sm;
+  double tuned_ms;      /* median time of one batched product while tuning     */
+} smat_batch_info_t;
+
+void smat_batch_opts_default(smat_batch_opts_t *opts);
+
+/* Group `count` handles of one storage dtype.  The handles stay owned by the
+ * caller and must outlive the batch; tune each first (each keeps its plan's
+ * format: CSR kernels map to 1/4/8/32 lanes per row, merge-path and COO plans
+ * to the fastest measured CSR row kernel, ELL and DIA stay ELL and DIA). */
+smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int32_t count);
+
+/* Build the work table (row tiles of every product, largest first), capture
+ * the persistent launch in a CUDA graph and autotune tile size and CTAs per
+ * SM by timing the graph.  Returns after `stream` has finished.  Must run
+ * again if a member handle is re-tuned. */
+smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, void *stream);
+
+/* y_i = alpha_i A_i x_i + beta_i y_i for every member i in one graph launch on
+ * `stream`.  alphas / betas: HOST arrays of `count` scalars of the compute
+ * type; xs / ys: HOST arrays of `count` DEVICE pointers.  Descriptors are
+ * re-uploaded only when a pointer or scalar changed.  Asynchronous. */
+smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *const *xs, const void *betas,
+                              void *const *ys, void *stream);
+
+smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info);
+
+/* Free the batch (not its handles).  NULL is a no-op. */
+smat_status_t smat_batch_destroy(smat_batch_t b);
+
+/* ------------------------------------------------------------------------ */
 /* Mixed-precision conjugate gradients (iterative refinement)               */
 /* The paper measures SpMV in single and double precision (Sec. 7.2) and     */
 /* motivates the library by solvers that call it hundreds of times (Sec. 1,  */

@@ -68,6 +68,15 @@ class smat_cg_info_t(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("converged", ctypes.c_int32)]
 
 
+class smat_batch_opts_t(ctypes.Structure):
+    _fields_ = [("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("trial_reps", ctypes.c_int32)]
+
+
+class smat_batch_info_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("tiles", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
+
+
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 _SIGS = {
     "smat_tune_opts_default": (None, [ctypes.POINTER(smat_tune_opts_t)]),
@@ -96,6 +105,12 @@ _SIGS = {
                                      ctypes.c_float, ctypes.c_float, _VP]),
     "smat_spmv_csr_merge_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP,
                                                    _VP, _VP]),
+    "smat_batch_opts_default": (None, [ctypes.POINTER(smat_batch_opts_t)]),
+    "smat_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I32]),
+    "smat_batch_tune": (ctypes.c_int, [_VP, ctypes.POINTER(smat_batch_opts_t), _VP]),
+    "smat_batch_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(smat_batch_info_t)]),
+    "smat_batch_destroy": (ctypes.c_int, [_VP]),
     "smat_cg_opts_default": (None, [ctypes.POINTER(smat_cg_opts_t)]),
     "smat_cg_mixed": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(smat_cg_opts_t),
                                      ctypes.POINTER(smat_cg_info_t), _VP]),
@@ -251,6 +266,57 @@ def smat_spmv_csr_merge_noalloc(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dty
     """Merge-path CSR product with no allocation (see include/smat.h)."""
     return lib().smat_spmv_csr_merge_noalloc(m, n, nnz, rowptr_ptr, colidx_ptr, vals_ptr, dtype, alpha_ptr, x_ptr,
                                              beta_ptr, y_ptr, stream)
+
+
+def smat_batch_opts_default() -> smat_batch_opts_t:
+    o = smat_batch_opts_t()
+    lib().smat_batch_opts_default(ctypes.byref(o))
+    return o
+
+
+class Batch:
+    """Several SpMatrix handles multiplied in one persistent launch (graph)."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (_VP * len(self.mats))(*[m.h for m in self.mats])
+        b = _VP()
+        _check(lib().smat_batch_create(ctypes.byref(b), arr, len(self.mats)), "smat_batch_create")
+        self.b = b.value
+        self.dtype = self.mats[0].dtype
+
+    def tune(self, stream=None, **opts):
+        o = smat_batch_opts_default()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        _check(lib().smat_batch_tune(self.b, ctypes.byref(o), _stream_ptr(stream)), "smat_batch_tune")
+        return self
+
+    def spmv(self, xs, ys, alphas=None, betas=None, stream=None):
+        n = len(self.mats)
+        ct = ctypes.c_double if self.dtype == "f64" else ctypes.c_float
+        a = (ct * n)(*(alphas if alphas is not None else [1.0] * n))
+        b = (ct * n)(*(betas if betas is not None else [0.0] * n))
+        xp = (_VP * n)(*[x.data_ptr() for x in xs])
+        yp = (_VP * n)(*[y.data_ptr() for y in ys])
+        _check(lib().smat_batch_spmv(self.b, a, xp, b, yp, _stream_ptr(stream)), "smat_batch_spmv")
+        return ys
+
+    def info(self) -> dict:
+        i = smat_batch_info_t()
+        _check(lib().smat_batch_get_info(self.b, ctypes.byref(i)), "smat_batch_get_info")
+        return {n: getattr(i, n) for n, _ in smat_batch_info_t._fields_}
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().smat_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def smat_cg_opts_default() -> smat_cg_opts_t:

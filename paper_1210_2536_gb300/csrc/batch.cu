@@ -1,0 +1,424 @@
+// Batched SpMV: many matrices of uneven size in one persistent launch.
+//
+// The paper motivates input adaptivity with algebraic multigrid, whose levels
+// are different sparse matrices used one after another (Sec. 1): no single
+// format fits all levels, and the coarse levels are far too small to fill a
+// GPU on their own.  Here every matrix keeps the format its own tuning chose
+// (CSR with 1/4/8/32 lanes per row, ELL or DIA); the products are cut into row
+// tiles, sorted largest first into one work table, and a persistent grid
+// takes tiles from an atomic counter until the table is empty.  The counter
+// reset and the kernel are captured once in a CUDA graph, so one product of
+// the whole batch is one graph launch.  An autotuner picks the tile size and
+// the number of resident CTAs per SM by timing the captured graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "smat_internal.h"
+#include "spmv_device.cuh"
+
+namespace smat {
+namespace {
+
+enum : int { KIND_CSR = 0, KIND_ELL = 1, KIND_DIA = 2 };
+
+struct BatchMat {
+  int kind, W, nd, pad;
+  long long m, n, K, P;
+  const int32_t *rowptr, *colidx;
+  const void *val;
+  const int32_t *ecol;
+  const void *eval;
+  const int32_t *doff;
+  const void *dval;
+  const void *x;
+  void *y;
+  double alpha, beta;
+};
+
+struct BatchTile {
+  int mat, row0, row1, pad;
+};
+
+constexpr int BNT = 256;
+
+// Rows [row0, row1) of a CSR product with W lanes per row (W = 1: one thread
+// per row).  The loop bound is uniform over the block, so shuffles see every
+// lane.
+template <typename V, typename T, int W>
+__device__ __forceinline__ void csr_rows(const BatchMat &M, T alpha, T beta, long long row0, long long row1) {
+  const int32_t *__restrict__ rowptr = M.rowptr;
+  const int32_t *__restrict__ col = M.colidx;
+  const V *__restrict__ val = (const V *)M.val;
+  const T *__restrict__ x = (const T *)M.x;
+  T *__restrict__ y = (T *)M.y;
+  constexpr int RPB = BNT / W;
+  constexpr int B = W == 1 ? 8 : 4;
+  const int sub = threadIdx.x % W;
+  for (long long base = row0; base < row1; base += RPB) {
+    const long long row = base + threadIdx.x / W;
+    T acc = 0;
+    if (row < row1) {
+      const int s = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+      for (int k = s + sub; k < e; k += B * W) {
+        int c[B];
+        T v[B], xv[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          c[u] = k + u * W < e ? ld_idx(col + k + u * W) : 0;
+          v[u] = k + u * W < e ? (T)ld_val(val + k + u * W) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) xv[u] = k + u * W < e ? __ldg(x + c[u]) : (T)0;
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+          if (k + u * W < e) acc = fused(acc, v[u], xv[u]);
+      }
+    }
+    if (W > 1) {
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, W);
+    }
+    if (sub == 0 && row < row1) y[row] = epilogue(acc, alpha, beta, y, row);
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BNT) batch_kernel(const BatchMat *__restrict__ mats,
+                                                    const BatchTile *__restrict__ tiles, int ntiles,
+                                                    unsigned int *counter) {
+  typedef typename Compute<V>::T T;
+  constexpr int R = 16 / (int)sizeof(V);
+  __shared__ int s_t;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();  // every thread has read s_t before it is overwritten
+    if (t >= ntiles) return;
+    const BatchTile tl = tiles[t];
+    const BatchMat &M = mats[tl.mat];
+    const T alpha = (T)M.alpha, beta = (T)M.beta;
+    if (M.kind == KIND_ELL) {
+      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+        ell_group<V, R>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, alpha, beta, (T *)M.y, M.m, i0);
+    } else if (M.kind == KIND_DIA) {
+      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+        dia_group<V, R>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, alpha, beta, (T *)M.y, M.m, M.n,
+                        i0);
+    } else {
+      switch (M.W) {
+        case 1: csr_rows<V, T, 1>(M, alpha, beta, tl.row0, tl.row1); break;
+        case 4: csr_rows<V, T, 4>(M, alpha, beta, tl.row0, tl.row1); break;
+        case 8: csr_rows<V, T, 8>(M, alpha, beta, tl.row0, tl.row1); break;
+        default: csr_rows<V, T, 32>(M, alpha, beta, tl.row0, tl.row1); break;
+      }
+    }
+  }
+}
+
+cudaError_t launch_batch_kernel(smat_dtype_t dt, int grid, const BatchMat *mats, const BatchTile *tiles, int ntiles,
+                                unsigned int *counter, cudaStream_t s) {
+  switch (dt) {
+    case SMAT_F64: batch_kernel<double><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+    case SMAT_F32: batch_kernel<float><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+    default: batch_kernel<__nv_bfloat16><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace smat
+
+struct smat_batch_s {
+  std::vector<smat_handle_t> hs;
+  smat_dtype_t dtype = SMAT_F64;
+  std::vector<smat::BatchMat> mats;        // host copy of the descriptors
+  std::vector<std::vector<int32_t>> rowptrs;  // CSR members: row pointers for nnz-balanced tiles
+  smat::BatchMat *d_mats = nullptr;
+  smat::BatchTile *d_tiles = nullptr;
+  unsigned int *d_counter = nullptr;
+  int ntiles = 0, grid = 0, tile_scale = 0, ctas_per_sm = 0;
+  double tuned_ms = -1.0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ready = false;
+};
+
+namespace smat {
+namespace {
+
+smat_status_t st_of(cudaError_t e) {
+  if (e == cudaSuccess) return SMAT_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SMAT_ERR_ALLOC;
+  }
+  return SMAT_ERR_CUDA;
+}
+
+#define BTRY(call)                    \
+  do {                                \
+    smat_status_t _s = st_of(call);   \
+    if (_s != SMAT_OK) return _s;     \
+  } while (0)
+
+int csr_width(const smat_s *h) {
+  switch (h->variant) {
+    case SMAT_V_CSR_SCALAR: return 1;
+    case SMAT_V_CSR_VEC4: return 4;
+    case SMAT_V_CSR_VEC8: return 8;
+    case SMAT_V_CSR_VEC32: return 32;
+  }
+  // merge-path / COO plans: the fastest measured CSR row kernel, else by mean row length
+  int best = -1;
+  float bt = 1e30f;
+  const int ws[4] = {1, 4, 8, 32};
+  for (int v = SMAT_V_CSR_SCALAR; v <= SMAT_V_CSR_VEC32; ++v)
+    if (h->timings[v] > 0 && h->timings[v] < bt) { bt = h->timings[v]; best = ws[v]; }
+  if (best > 0) return best;
+  const double a = h->have_features ? h->f.aver_rd : 8.0;
+  return a < 8.0 ? 4 : (a < 24.0 ? 8 : 32);
+}
+
+void free_graph(smat_batch_s *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Work table for a tile scale: CSR tiles hold about 2048*scale stored entries
+// (whole rows, so one long row is a tile of its own); ELL/DIA tiles hold
+// 256*R*scale rows.  Sorted by estimated work, largest first.
+std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
+  struct Est { BatchTile t; long long w; };
+  std::vector<Est> v;
+  const int R = 16 / elem_size(b->dtype);
+  for (size_t i = 0; i < b->mats.size(); ++i) {
+    const BatchMat &M = b->mats[i];
+    if (M.m == 0) continue;
+    if (M.kind == KIND_CSR) {
+      const std::vector<int32_t> &rp = b->rowptrs[i];
+      const long long target = 2048LL * scale;
+      long long r0 = 0;
+      while (r0 < M.m) {
+        long long r1 = r0;
+        const long long cap_rows = 8192LL * scale;
+        while (r1 < M.m && (long long)rp[r1] - rp[r0] < target && r1 - r0 < cap_rows) ++r1;
+        if (r1 == r0) ++r1;
+        v.push_back({{(int)i, (int)r0, (int)r1, 0}, (long long)rp[r1] - rp[r0] + (r1 - r0)});
+        r0 = r1;
+      }
+    } else {
+      const long long rows = (long long)BNT * R * scale;
+      const long long per_row = M.kind == KIND_ELL ? M.K : M.nd;
+      for (long long r0 = 0; r0 < M.m; r0 += rows) {
+        long long r1 = std::min(M.m, r0 + rows);
+        v.push_back({{(int)i, (int)r0, (int)r1, 0}, (r1 - r0) * (per_row + 1)});
+      }
+    }
+  }
+  std::stable_sort(v.begin(), v.end(), [](const Est &a, const Est &c) { return a.w > c.w; });
+  std::vector<BatchTile> out;
+  out.reserve(v.size());
+  for (auto &e : v) out.push_back(e.t);
+  return out;
+}
+
+smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
+  free_graph(b);
+  dev_free(b->d_tiles);
+  b->d_tiles = nullptr;
+  std::vector<BatchTile> tiles = make_tiles(b, scale);
+  b->ntiles = (int)tiles.size();
+  if (b->ntiles > 0) {
+    void *p = nullptr;
+    BTRY(dev_alloc(&p, tiles.size() * sizeof(BatchTile)));
+    b->d_tiles = (BatchTile *)p;
+    BTRY(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = std::max(1, std::min(sms * ctas_per_sm, std::max(b->ntiles, 1)));
+  b->tile_scale = scale;
+  b->ctas_per_sm = ctas_per_sm;
+  // capture: reset the tile counter, run the persistent kernel
+  BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->cap);
+  cudaError_t e2 = b->ntiles > 0 ? launch_batch_kernel(b->dtype, b->grid, b->d_mats, b->d_tiles, b->ntiles,
+                                                        b->d_counter, b->cap)
+                                  : cudaSuccess;
+  cudaError_t e3 = cudaStreamEndCapture(b->cap, &b->graph);
+  BTRY(e1);
+  BTRY(e2);
+  BTRY(e3);
+  BTRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  b->ready = true;
+  return SMAT_OK;
+}
+
+}  // namespace
+}  // namespace smat
+
+using namespace smat;
+
+extern "C" {
+
+smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int32_t count) {
+  if (!out || !hs || count <= 0) return SMAT_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return SMAT_ERR_INVALID_ARG;
+    if (hs[i]->dtype != hs[0]->dtype) return SMAT_ERR_INVALID_ARG;
+  }
+  smat_batch_s *b = new (std::nothrow) smat_batch_s();
+  if (!b) return SMAT_ERR_ALLOC;
+  b->hs.assign(hs, hs + count);
+  b->dtype = hs[0]->dtype;
+  auto fail = [&](smat_status_t s) { smat_batch_destroy(b); return s; };
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(SMAT_ERR_CUDA);
+  void *p = nullptr;
+  if ((e = dev_alloc(&p, sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
+  b->d_counter = (unsigned int *)p;
+  if ((e = dev_alloc(&p, sizeof(BatchMat) * (size_t)count)) != cudaSuccess) return fail(st_of(e));
+  b->d_mats = (BatchMat *)p;
+  *out = b;
+  return SMAT_OK;
+}
+
+smat_status_t smat_batch_destroy(smat_batch_t b) {
+  if (!b) return SMAT_OK;
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  free_graph(b);
+  dev_free(b->d_tiles);
+  dev_free(b->d_mats);
+  dev_free(b->d_counter);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return SMAT_OK;
+}
+
+smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, void *stream) {
+  if (!b) return SMAT_ERR_INVALID_ARG;
+  smat_batch_opts_t o;
+  if (opts) o = *opts; else smat_batch_opts_default(&o);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = (int)b->hs.size();
+  b->mats.assign((size_t)n, BatchMat{});
+  b->rowptrs.assign((size_t)n, {});
+  const int tsz = b->dtype == SMAT_F64 ? 8 : 4;
+  // per-matrix descriptors from each handle's plan, with scratch x / y for timing
+  std::vector<void *> tmp;
+  struct Free { std::vector<void *> &v; ~Free() { for (void *p : v) dev_free(p); } } guard{tmp};
+  for (int i = 0; i < n; ++i) {
+    smat_s *h = b->hs[(size_t)i];
+    BatchMat &M = b->mats[(size_t)i];
+    M.m = h->m; M.n = h->n; M.P = h->P;
+    if (h->variant == SMAT_V_ELL && h->ell_val) {
+      M.kind = KIND_ELL; M.ecol = h->ell_col; M.eval = h->ell_val; M.K = h->ell_K;
+    } else if (h->variant == SMAT_V_DIA && h->dia_val) {
+      M.kind = KIND_DIA; M.doff = h->dia_off; M.dval = h->dia_val; M.nd = (int)h->dia_nd;
+    } else {
+      M.kind = KIND_CSR; M.W = csr_width(h); M.rowptr = h->rowptr; M.colidx = h->colidx; M.val = h->val;
+      b->rowptrs[(size_t)i].resize((size_t)h->m + 1);
+      BTRY(cudaMemcpy(b->rowptrs[(size_t)i].data(), h->rowptr, (size_t)(h->m + 1) * 4, cudaMemcpyDeviceToHost));
+    }
+    void *x = nullptr, *y = nullptr;
+    BTRY(dev_alloc(&x, (size_t)std::max<int64_t>(h->n, 1) * tsz));
+    tmp.push_back(x);
+    BTRY(dev_alloc(&y, (size_t)std::max<int64_t>(h->m, 1) * tsz));
+    tmp.push_back(y);
+    BTRY(cudaMemsetAsync(x, 0, (size_t)std::max<int64_t>(h->n, 1) * tsz, s));
+    M.x = x; M.y = y; M.alpha = 1.0; M.beta = 0.0;
+  }
+  BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
+  BTRY(cudaStreamSynchronize(s));
+  // autotune: tile scale x resident CTAs per SM, timed as the captured graph
+  std::vector<int> scales, ctas;
+  if (o.tile_scale > 0) scales.push_back(o.tile_scale); else scales = {1, 2, 4, 8};
+  if (o.ctas_per_sm > 0) ctas.push_back(o.ctas_per_sm); else ctas = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  BTRY(cudaEventCreate(&e0));
+  BTRY(cudaEventCreate(&e1));
+  struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
+  double best = 1e30;
+  int best_s = scales[0], best_c = ctas[0];
+  const int reps = std::max(1, o.trial_reps);
+  for (int sc : scales) {
+    for (int cp : ctas) {
+      {
+        smat_status_t st = build_plan(b, sc, cp);
+        if (st != SMAT_OK) return st;
+      }
+      for (int w = 0; w < 2; ++w) BTRY(cudaGraphLaunch(b->exec, s));
+      std::vector<float> ms((size_t)reps);
+      for (int r = 0; r < reps; ++r) {
+        BTRY(cudaEventRecord(e0, s));
+        BTRY(cudaGraphLaunch(b->exec, s));
+        BTRY(cudaEventRecord(e1, s));
+        BTRY(cudaEventSynchronize(e1));
+        BTRY(cudaEventElapsedTime(&ms[(size_t)r], e0, e1));
+      }
+      std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
+      const double med = ms[(size_t)reps / 2];
+      if (med < best) { best = med; best_s = sc; best_c = cp; }
+    }
+  }
+  smat_status_t st = build_plan(b, best_s, best_c);
+  if (st != SMAT_OK) return st;
+  b->tuned_ms = best;
+  // forget the timing buffers: the next smat_batch_spmv installs the caller's vectors
+  for (auto &M : b->mats) { M.x = nullptr; M.y = nullptr; }
+  BTRY(cudaStreamSynchronize(s));
+  return SMAT_OK;
+}
+
+smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *const *xs, const void *betas,
+                              void *const *ys, void *stream) {
+  if (!b || !alphas || !betas || !xs || !ys) return SMAT_ERR_INVALID_ARG;
+  if (!b->ready) return SMAT_ERR_UNSUPPORTED;
+  const int n = (int)b->hs.size();
+  bool changed = false;
+  for (int i = 0; i < n; ++i) {
+    BatchMat &M = b->mats[(size_t)i];
+    const double a = b->dtype == SMAT_F64 ? ((const double *)alphas)[i] : (double)((const float *)alphas)[i];
+    const double c = b->dtype == SMAT_F64 ? ((const double *)betas)[i] : (double)((const float *)betas)[i];
+    if ((M.m > 0 && !ys[i]) || (M.n > 0 && M.m > 0 && !xs[i])) return SMAT_ERR_INVALID_ARG;
+    if (M.x != xs[i] || M.y != ys[i] || M.alpha != a || M.beta != c) {
+      M.x = xs[i]; M.y = ys[i]; M.alpha = a; M.beta = c;
+      changed = true;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (changed)
+    BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
+  BTRY(cudaGraphLaunch(b->exec, s));
+  return SMAT_OK;
+}
+
+smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info) {
+  if (!b || !info) return SMAT_ERR_INVALID_ARG;
+  info->count = (int32_t)b->hs.size();
+  info->tiles = b->ntiles;
+  info->grid = b->grid;
+  info->tile_scale = b->tile_scale;
+  info->ctas_per_sm = b->ctas_per_sm;
+  info->tuned_ms = b->tuned_ms;
+  return SMAT_OK;
+}
+
+void smat_batch_opts_default(smat_batch_opts_t *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tile_scale = 0;
+  o->ctas_per_sm = 0;
+  o->trial_reps = 10;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// Device-side building blocks of the SpMV kernels, shared by the single-
+// matrix kernels (spmv.cu) and the batched persistent kernel (batch.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace smat {
+namespace {
+
+template <typename V> struct Compute { typedef float T; };
+template <> struct Compute<double> { typedef double T; };
+
+// Matrix arrays are read once per product: load them with the streaming
+// (evict-first) policy so that x, which every product gathers from, stays in L2.
+__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) {
+  return __uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short *>(p)) << 16);
+}
+__device__ __forceinline__ int ld_idx(const int32_t *p) { return __ldcs(p); }
+
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// acc + v*x.  GB300 executes FP64 arithmetic at about 2 operations per clock
+// per SM, so FP64 SpMV is bound by the FP64 pipe about as much as by HBM:
+// every kernel spends exactly one fused multiply-add per stored product.
+// The EXACT flavour (CSR-scalar only) instead rounds the product and the sum
+// separately, in ascending column order -- the CSR definition operation for
+// operation -- at twice the FP64 cost.
+__device__ __forceinline__ double fused(double acc, double v, double x) { return fma(v, x, acc); }
+__device__ __forceinline__ float fused(float acc, float v, float x) { return fmaf(v, x, acc); }
+template <bool EXACT>
+__device__ __forceinline__ double madd(double acc, double v, double x) {
+  return EXACT ? __dadd_rn(acc, __dmul_rn(v, x)) : fma(v, x, acc);
+}
+template <bool EXACT>
+__device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf(v, x, acc); }
+
+// y_i = alpha*acc (+ beta*y_i).  alpha == 1 skips the multiply (exact);
+// beta != 0 folds beta*y_i into one fused multiply-add unless EXACT.
+template <typename T, bool EXACT = false>
+__device__ __forceinline__ T epilogue(T acc, T alpha, T beta, const T *y, long long i) {
+  const T ax = alpha == (T)1 ? acc : mul_rn(alpha, acc);
+  if (beta == (T)0) return ax;
+  if (EXACT) return add_rn(ax, mul_rn(beta, y[i]));
+  return fused(ax, beta, y[i]);
+}
+
+// 16-byte vector loads of R consecutive values (R * sizeof(V) == 16) and of
+// R consecutive column indices.
+template <typename V, int R> struct VecOf;
+template <> struct VecOf<double, 2> { typedef double2 T; };
+template <> struct VecOf<float, 4> { typedef float4 T; };
+template <> struct VecOf<__nv_bfloat16, 8> { typedef uint4 T; };
+
+template <typename V, int R>
+__device__ __forceinline__ void load_vals(const V *p, typename Compute<V>::T (&out)[R]);
+template <>
+__device__ __forceinline__ void load_vals<double, 2>(const double *p, double (&out)[2]) {
+  double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
+  out[0] = v.x; out[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load_vals<float, 4>(const float *p, float (&out)[4]) {
+  float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_vals<__nv_bfloat16, 8>(const __nv_bfloat16 *p, float (&out)[8]) {
+  uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
+  unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    out[2 * q] = __uint_as_float(w[q] << 16);
+    out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_cols(const int32_t *p, int (&c)[R]) {
+  if constexpr (R == 2) {
+    int2 v = __ldcs(reinterpret_cast<const int2 *>(p));
+    c[0] = v.x; c[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      int4 v = __ldcs(reinterpret_cast<const int4 *>(p) + q);
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+  }
+}
+
+// y[i0 .. i0+R) from R accumulators: one vector store (and load when beta != 0)
+// for full groups, scalar at the tail.
+template <typename T, int R> struct YVec;
+template <> struct YVec<double, 2> {
+  static __device__ __forceinline__ void ld(const double *p, double (&o)[2]) { double2 v = *reinterpret_cast<const double2 *>(p); o[0] = v.x; o[1] = v.y; }
+  static __device__ __forceinline__ void st(double *p, const double (&o)[2]) { *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]); }
+};
+template <> struct YVec<float, 4> {
+  static __device__ __forceinline__ void ld(const float *p, float (&o)[4]) { float4 v = *reinterpret_cast<const float4 *>(p); o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  static __device__ __forceinline__ void st(float *p, const float (&o)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct YVec<float, 8> {
+  static __device__ __forceinline__ void ld(const float *p, float (&o)[8]) {
+    float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+  }
+  static __device__ __forceinline__ void st(float *p, const float (&o)[8]) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
+  }
+};
+
+template <typename T, int R>
+__device__ __forceinline__ void write_rows(T *__restrict__ y, long long i0, long long m, const T (&acc)[R], T alpha,
+                                           T beta) {
+  if (i0 + R <= m) {
+    T out[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = alpha == (T)1 ? acc[r] : mul_rn(alpha, acc[r]);
+    if (beta != (T)0) {
+      T yo[R];
+      YVec<T, R>::ld(y + i0, yo);
+#pragma unroll
+      for (int r = 0; r < R; ++r) out[r] = fused(out[r], beta, yo[r]);
+    }
+    YVec<T, R>::st(y + i0, out);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+  }
+}
+
+// One thread's R consecutive rows [i0, i0 + R) of an ELL product
+// (column-major, pitch P, K slots).  16/R slots are loaded before their
+// gathers are issued; padding (column -1) is dropped.
+template <typename V, int R>
+__device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, const V *__restrict__ eval, long long P,
+                                          long long K, const typename Compute<V>::T *__restrict__ x,
+                                          typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                          typename Compute<V>::T *__restrict__ y, long long m, long long i0) {
+  typedef typename Compute<V>::T T;
+  constexpr int U = 16 / R;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+  for (long long q = 0; q < K; q += U) {
+    T v[U][R], xv[U][R];
+    int c[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (q + u < K) {
+        load_vals<V, R>(eval + (q + u) * P + i0, v[u]);
+        load_cols<R>(ecol + (q + u) * P + i0, c[u]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) { v[u][r] = 0; c[u][r] = -1; }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) xv[u][r] = c[u][r] >= 0 ? __ldg(x + c[u][r]) : (T)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (c[u][r] >= 0) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+  }
+  write_rows<T, R>(y, i0, m, acc, alpha, beta);
+}
+
+// One thread's R consecutive rows of a DIA product; `off` holds the nd
+// ascending diagonal offsets (shared or global memory).  Fill zeros are
+// multiplied like stored values; positions whose column falls outside the
+// matrix are dropped.
+template <typename V, int R>
+__device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *__restrict__ dval, long long P,
+                                          const typename Compute<V>::T *__restrict__ x,
+                                          typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                          typename Compute<V>::T *__restrict__ y, long long m, long long n,
+                                          long long i0) {
+  typedef typename Compute<V>::T T;
+  constexpr int U = 16 / R;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+  for (int t = 0; t < nd; t += U) {
+    T v[U][R], xv[U][R];
+    bool in[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool live = t + u < nd;
+      const long long o = live ? off[t + u] : 0;
+      if (live) {
+        load_vals<V, R>(dval + (long long)(t + u) * P + i0, v[u]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u][r] = 0;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long j = i0 + r + o;
+        in[u][r] = live && j >= 0 && j < n;
+        xv[u][r] = in[u][r] ? __ldg(x + j) : (T)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (in[u][r]) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+  }
+  write_rows<T, R>(y, i0, m, acc, alpha, beta);
+}
+
+}  // namespace
+}  // namespace smat

@@ -1,0 +1,78 @@
+"""Batched persistent SpMV (one graph launch for many matrices) against the
+oracle and against the per-matrix products."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1210_2536_gb300 as smat
+from paper_1210_2536_gb300 import synth
+from paper_1210_2536_gb300.synth import CSR
+from helpers import TOL, assert_close_rows, reference, stored_values
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _members():
+    mats = synth.amg_like_hierarchy(16)[:3] + synth.mixed_batch(12, 1e3, 3e4, base_seed=7)
+    mats.append(CSR(40, 40, np.zeros(41, np.int32), np.zeros(0, np.int32), np.zeros(0), "empty40"))
+    mats.append(CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]), "one"))
+    return mats
+
+
+def _handles(mats, dtype):
+    hs = []
+    for A in mats:
+        vals, _ = stored_values(A, dtype)
+        M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, np.ascontiguousarray(vals), dtype)
+        M.tune("exhaustive", trial_reps=3)
+        hs.append(M)
+    return hs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_matches_oracle_and_single_products(dtype):
+    mats = _members()
+    hs = _handles(mats, dtype)
+    B = smat.Batch(hs).tune(trial_reps=3)
+    info = B.info()
+    assert info["count"] == len(mats) and info["tiles"] > 0 and info["grid"] > 0 and info["tuned_ms"] > 0
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    npdt = np.float64 if dtype == "f64" else np.float32
+    for call, seed in enumerate((0, 3)):
+        xs = [torch.from_numpy(synth.uniform(seed + i, 1, A.n).astype(npdt)).to(DEV) for i, A in enumerate(mats)]
+        y0 = [synth.uniform(seed + i, 2, A.m).astype(npdt) for i, A in enumerate(mats)]
+        ys = [torch.from_numpy(v.copy()).to(DEV) for v in y0]
+        alphas = [1.0 + 0.5 * i for i in range(len(mats))]
+        betas = [0.0 if (i + call) % 2 == 0 else -0.75 for i in range(len(mats))]
+        B.spmv(xs, ys, alphas, betas)
+        torch.cuda.synchronize()
+        for i, A in enumerate(mats):
+            _, v64 = stored_values(A, dtype)
+            ref, scale = reference(A, v64, xs[i].cpu().numpy(), alphas[i], betas[i], y0[i] if betas[i] else None)
+            got = ys[i].cpu().numpy().astype(np.float64)
+            assert_close_rows(got, ref, scale, TOL[dtype], f"call {call} member {i} ({A.name}) vs oracle")
+            single = hs[i].spmv(xs[i], torch.from_numpy(y0[i].copy()).to(DEV), alphas[i], betas[i])
+            assert_close_rows(got, single.cpu().numpy().astype(np.float64), scale, TOL[dtype],
+                              f"call {call} member {i} vs its own plan")
+    B.close()
+    for M in hs:
+        M.close()
+
+
+def test_batch_rejects_mixed_dtypes_and_untuned_use():
+    A = synth.stencil3d7(6)
+    h64 = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
+    h32 = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val.astype(np.float32), "f32")
+    import ctypes
+    arr = (ctypes.c_void_p * 2)(h64.h, h32.h)
+    b = ctypes.c_void_p()
+    assert smat.lib().smat_batch_create(ctypes.byref(b), arr, 2) == smat.SMAT_ERR_INVALID_ARG
+    B = smat.Batch([h64])
+    x = torch.zeros(A.n, dtype=torch.float64, device=DEV)
+    y = torch.zeros(A.m, dtype=torch.float64, device=DEV)
+    with pytest.raises(smat.SmatError):
+        B.spmv([x], [y])  # not tuned yet
+    B.close()
+    h64.close(), h32.close()
