@@ -25,7 +25,7 @@ namespace {
 enum : int { KIND_CSR = 0, KIND_ELL = 1, KIND_DIA = 2 };
 
 struct BatchMat {
-  int kind, W, nd, pad;
+  int kind, W, nd, epi;
   long long m, n, K, P;
   const int32_t *rowptr, *colidx;
   const void *val;
@@ -47,8 +47,8 @@ constexpr int BNT = 256;
 // Rows [row0, row1) of a CSR product with W lanes per row (W = 1: one thread
 // per row).  The loop bound is uniform over the block, so shuffles see every
 // lane.
-template <typename V, typename T, int W>
-__device__ __forceinline__ void csr_rows(const BatchMat &M, T alpha, T beta, long long row0, long long row1) {
+template <typename V, typename T, int W, int MODE>
+__device__ __forceinline__ void csr_rows(const BatchMat &M, const Epi<T, MODE> &ep, long long row0, long long row1) {
   const int32_t *__restrict__ rowptr = M.rowptr;
   const int32_t *__restrict__ col = M.colidx;
   const V *__restrict__ val = (const V *)M.val;
@@ -81,7 +81,29 @@ __device__ __forceinline__ void csr_rows(const BatchMat &M, T alpha, T beta, lon
 #pragma unroll
       for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, W);
     }
-    if (sub == 0 && row < row1) y[row] = epilogue(acc, alpha, beta, y, row);
+    if (sub == 0 && row < row1) y[row] = ep(acc, y, row);
+  }
+}
+
+// One tile of one member, in the member's format.
+template <typename V, int MODE>
+__device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &tl) {
+  typedef typename Compute<V>::T T;
+  constexpr int R = 16 / (int)sizeof(V);
+  const Epi<T, MODE> ep{(T)M.alpha, (T)M.beta};
+  if (M.kind == KIND_ELL) {
+    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+      ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
+  } else if (M.kind == KIND_DIA) {
+    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+      dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
+  } else {
+    switch (M.W) {
+      case 1: csr_rows<V, T, 1, MODE>(M, ep, tl.row0, tl.row1); break;
+      case 4: csr_rows<V, T, 4, MODE>(M, ep, tl.row0, tl.row1); break;
+      case 8: csr_rows<V, T, 8, MODE>(M, ep, tl.row0, tl.row1); break;
+      default: csr_rows<V, T, 32, MODE>(M, ep, tl.row0, tl.row1); break;
+    }
   }
 }
 
@@ -89,8 +111,6 @@ template <typename V>
 __global__ void __launch_bounds__(BNT) batch_kernel(const BatchMat *__restrict__ mats,
                                                     const BatchTile *__restrict__ tiles, int ntiles,
                                                     unsigned int *counter) {
-  typedef typename Compute<V>::T T;
-  constexpr int R = 16 / (int)sizeof(V);
   __shared__ int s_t;
   for (;;) {
     if (threadIdx.x == 0) s_t = (int)atomicAdd(counter, 1u);
@@ -100,21 +120,10 @@ __global__ void __launch_bounds__(BNT) batch_kernel(const BatchMat *__restrict__
     if (t >= ntiles) return;
     const BatchTile tl = tiles[t];
     const BatchMat &M = mats[tl.mat];
-    const T alpha = (T)M.alpha, beta = (T)M.beta;
-    if (M.kind == KIND_ELL) {
-      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-        ell_group<V, R>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, alpha, beta, (T *)M.y, M.m, i0);
-    } else if (M.kind == KIND_DIA) {
-      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-        dia_group<V, R>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, alpha, beta, (T *)M.y, M.m, M.n,
-                        i0);
-    } else {
-      switch (M.W) {
-        case 1: csr_rows<V, T, 1>(M, alpha, beta, tl.row0, tl.row1); break;
-        case 4: csr_rows<V, T, 4>(M, alpha, beta, tl.row0, tl.row1); break;
-        case 8: csr_rows<V, T, 8>(M, alpha, beta, tl.row0, tl.row1); break;
-        default: csr_rows<V, T, 32>(M, alpha, beta, tl.row0, tl.row1); break;
-      }
+    switch (M.epi) {
+      case EPI_COPY: batch_tile<V, EPI_COPY>(M, tl); break;
+      case EPI_SCALE: batch_tile<V, EPI_SCALE>(M, tl); break;
+      default: batch_tile<V, EPI_AXPBY>(M, tl); break;
     }
   }
 }
@@ -335,7 +344,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
     BTRY(dev_alloc(&y, (size_t)std::max<int64_t>(h->m, 1) * tsz));
     tmp.push_back(y);
     BTRY(cudaMemsetAsync(x, 0, (size_t)std::max<int64_t>(h->n, 1) * tsz, s));
-    M.x = x; M.y = y; M.alpha = 1.0; M.beta = 0.0;
+    M.x = x; M.y = y; M.alpha = 1.0; M.beta = 0.0; M.epi = EPI_COPY;
   }
   BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
   BTRY(cudaStreamSynchronize(s));
@@ -392,6 +401,7 @@ smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *co
     if ((M.m > 0 && !ys[i]) || (M.n > 0 && M.m > 0 && !xs[i])) return SMAT_ERR_INVALID_ARG;
     if (M.x != xs[i] || M.y != ys[i] || M.alpha != a || M.beta != c) {
       M.x = xs[i]; M.y = ys[i]; M.alpha = a; M.beta = c;
+      M.epi = epi_mode(a, c);
       changed = true;
     }
   }

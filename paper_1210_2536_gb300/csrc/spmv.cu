@@ -26,11 +26,11 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // K7: CSR-scalar, one thread per row.
 // ---------------------------------------------------------------------------
-template <typename V, typename T, bool EXACT>
+template <typename V, typename T, bool EXACT, int MODE>
 __global__ void __launch_bounds__(256) csr_scalar_kernel(const int32_t *__restrict__ rowptr,
                                                          const int32_t *__restrict__ col,
                                                          const V *__restrict__ val, const T *__restrict__ x,
-                                                         T alpha, T beta, T *__restrict__ y, long long m) {
+                                                         Epi<T, MODE, EXACT> ep, T *__restrict__ y, long long m) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
     const int s = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
@@ -51,18 +51,18 @@ __global__ void __launch_bounds__(256) csr_scalar_kernel(const int32_t *__restri
       for (int u = 0; u < 8; ++u)
         if (k + u < e) acc = madd<EXACT>(acc, v[u], xv[u]);
     }
-    y[i] = epilogue<T, EXACT>(acc, alpha, beta, y, i);
+    y[i] = ep(acc, y, i);
   }
 }
 
 // ---------------------------------------------------------------------------
 // K8: CSR-vector, W lanes per row, lane-strided loads, shuffle reduction.
 // ---------------------------------------------------------------------------
-template <typename V, typename T, int W>
+template <typename V, typename T, int W, int MODE>
 __global__ void __launch_bounds__(256) csr_vector_kernel(const int32_t *__restrict__ rowptr,
                                                          const int32_t *__restrict__ col,
                                                          const V *__restrict__ val, const T *__restrict__ x,
-                                                         T alpha, T beta, T *__restrict__ y, long long m) {
+                                                         Epi<T, MODE> ep, T *__restrict__ y, long long m) {
   constexpr int RPW = 32 / W;  // rows per warp per step
   const int lane = threadIdx.x & 31, sub = lane % W;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -89,34 +89,35 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(const int32_t *__restri
     }
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o, W);
-    if (sub == 0 && row < m) y[row] = epilogue(acc, alpha, beta, y, row);
+    if (sub == 0 && row < m) y[row] = ep(acc, y, row);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Tiled segmented reduction shared by merge-path CSR (K9) and COO (K12).
 // A CTA consumes a tile of NT*IPT items; each thread walks IPT consecutive
-// items, finishing the rows whose last nonzero it sees.  Partial sums that
-// cross thread boundaries are combined by a deterministic block-wide
-// segmented scan; the partial sum of the row still open at the end of the
-// tile is written to a per-tile carry and added by a fix-up kernel.
+// items, finishing the rows whose last nonzero it sees.  A thread's partial
+// sum of the row still open at its end flows into the first row finished by a
+// later thread.  Which thread that is follows from an integer max-scan of
+// "last thread that finished a row", so the floating-point work is one add
+// per partial (in thread order, hence deterministic) instead of a
+// floating-point scan -- FP64 adds are scarce on GB300.  The partial of the
+// row still open at the end of the tile becomes the tile's carry, added by a
+// fix-up kernel.
 // ---------------------------------------------------------------------------
+// Fallback for tiles where a row spans many threads: a block-wide segmented
+// scan of (finished-a-row, partial) pairs in thread order (deterministic).
 template <typename T>
 struct SegPair {
-  int h;  // this range finished at least one row
-  T v;    // partial sum of the row open at the end of the range
+  int h;
+  T v;
 };
 
 template <typename T>
 __device__ __forceinline__ SegPair<T> seg_combine(SegPair<T> a, SegPair<T> b) {
-  SegPair<T> r;
-  r.h = a.h | b.h;
-  r.v = b.h ? b.v : a.v + b.v;
-  return r;
+  return SegPair<T>{a.h | b.h, b.h ? b.v : a.v + b.v};
 }
 
-// Exclusive block scan of (h, v) pairs in thread order.  Returns the exclusive
-// prefix for this thread and writes the block total to *total.
 template <typename T, int NT>
 __device__ __forceinline__ SegPair<T> block_seg_scan(SegPair<T> x, SegPair<T> *total) {
   __shared__ int sh_h[NT / 32];
@@ -125,43 +126,74 @@ __device__ __forceinline__ SegPair<T> block_seg_scan(SegPair<T> x, SegPair<T> *t
   SegPair<T> inc = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int ph = __shfl_up_sync(FULL, inc.h, o);
-    T pv = __shfl_up_sync(FULL, inc.v, o);
-    if (lane >= o) {
-      SegPair<T> p{ph, pv};
-      inc = seg_combine(p, inc);
-    }
+    const int ph = __shfl_up_sync(FULL, inc.h, o);
+    const T pv = __shfl_up_sync(FULL, inc.v, o);
+    if (lane >= o) inc = seg_combine(SegPair<T>{ph, pv}, inc);
   }
-  SegPair<T> exc;
-  exc.h = __shfl_up_sync(FULL, inc.h, 1);
-  exc.v = __shfl_up_sync(FULL, inc.v, 1);
-  if (lane == 0) { exc.h = 0; exc.v = (T)0; }
+  SegPair<T> exc{__shfl_up_sync(FULL, inc.h, 1), __shfl_up_sync(FULL, inc.v, 1)};
+  if (lane == 0) exc = SegPair<T>{0, (T)0};
   if (lane == 31) { sh_h[w] = inc.h; sh_v[w] = inc.v; }
   __syncthreads();
   if (w == 0) {
-    SegPair<T> wv;
-    wv.h = lane < NT / 32 ? sh_h[lane] : 0;
-    wv.v = lane < NT / 32 ? sh_v[lane] : (T)0;
-    SegPair<T> wi = wv;
+    SegPair<T> wi{lane < NT / 32 ? sh_h[lane] : 0, lane < NT / 32 ? sh_v[lane] : (T)0};
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int ph = __shfl_up_sync(FULL, wi.h, o);
-      T pv = __shfl_up_sync(FULL, wi.v, o);
-      if (lane >= o) {
-        SegPair<T> p{ph, pv};
-        wi = seg_combine(p, wi);
-      }
+      const int ph = __shfl_up_sync(FULL, wi.h, o);
+      const T pv = __shfl_up_sync(FULL, wi.v, o);
+      if (lane >= o) wi = seg_combine(SegPair<T>{ph, pv}, wi);
     }
-    // exclusive prefix of warp totals
     int eh = __shfl_up_sync(FULL, wi.h, 1);
     T ev = __shfl_up_sync(FULL, wi.v, 1);
     if (lane == 0) { eh = 0; ev = (T)0; }
     if (lane < NT / 32) { sh_h[lane] = eh; sh_v[lane] = ev; }
-    if (lane == NT / 32 - 1) { total->h = wi.h; total->v = wi.v; }
+    if (lane == NT / 32 - 1) *total = wi;
   }
   __syncthreads();
-  SegPair<T> wp{sh_h[w], sh_v[w]};
-  return seg_combine(wp, exc);
+  return seg_combine(SegPair<T>{sh_h[w], sh_v[w]}, exc);
+}
+
+// h: this thread finished at least one row; c: its partial of the row open at
+// its end.  Returns the sum of the earlier partials that belong to this
+// thread's first finished row (meaningful when h); the last thread also
+// returns the tile's open partial in *open.  Runs of up to 16 partials are
+// summed serially (one add each); a tile with a longer run -- a row spanning
+// many threads -- uses the block-wide segmented scan instead.
+template <typename T, int NT>
+__device__ __forceinline__ T tile_carries(bool h, T c, T *open) {
+  __shared__ T s_c[NT];
+  __shared__ int s_wmax[NT / 32];
+  __shared__ SegPair<T> s_total;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  s_c[threadIdx.x] = c;
+  int v = h ? (int)threadIdx.x : -1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int p = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v = max(v, p);
+  }
+  if (lane == 31) s_wmax[w] = v;
+  __syncthreads();
+  int before = -1;
+  for (int k = 0; k < w; ++k) before = max(before, s_wmax[k]);
+  const int incl = max(v, before);        // last thread <= me that finished a row
+  int excl = __shfl_up_sync(FULL, incl, 1);
+  if (lane == 0) excl = before;          // last thread < me that finished a row
+  const int run = h ? (int)threadIdx.x - max(excl, 0) : 0;
+  const int open_run = threadIdx.x == NT - 1 ? NT - max(incl, 0) : 0;
+  if (__syncthreads_or(run > 16 || open_run > 16)) {
+    const SegPair<T> in = block_seg_scan<T, NT>(SegPair<T>{h ? 1 : 0, c}, &s_total);
+    if (threadIdx.x == NT - 1) *open = s_total.v;
+    return in.v;
+  }
+  T in = 0;
+  if (h)
+    for (int j = max(excl, 0); j < (int)threadIdx.x; ++j) in += s_c[j];
+  if (threadIdx.x == NT - 1) {
+    T o = 0;
+    for (int j = max(incl, 0); j < NT; ++j) o += s_c[j];
+    *open = o;
+  }
+  return in;
 }
 
 // Merge-path coordinate: number of row ends a among the first d merge items
@@ -202,17 +234,16 @@ __device__ __forceinline__ void stage_pairs(const int32_t *__restrict__ col, con
   }
 }
 
-template <typename V, typename T, int NT, int IPT>
+template <typename V, typename T, int NT, int IPT, int MODE>
 __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict__ rowptr,
                                                        const int32_t *__restrict__ col,
                                                        const V *__restrict__ val, const T *__restrict__ x,
-                                                       T alpha, T beta, T *__restrict__ y, long long m,
+                                                       Epi<T, MODE> ep, T *__restrict__ y, long long m,
                                                        long long nnz, int32_t *carry_row, T *carry_val) {
   constexpr int TILE = NT * IPT;
   __shared__ int32_t s_rowend[TILE + 1];
   __shared__ T s_v[TILE], s_x[TILE];
   __shared__ long long s_coord[4];
-  __shared__ SegPair<T> s_total;
   const long long total = m + nnz;
   const long long d0 = (long long)blockIdx.x * TILE;
   const long long d1 = d0 + TILE < total ? d0 + TILE : total;
@@ -248,7 +279,7 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
         first_acc = acc;
       } else {
         long long r = a0 + a;
-        y[r] = epilogue(acc, alpha, beta, y, r);
+        y[r] = ep(acc, y, r);
       }
       acc = 0;
       ++a;
@@ -257,16 +288,16 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
       ++b;
     }
   }
-  SegPair<T> mine{first_row >= 0 ? 1 : 0, acc};
-  SegPair<T> incoming = block_seg_scan<T, NT>(mine, &s_total);
+  T tile_open = 0;
+  const T incoming = tile_carries<T, NT>(first_row >= 0, acc, &tile_open);
   if (first_row >= 0) {
     long long r = a0 + first_row;
-    y[r] = epilogue(add_rn(incoming.v, first_acc), alpha, beta, y, r);
+    y[r] = ep(incoming + first_acc, y, r);
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == NT - 1) {
     bool open = a1 < m && b1 > b0;
     carry_row[blockIdx.x] = open ? (int32_t)a1 : -1;
-    carry_val[blockIdx.x] = open ? s_total.v : (T)0;
+    carry_val[blockIdx.x] = open ? tile_open : (T)0;
   }
 }
 
@@ -307,15 +338,14 @@ __device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full,
 // K12: COO.  A CTA owns NT*IPT consecutive stored entries; thread t owns IPT
 // consecutive ones, read with 16-byte vector loads, and accumulates them with
 // one fused multiply-add each.  A row ends at entry k when row[k+1] differs.
-template <typename V, typename T, int NT, int IPT>
+template <typename V, typename T, int NT, int IPT, int MODE>
 __global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row,
                                                  const int32_t *__restrict__ col,
                                                  const V *__restrict__ val, const T *__restrict__ x,
-                                                 T alpha, T beta, T *__restrict__ y, long long nnz,
+                                                 Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
                                                  int32_t *carry_row, T *carry_val) {
   constexpr int TILE = NT * IPT;
   static_assert(IPT % 8 == 0, "vector loads need 8 entries per thread");
-  __shared__ SegPair<T> s_total;
   const long long b0 = (long long)blockIdx.x * TILE;
   const long long k0 = b0 + (long long)threadIdx.x * IPT;
   const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
@@ -340,45 +370,46 @@ __global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row
           first_row = r[q];
           first_acc = acc;
         } else {
-          y[r[q]] = epilogue(acc, alpha, beta, y, (long long)r[q]);
+          y[r[q]] = ep(acc, y, (long long)r[q]);
         }
         acc = 0;
       }
     }
   }
-  SegPair<T> mine{first_row >= 0 ? 1 : 0, acc};
-  SegPair<T> incoming = block_seg_scan<T, NT>(mine, &s_total);
-  if (first_row >= 0) y[first_row] = epilogue(add_rn(incoming.v, first_acc), alpha, beta, y, (long long)first_row);
+  T tile_open = 0;
+  const T incoming = tile_carries<T, NT>(first_row >= 0, acc, &tile_open);
+  if (first_row >= 0) y[first_row] = ep(incoming + first_acc, y, (long long)first_row);
   if (threadIdx.x == NT - 1) {
     // the row open at the end of the tile continues into the next tile
     const long long kl = min(b0 + TILE, nnz) - 1;
     const bool open = kl + 1 < nnz && __ldg(row + kl + 1) == __ldg(row + kl);
     carry_row[blockIdx.x] = open ? __ldg(row + kl) : -1;
-    carry_val[blockIdx.x] = open ? s_total.v : (T)0;
+    carry_val[blockIdx.x] = open ? tile_open : (T)0;
   }
 }
 
 // Fix-up: y[r] += alpha * (sum of the carries of row r), runs of equal rows
 // summed in tile order by the run's first entry.
-template <typename T>
+template <typename T, int MODE>
 __global__ void carry_fixup_kernel(const int32_t *__restrict__ carry_row, const T *__restrict__ carry_val,
-                                   long long ntiles, T alpha, T *__restrict__ y) {
+                                   long long ntiles, Epi<T, MODE> ep, T *__restrict__ y) {
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ntiles;
        c += (long long)gridDim.x * blockDim.x) {
     int r = carry_row[c];
     if (r < 0 || (c > 0 && carry_row[c - 1] == r)) continue;
     T s = carry_val[c];
     for (long long q = c + 1; q < ntiles && carry_row[q] == r; ++q) s = add_rn(s, carry_val[q]);
-    y[r] = add_rn(y[r], mul_rn(alpha, s));
+    y[r] = add_rn(y[r], MODE == EPI_COPY ? s : mul_rn(ep.alpha, s));
   }
 }
 
-template <typename T>
-__global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long count, T beta, T *__restrict__ y) {
+template <typename T, int MODE>
+__global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long count, Epi<T, MODE> ep,
+                                  T *__restrict__ y) {
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < count;
        c += (long long)gridDim.x * blockDim.x) {
     int r = rows[c];
-    y[r] = beta == (T)0 ? (T)0 : mul_rn(beta, y[r]);
+    y[r] = MODE == EPI_AXPBY ? mul_rn(ep.beta, y[r]) : (T)0;
   }
 }
 
@@ -389,14 +420,14 @@ __global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long co
 // padding (column -1) gathers x[0] and is dropped by a select, so no load
 // sits behind a branch.
 // ---------------------------------------------------------------------------
-template <typename V, int R>
+template <typename V, int R, int MODE>
 __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
                                                   long long P, long long K,
                                                   const typename Compute<V>::T *__restrict__ x,
-                                                  typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                                  Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m) {
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) ell_group<V, R>(ecol, eval, P, K, x, alpha, beta, y, m, i0);
+  if (i0 < m) ell_group<V, R, MODE>(ecol, eval, P, K, x, ep, y, m, i0);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,18 +437,18 @@ __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ec
 // computation decided by zero filling); positions whose column falls outside
 // the matrix gather x[0] and are dropped by a select.
 // ---------------------------------------------------------------------------
-template <typename V, int R>
+template <typename V, int R, int MODE>
 __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ off, int nd,
                                                   const V *__restrict__ dval, long long P,
                                                   const typename Compute<V>::T *__restrict__ x,
-                                                  typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                                  Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m,
                                                   long long n) {
   extern __shared__ int32_t s_off[];
   for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
   __syncthreads();
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) dia_group<V, R>(s_off, nd, dval, P, x, alpha, beta, y, m, n, i0);
+  if (i0 < m) dia_group<V, R, MODE>(s_off, nd, dval, P, x, ep, y, m, n, i0);
 }
 
 int grid_for(long long work, int block, int max_blocks) {
@@ -430,56 +461,58 @@ int grid_for(long long work, int block, int max_blocks) {
 constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 constexpr int COO_NT = 256, COO_IPT = 8;
 
-template <typename V>
-cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p,
-                       const void *beta_p, void *y_p, cudaStream_t s) {
+template <typename V, int MODE>
+cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha, const void *x_p,
+                      typename Compute<V>::T beta, void *y_p, cudaStream_t s) {
   typedef typename Compute<V>::T T;
-  const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
+  const Epi<T, MODE> ep{alpha, beta};
   const T *x = (const T *)x_p;
   T *y = (T *)y_p;
   const V *val = (const V *)h->val;
   const long long m = h->m;
-  if (m == 0) return cudaSuccess;
   switch (variant) {
     case SMAT_V_CSR_SCALAR:
-      csr_scalar_kernel<V, T, false><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_scalar_kernel<V, T, false, MODE><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x,
+                                                                                     Epi<T, MODE, false>{alpha, beta}, y, m);
       break;
     case SMAT_V_CSR_SCALAR_EXACT:
-      csr_scalar_kernel<V, T, true><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_scalar_kernel<V, T, true, MODE><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x,
+                                                                                    Epi<T, MODE, true>{alpha, beta}, y, m);
       break;
     case SMAT_V_CSR_VEC4:
-      csr_vector_kernel<V, T, 4><<<grid_for(m * 4, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_vector_kernel<V, T, 4, MODE><<<grid_for(m * 4, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_VEC8:
-      csr_vector_kernel<V, T, 8><<<grid_for(m * 8, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_vector_kernel<V, T, 8, MODE><<<grid_for(m * 8, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_VEC32:
-      csr_vector_kernel<V, T, 32><<<grid_for(m * 32, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, alpha, beta, y, m);
+      csr_vector_kernel<V, T, 32, MODE><<<grid_for(m * 32, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_MERGE: {
       long long tiles = (m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
       int32_t *crow = (int32_t *)h->carry;
       T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
-      csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
-          h->rowptr, h->colidx, val, x, alpha, beta, y, m, h->nnz, crow, cval);
+      csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
+          h->rowptr, h->colidx, val, x, ep, y, m, h->nnz, crow, cval);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       if (tiles > 1)
-        carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, y);
+        carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
     } break;
     case SMAT_V_ELL: {
       constexpr int R = 16 / (int)sizeof(V);
-      ell_kernel<V, R><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
-          h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, alpha, beta, y, m);
+      ell_kernel<V, R, MODE><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
+          h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, ep, y, m);
     } break;
     case SMAT_V_DIA: {
       constexpr int R = 16 / (int)sizeof(V);
-      dia_kernel<V, R><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
-          h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, alpha, beta, y, m, h->n);
+      dia_kernel<V, R, MODE><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
+          h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, ep, y, m, h->n);
     } break;
     case SMAT_V_COO: {
       if (h->coo_nempty > 0) {
-        scale_rows_kernel<T><<<grid_for(h->coo_nempty, 256, 152 * 8), 256, 0, s>>>(h->coo_empty, h->coo_nempty, beta, y);
+        scale_rows_kernel<T, MODE><<<grid_for(h->coo_nempty, 256, 152 * 8), 256, 0, s>>>(h->coo_empty, h->coo_nempty,
+                                                                                          ep, y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -487,17 +520,30 @@ cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const 
       long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
       int32_t *crow = (int32_t *)h->carry;
       T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
-      coo_kernel<V, T, COO_NT, COO_IPT><<<(unsigned)tiles, COO_NT, 0, s>>>(
-          h->coo_row, h->colidx, val, x, alpha, beta, y, h->nnz, crow, cval);
+      coo_kernel<V, T, COO_NT, COO_IPT, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(
+          h->coo_row, h->colidx, val, x, ep, y, h->nnz, crow, cval);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       if (tiles > 1)
-        carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, y);
+        carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
     } break;
     default:
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p, const void *beta_p,
+                       void *y_p, cudaStream_t s) {
+  typedef typename Compute<V>::T T;
+  const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
+  if (h->m == 0) return cudaSuccess;
+  switch (epi_mode((double)alpha, (double)beta)) {
+    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s);
+    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s);
+    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s);
+  }
 }
 
 }  // namespace
@@ -583,21 +629,34 @@ cudaError_t noalloc_scratch(void **out) {
   return cudaSuccess;
 }
 
+template <typename V, int MODE>
+cudaError_t merge_noalloc_mode(long long m, long long nnz, const int32_t *rowptr, const int32_t *colidx,
+                               const void *vals, typename Compute<V>::T alpha, const void *x_p,
+                               typename Compute<V>::T beta, void *y_p, unsigned char *scratch, cudaStream_t s) {
+  typedef typename Compute<V>::T T;
+  const Epi<T, MODE> ep{alpha, beta};
+  const long long tiles = (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
+  int32_t *crow = (int32_t *)scratch;
+  T *cval = (T *)(scratch + NOALLOC_ROW_BYTES);
+  csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
+      rowptr, colidx, (const V *)vals, (const T *)x_p, ep, (T *)y_p, m, nnz, crow, cval);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || tiles <= 1) return e;
+  carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, (T *)y_p);
+  return cudaGetLastError();
+}
+
 template <typename V>
 cudaError_t merge_noalloc_typed(long long m, long long nnz, const int32_t *rowptr, const int32_t *colidx,
                                 const void *vals, const void *alpha_p, const void *x_p, const void *beta_p,
                                 void *y_p, unsigned char *scratch, cudaStream_t s) {
   typedef typename Compute<V>::T T;
   const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
-  const long long tiles = (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
-  int32_t *crow = (int32_t *)scratch;
-  T *cval = (T *)(scratch + NOALLOC_ROW_BYTES);
-  csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
-      rowptr, colidx, (const V *)vals, (const T *)x_p, alpha, beta, (T *)y_p, m, nnz, crow, cval);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || tiles <= 1) return e;
-  carry_fixup_kernel<T><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, alpha, (T *)y_p);
-  return cudaGetLastError();
+  switch (epi_mode((double)alpha, (double)beta)) {
+    case EPI_COPY: return merge_noalloc_mode<V, EPI_COPY>(m, nnz, rowptr, colidx, vals, alpha, x_p, beta, y_p, scratch, s);
+    case EPI_SCALE: return merge_noalloc_mode<V, EPI_SCALE>(m, nnz, rowptr, colidx, vals, alpha, x_p, beta, y_p, scratch, s);
+    default: return merge_noalloc_mode<V, EPI_AXPBY>(m, nnz, rowptr, colidx, vals, alpha, x_p, beta, y_p, scratch, s);
+  }
 }
 
 }  // namespace

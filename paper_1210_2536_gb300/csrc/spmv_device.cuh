@@ -40,15 +40,29 @@ __device__ __forceinline__ double madd(double acc, double v, double x) {
 template <bool EXACT>
 __device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf(v, x, acc); }
 
-// y_i = alpha*acc (+ beta*y_i).  alpha == 1 skips the multiply (exact);
-// beta != 0 folds beta*y_i into one fused multiply-add unless EXACT.
-template <typename T, bool EXACT = false>
-__device__ __forceinline__ T epilogue(T acc, T alpha, T beta, const T *y, long long i) {
-  const T ax = alpha == (T)1 ? acc : mul_rn(alpha, acc);
-  if (beta == (T)0) return ax;
-  if (EXACT) return add_rn(ax, mul_rn(beta, y[i]));
-  return fused(ax, beta, y[i]);
+// The epilogue y_i = alpha*acc (+ beta*y_i) in one of three forms chosen on
+// the host, so no kernel compares alpha or beta (FP64 compares occupy the
+// same scarce FP64 pipe as the products):
+//   EPI_COPY   beta == 0, alpha == 1:  y_i = acc
+//   EPI_SCALE  beta == 0:              y_i = alpha*acc        (y not read)
+//   EPI_AXPBY  otherwise:              y_i = alpha*acc + beta*y_i
+// EXACT rounds beta*y_i and the sum separately; otherwise they are fused.
+enum : int { EPI_COPY = 0, EPI_SCALE = 1, EPI_AXPBY = 2 };
+
+inline int epi_mode(double alpha, double beta) {
+  return beta != 0.0 ? EPI_AXPBY : (alpha != 1.0 ? EPI_SCALE : EPI_COPY);
 }
+
+template <typename T, int MODE, bool EXACT = false>
+struct Epi {
+  T alpha, beta;
+  __device__ __forceinline__ T operator()(T acc, const T *y, long long i) const {
+    if (MODE == EPI_COPY) return acc;
+    const T ax = mul_rn(alpha, acc);
+    if (MODE == EPI_SCALE) return ax;
+    return EXACT ? add_rn(ax, mul_rn(beta, y[i])) : fused(ax, beta, y[i]);
+  }
+};
 
 // 16-byte vector loads of R consecutive values (R * sizeof(V) == 16) and of
 // R consecutive column indices.
@@ -116,34 +130,34 @@ template <> struct YVec<float, 8> {
   }
 };
 
-template <typename T, int R>
-__device__ __forceinline__ void write_rows(T *__restrict__ y, long long i0, long long m, const T (&acc)[R], T alpha,
-                                           T beta) {
+template <typename T, int R, int MODE>
+__device__ __forceinline__ void write_rows(T *__restrict__ y, long long i0, long long m, const T (&acc)[R],
+                                           const Epi<T, MODE> &ep) {
   if (i0 + R <= m) {
     T out[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[r] = alpha == (T)1 ? acc[r] : mul_rn(alpha, acc[r]);
-    if (beta != (T)0) {
+    for (int r = 0; r < R; ++r) out[r] = MODE == EPI_COPY ? acc[r] : mul_rn(ep.alpha, acc[r]);
+    if (MODE == EPI_AXPBY) {
       T yo[R];
       YVec<T, R>::ld(y + i0, yo);
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[r] = fused(out[r], beta, yo[r]);
+      for (int r = 0; r < R; ++r) out[r] = fused(out[r], ep.beta, yo[r]);
     }
     YVec<T, R>::st(y + i0, out);
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (i0 + r < m) y[i0 + r] = epilogue(acc[r], alpha, beta, y, i0 + r);
+      if (i0 + r < m) y[i0 + r] = ep(acc[r], y, i0 + r);
   }
 }
 
 // One thread's R consecutive rows [i0, i0 + R) of an ELL product
 // (column-major, pitch P, K slots).  16/R slots are loaded before their
 // gathers are issued; padding (column -1) is dropped.
-template <typename V, int R>
+template <typename V, int R, int MODE>
 __device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, const V *__restrict__ eval, long long P,
                                           long long K, const typename Compute<V>::T *__restrict__ x,
-                                          typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                          const Epi<typename Compute<V>::T, MODE> &ep,
                                           typename Compute<V>::T *__restrict__ y, long long m, long long i0) {
   typedef typename Compute<V>::T T;
   constexpr int U = 16 / R;
@@ -169,21 +183,23 @@ __device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, cons
       for (int r = 0; r < R; ++r) xv[u][r] = c[u][r] >= 0 ? __ldg(x + c[u][r]) : (T)0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
+      if (q + u < K) {  // uniform across the warp: dead slots issue no FP work
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (c[u][r] >= 0) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+        for (int r = 0; r < R; ++r)
+          if (c[u][r] >= 0) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+      }
   }
-  write_rows<T, R>(y, i0, m, acc, alpha, beta);
+  write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
 
 // One thread's R consecutive rows of a DIA product; `off` holds the nd
 // ascending diagonal offsets (shared or global memory).  Fill zeros are
 // multiplied like stored values; positions whose column falls outside the
 // matrix are dropped.
-template <typename V, int R>
+template <typename V, int R, int MODE>
 __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *__restrict__ dval, long long P,
                                           const typename Compute<V>::T *__restrict__ x,
-                                          typename Compute<V>::T alpha, typename Compute<V>::T beta,
+                                          const Epi<typename Compute<V>::T, MODE> &ep,
                                           typename Compute<V>::T *__restrict__ y, long long m, long long n,
                                           long long i0) {
   typedef typename Compute<V>::T T;
@@ -213,11 +229,13 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
+      if (t + u < nd) {  // uniform across the warp: dead slots issue no FP work
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (in[u][r]) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+        for (int r = 0; r < R; ++r)
+          if (in[u][r]) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+      }
   }
-  write_rows<T, R>(y, i0, m, acc, alpha, beta);
+  write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
 
 }  // namespace
