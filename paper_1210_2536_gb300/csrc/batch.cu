@@ -85,16 +85,16 @@ __device__ __forceinline__ void csr_rows(const BatchMat &M, const Epi<T, MODE> &
   }
 }
 
-// One tile of one member, in the member's format.
-template <typename V, int MODE>
+// One tile of one member, in the member's format (KIND is the member's kind).
+template <typename V, int KIND, int MODE>
 __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &tl) {
   typedef typename Compute<V>::T T;
   constexpr int R = 16 / (int)sizeof(V);
   const Epi<T, MODE> ep{(T)M.alpha, (T)M.beta};
-  if (M.kind == KIND_ELL) {
+  if (KIND == KIND_ELL) {
     for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
       ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
-  } else if (M.kind == KIND_DIA) {
+  } else if (KIND == KIND_DIA) {
     for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
       dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
   } else {
@@ -107,8 +107,11 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
   }
 }
 
-template <typename V>
-__global__ void __launch_bounds__(BNT) batch_kernel(const BatchMat *__restrict__ mats,
+// Persistent CTAs of one format kind take tiles of that kind from an atomic
+// counter, largest first, until none are left.  One kernel per kind keeps
+// each kernel's register budget to its own format's needs.
+template <typename V, int KIND>
+__global__ void __launch_bounds__(BNT, KIND == KIND_ELL ? 2 : 4) batch_kernel(const BatchMat *__restrict__ mats,
                                                     const BatchTile *__restrict__ tiles, int ntiles,
                                                     unsigned int *counter) {
   __shared__ int s_t;
@@ -121,21 +124,29 @@ __global__ void __launch_bounds__(BNT) batch_kernel(const BatchMat *__restrict__
     const BatchTile tl = tiles[t];
     const BatchMat &M = mats[tl.mat];
     switch (M.epi) {
-      case EPI_COPY: batch_tile<V, EPI_COPY>(M, tl); break;
-      case EPI_SCALE: batch_tile<V, EPI_SCALE>(M, tl); break;
-      default: batch_tile<V, EPI_AXPBY>(M, tl); break;
+      case EPI_COPY: batch_tile<V, KIND, EPI_COPY>(M, tl); break;
+      case EPI_SCALE: batch_tile<V, KIND, EPI_SCALE>(M, tl); break;
+      default: batch_tile<V, KIND, EPI_AXPBY>(M, tl); break;
     }
   }
 }
 
-cudaError_t launch_batch_kernel(smat_dtype_t dt, int grid, const BatchMat *mats, const BatchTile *tiles, int ntiles,
-                                unsigned int *counter, cudaStream_t s) {
+template <int KIND>
+cudaError_t launch_kind(smat_dtype_t dt, int grid, const BatchMat *mats, const BatchTile *tiles, int ntiles,
+                        unsigned int *counter, cudaStream_t s) {
   switch (dt) {
-    case SMAT_F64: batch_kernel<double><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
-    case SMAT_F32: batch_kernel<float><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
-    default: batch_kernel<__nv_bfloat16><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+    case SMAT_F64: batch_kernel<double, KIND><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+    case SMAT_F32: batch_kernel<float, KIND><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
+    default: batch_kernel<__nv_bfloat16, KIND><<<grid, BNT, 0, s>>>(mats, tiles, ntiles, counter); break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kernel(int kind, smat_dtype_t dt, int grid, const BatchMat *mats, const BatchTile *tiles,
+                                int ntiles, unsigned int *counter, cudaStream_t s) {
+  if (kind == KIND_ELL) return launch_kind<KIND_ELL>(dt, grid, mats, tiles, ntiles, counter, s);
+  if (kind == KIND_DIA) return launch_kind<KIND_DIA>(dt, grid, mats, tiles, ntiles, counter, s);
+  return launch_kind<KIND_CSR>(dt, grid, mats, tiles, ntiles, counter, s);
 }
 
 }  // namespace
@@ -148,10 +159,12 @@ struct smat_batch_s {
   std::vector<std::vector<int32_t>> rowptrs;  // CSR members: row pointers for nnz-balanced tiles
   smat::BatchMat *d_mats = nullptr;
   smat::BatchTile *d_tiles = nullptr;
-  unsigned int *d_counter = nullptr;
+  unsigned int *d_counter = nullptr;  // one tile counter per format kind
   int ntiles = 0, grid = 0, tile_scale = 0, ctas_per_sm = 0;
+  int kind_tiles[3] = {0, 0, 0}, kind_first[3] = {0, 0, 0}, kind_grid[3] = {0, 0, 0};
   double tuned_ms = -1.0;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, fork[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ready = false;
@@ -231,7 +244,11 @@ std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
       }
     }
   }
-  std::stable_sort(v.begin(), v.end(), [](const Est &a, const Est &c) { return a.w > c.w; });
+  // grouped by format kind (CSR, ELL, DIA), each group largest first
+  std::stable_sort(v.begin(), v.end(), [&](const Est &a, const Est &c) {
+    const int ka = b->mats[(size_t)a.t.mat].kind, kc = b->mats[(size_t)c.t.mat].kind;
+    return ka != kc ? ka < kc : a.w > c.w;
+  });
   std::vector<BatchTile> out;
   out.reserve(v.size());
   for (auto &e : v) out.push_back(e.t);
@@ -244,6 +261,11 @@ smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
   b->d_tiles = nullptr;
   std::vector<BatchTile> tiles = make_tiles(b, scale);
   b->ntiles = (int)tiles.size();
+  for (int k = 0; k < 3; ++k) b->kind_tiles[k] = 0;
+  for (const BatchTile &t : tiles) ++b->kind_tiles[b->mats[(size_t)t.mat].kind];
+  b->kind_first[0] = 0;
+  b->kind_first[1] = b->kind_tiles[0];
+  b->kind_first[2] = b->kind_tiles[0] + b->kind_tiles[1];
   if (b->ntiles > 0) {
     void *p = nullptr;
     BTRY(dev_alloc(&p, tiles.size() * sizeof(BatchTile)));
@@ -253,18 +275,30 @@ smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid = std::max(1, std::min(sms * ctas_per_sm, std::max(b->ntiles, 1)));
+  b->grid = 0;
+  for (int k = 0; k < 3; ++k) {
+    b->kind_grid[k] = b->kind_tiles[k] > 0 ? std::min(sms * ctas_per_sm, b->kind_tiles[k]) : 0;
+    b->grid += b->kind_grid[k];
+  }
   b->tile_scale = scale;
   b->ctas_per_sm = ctas_per_sm;
-  // capture: reset the tile counter, run the persistent kernel
+  // capture: reset the three tile counters, then one persistent kernel per
+  // format kind on parallel branches of the graph
   BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->cap);
-  cudaError_t e2 = b->ntiles > 0 ? launch_batch_kernel(b->dtype, b->grid, b->d_mats, b->d_tiles, b->ntiles,
-                                                        b->d_counter, b->cap)
-                                  : cudaSuccess;
+  cudaError_t err = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(unsigned int), b->cap);
+  if (err == cudaSuccess) err = cudaEventRecord(b->ev_fork, b->cap);
+  cudaStream_t st[3] = {b->cap, b->fork[0], b->fork[1]};
+  for (int k = 1; k < 3 && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(st[k], b->ev_fork, 0);
+  for (int k = 0; k < 3 && err == cudaSuccess; ++k)
+    if (b->kind_tiles[k] > 0)
+      err = launch_batch_kernel(k, b->dtype, b->kind_grid[k], b->d_mats, b->d_tiles + b->kind_first[k],
+                                b->kind_tiles[k], b->d_counter + k, st[k]);
+  for (int k = 1; k < 3 && err == cudaSuccess; ++k) {
+    err = cudaEventRecord(b->ev_join[k - 1], st[k]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, b->ev_join[k - 1], 0);
+  }
   cudaError_t e3 = cudaStreamEndCapture(b->cap, &b->graph);
-  BTRY(e1);
-  BTRY(e2);
+  BTRY(err);
   BTRY(e3);
   BTRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
   b->ready = true;
@@ -291,9 +325,12 @@ smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int3
   b->dtype = hs[0]->dtype;
   auto fail = [&](smat_status_t s) { smat_batch_destroy(b); return s; };
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(SMAT_ERR_CUDA);
   void *p = nullptr;
-  if ((e = dev_alloc(&p, sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
+  if ((e = dev_alloc(&p, 3 * sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
   b->d_counter = (unsigned int *)p;
   if ((e = dev_alloc(&p, sizeof(BatchMat) * (size_t)count)) != cudaSuccess) return fail(st_of(e));
   b->d_mats = (BatchMat *)p;
@@ -308,6 +345,11 @@ smat_status_t smat_batch_destroy(smat_batch_t b) {
   dev_free(b->d_tiles);
   dev_free(b->d_mats);
   dev_free(b->d_counter);
+  for (int k = 0; k < 2; ++k) {
+    if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return SMAT_OK;
