@@ -229,6 +229,7 @@ def run_ours(args):
     import paper_1210_2536_gb300 as smat
     from paper_1210_2536_gb300.roofline import algorithmic_bytes
     from paper_1210_2536_gb300.roofline import bound as roof_bound
+    from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -330,13 +331,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
     flops_step = sum(2.0 * p["A"].nnz for p in prods)
-    value = world * flops_step * K / (ms / 1e3) / 1e9
+    value = weak_scaling_throughput(flops_step * K, ms / 1e3, world) / 1e9
     launches_per_step = sum(p["launches"] for p in prods)
 
     peak, peak_kind = measured_peak()
@@ -386,12 +383,8 @@ def run_ours(args):
     for _ in range(E):
         for p, (xh, yh) in zip(prods, pinned):
             p["M"].spmv_host(xh, yh)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * flops_step * E / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
 
     if rank == 0:
         cpu = cpu_baseline(mats, xs, dtypes, args.cpu_seconds) if world == 1 else None

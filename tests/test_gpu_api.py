@@ -1,0 +1,120 @@
+"""The C ABI's behaviour on the GPU: CSR validation through the device flag,
+allocation failures without leaks, the tuning modes, and parity at the full
+size of the bench workload."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1210_2536_gb300 as smat
+from paper_1210_2536_gb300 import synth
+from paper_1210_2536_gb300.synth import CSR
+from helpers import TOL, assert_close_rows, reference, stored_values
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _create(m, n, rp, ci, v, dtype=smat.SMAT_F64):
+    rp = np.ascontiguousarray(rp, np.int32)
+    ci = np.ascontiguousarray(ci, np.int32)
+    v = np.ascontiguousarray(v, np.float64)
+    st, h = smat.smat_create(m, n, len(ci), rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                             v.ctypes.data if len(v) else None, dtype)
+    return st, h
+
+
+BAD = {
+    "unsorted columns": (3, 4, [0, 2, 3, 4], [2, 1, 0, 3], [1, 1, 1, 1]),
+    "duplicate column": (2, 4, [0, 2, 3], [1, 1, 0], [1, 1, 1]),
+    "column out of range": (2, 4, [0, 1, 2], [0, 4], [1, 1]),
+    "negative column": (2, 4, [0, 1, 2], [-1, 0], [1, 1]),
+    "rowptr decreasing": (3, 3, [0, 2, 1, 3], [0, 1, 2], [1, 1, 1]),
+    "rowptr end mismatch": (2, 3, [0, 1, 3], [0, 1], [1, 1]),
+    "rowptr start nonzero": (2, 3, [1, 1, 2], [0, 1], [1, 1]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BAD))
+def test_invalid_csr_is_rejected(case):
+    m, n, rp, ci, v = BAD[case]
+    st, h = _create(m, n, rp, ci, v)
+    assert st == smat.SMAT_ERR_INVALID_CSR and not h
+
+
+def test_valid_edge_cases_are_accepted():
+    for m, n, rp, ci in [(0, 0, [0], []), (3, 0, [0, 0, 0, 0], []), (1, 1, [0, 1], [0])]:
+        st, h = _create(m, n, rp, ci, np.ones(len(ci)))
+        assert st == smat.SMAT_OK
+        smat.smat_destroy(h)
+
+
+def test_allocation_failure_returns_alloc_and_leaks_nothing():
+    A = synth.powerlaw(50000, 1.8, 2000, 1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    seen = set()
+    for k in range(1, 12):
+        smat.lib().smat_test_fail_alloc_after(k)
+        try:
+            st, h = _create(A.m, A.n, A.rowptr, A.colidx, A.val)
+            if st == smat.SMAT_OK:
+                M = h
+                o = smat.smat_tune_opts_default()
+                o.mode = smat.SMAT_TUNE_EXHAUSTIVE
+                o.trial_reps = 2
+                st = smat.smat_tune(M, o, 0)
+                smat.smat_destroy(M)
+        finally:
+            smat.lib().smat_test_fail_alloc_after(0)
+        seen.add(st)
+        assert st in (smat.SMAT_OK, smat.SMAT_ERR_ALLOC), smat.smat_status_string(st)
+    assert smat.SMAT_ERR_ALLOC in seen
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)   # nothing left allocated
+
+
+def test_tuning_modes():
+    A = synth.stencil3d7(24)
+    M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
+    adm = M.features()["admissible"]
+    assert (adm >> smat.SMAT_V_DIA) & 1 and (adm >> smat.SMAT_V_ELL) & 1
+    M.tune("rules")                                  # the paper's thresholds: few, full diagonals -> DIA
+    assert M.plan()["variant"] == smat.SMAT_V_DIA and M.plan()["trialled"] == 0
+    M.tune("fixed", variant=smat.SMAT_V_CSR_MERGE)
+    assert M.plan()["variant"] == smat.SMAT_V_CSR_MERGE
+    M.tune("exhaustive", trial_reps=5, allowed=0b11100001)
+    t = M.timings()
+    tried = [v for v in range(8) if t[v] > 0]
+    assert set(tried) == {0, 5, 6, 7}
+    assert M.plan()["variant"] == min(tried, key=lambda v: t[v])
+    smat.smat_set_model(None, None, None)
+    with pytest.raises(smat.SmatError):
+        M.tune("learned")                             # no model installed
+    P = synth.powerlaw(5000, 1.8, 1000, 3)
+    Q = smat.SpMatrix(P.m, P.n, P.rowptr, P.colidx, P.val, "f64")
+    assert not (Q.features()["admissible"] >> smat.SMAT_V_DIA) & 1   # 20x fill rule
+    with pytest.raises(smat.SmatError):
+        Q.tune("fixed", variant=smat.SMAT_V_DIA)
+    M.close(), Q.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_bench_workload_parity(dtype):
+    # the bench's matrices at full size, tuned as the bench tunes them, all rows
+    if smat.smat_load_model(smat.MODEL_PATH) != 0:
+        pytest.skip("no selector model")
+    for A in synth.structures_suite(1.0):
+        vals, v64 = stored_values(A, dtype)
+        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
+                          torch.from_numpy(np.ascontiguousarray(vals)).to(DEV), dtype)
+        M.tune("learned")
+        x = synth.uniform(0, 1, A.n).astype(np.float64 if dtype == "f64" else np.float32)
+        y = M.spmv(torch.from_numpy(x).to(DEV)).cpu().numpy().astype(np.float64)
+        ref, scale = reference(A, v64, x, 1.0, 0.0, None)
+        assert_close_rows(y, ref, scale, TOL[dtype], f"{A.name} {dtype} {M.plan()['name']}")
+        f, fo = M.features(), oracle.features(A.m, A.n, A.rowptr, A.colidx)
+        for k in ("nnz", "max_rd", "min_rd", "ndiags", "ntdiags", "var_rd", "er_dia", "er_ell", "r"):
+            assert f[k] == fo[k], (A.name, k)
+        M.close()
+    smat.smat_set_model(None, None, None)
