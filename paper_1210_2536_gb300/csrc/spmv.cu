@@ -335,44 +335,50 @@ __device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full,
   }
 }
 
-// K12: COO.  A CTA owns NT*IPT consecutive stored entries; thread t owns IPT
-// consecutive ones, read with 16-byte vector loads, and accumulates them with
-// one fused multiply-add each.  A row ends at entry k when row[k+1] differs.
-template <typename V, typename T, int NT, int IPT, int MODE>
+// K12: COO.  A CTA owns NT*CH*8 consecutive stored entries; thread t owns
+// CH*8 consecutive ones, read 8 at a time with 16-byte vector loads, and
+// accumulates them with one fused multiply-add each.  A row ends at entry k
+// when row[k+1] differs.  CH chunks per thread amortise the tile's fixed work
+// (carry resolution, barriers) over more entries.
+template <typename V, typename T, int NT, int CH, int MODE>
 __global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row,
                                                  const int32_t *__restrict__ col,
                                                  const V *__restrict__ val, const T *__restrict__ x,
                                                  Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
                                                  int32_t *carry_row, T *carry_val) {
-  constexpr int TILE = NT * IPT;
-  static_assert(IPT % 8 == 0, "vector loads need 8 entries per thread");
+  constexpr int IPT = 8, TILE = NT * CH * IPT;
   const long long b0 = (long long)blockIdx.x * TILE;
-  const long long k0 = b0 + (long long)threadIdx.x * IPT;
-  const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
-  const bool full = valid == IPT;
-  int r[IPT], c[IPT];
-  T v[IPT], xv[IPT];
-  load_i32_run<IPT>(row + k0, full, valid, r, -1);
-  load_i32_run<IPT>(col + k0, full, valid, c, 0);
-  load_val_run<V, IPT>(val + k0, full, valid, v);
-  const int r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
-#pragma unroll
-  for (int q = 0; q < IPT; ++q) xv[q] = q < valid ? __ldg(x + c[q]) : (T)0;
+  const long long kt = b0 + (long long)threadIdx.x * (CH * IPT);
   T acc = 0, first_acc = 0;
   int first_row = -1;
+#pragma unroll 1
+  for (int ch = 0; ch < CH; ++ch) {
+    const long long k0 = kt + ch * IPT;
+    const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
+    if (valid == 0) break;
+    const bool full = valid == IPT;
+    int r[IPT], c[IPT];
+    T v[IPT], xv[IPT];
+    load_i32_run<IPT>(row + k0, full, valid, r, -1);
+    load_i32_run<IPT>(col + k0, full, valid, c, 0);
+    load_val_run<V, IPT>(val + k0, full, valid, v);
+    const int r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
 #pragma unroll
-  for (int q = 0; q < IPT; ++q) {
-    if (q < valid) {
-      acc = fused(acc, v[q], xv[q]);
-      const int rn = q + 1 < IPT ? r[q + 1] : r_next;
-      if (rn != r[q]) {  // last stored entry of row r[q]
-        if (first_row < 0) {
-          first_row = r[q];
-          first_acc = acc;
-        } else {
-          y[r[q]] = ep(acc, y, (long long)r[q]);
+    for (int q = 0; q < IPT; ++q) xv[q] = q < valid ? __ldg(x + c[q]) : (T)0;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      if (q < valid) {
+        acc = fused(acc, v[q], xv[q]);
+        const int rn = q + 1 < IPT ? r[q + 1] : r_next;
+        if (rn != r[q]) {  // last stored entry of row r[q]
+          if (first_row < 0) {
+            first_row = r[q];
+            first_acc = acc;
+          } else {
+            y[r[q]] = ep(acc, y, (long long)r[q]);
+          }
+          acc = 0;
         }
-        acc = 0;
       }
     }
   }
@@ -459,7 +465,13 @@ int grid_for(long long work, int block, int max_blocks) {
 }
 
 constexpr int MERGE_NT = 256, MERGE_IPT = 8;
-constexpr int COO_NT = 256, COO_IPT = 8;
+#ifndef SMAT_COO_NT
+#define SMAT_COO_NT 256
+#endif
+#ifndef SMAT_COO_CH
+#define SMAT_COO_CH 1
+#endif
+constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 
 template <typename V, int MODE>
 cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha, const void *x_p,
@@ -520,7 +532,7 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
       int32_t *crow = (int32_t *)h->carry;
       T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
-      coo_kernel<V, T, COO_NT, COO_IPT, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(
+      coo_kernel<V, T, COO_NT, COO_CH, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(
           h->coo_row, h->colidx, val, x, ep, y, h->nnz, crow, cval);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
