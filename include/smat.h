@@ -167,7 +167,9 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts, void *str
 
 /* y = alpha*A*x + beta*y through the handle's plan.  x[n] and y[m] are DEVICE
  * pointers of the compute type; alpha and beta HOST pointers.  Asynchronous on
- * `stream`; only launch errors are reported.  x and y must not overlap. */
+ * `stream`; only launch errors are reported.  x and y must not overlap.  ELL
+ * and DIA plans use 16-byte vector accesses to x and y; when either is not
+ * 16-byte aligned the product runs through the CSR-scalar kernel instead. */
 smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const void *beta,
                         void *y, void *stream);
 
@@ -287,8 +289,10 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
 
 /* y_i = alpha_i A_i x_i + beta_i y_i for every member i in one graph launch on
  * `stream`.  alphas / betas: HOST arrays of `count` scalars of the compute
- * type; xs / ys: HOST arrays of `count` DEVICE pointers.  Descriptors are
- * re-uploaded only when a pointer or scalar changed.  Asynchronous. */
+ * type; xs / ys: HOST arrays of `count` DEVICE pointers, 16-byte aligned for
+ * ELL and DIA members (SMAT_ERR_INVALID_ARG otherwise).  Descriptors are
+ * re-uploaded only when a pointer or scalar changed.  Asynchronous; calls on
+ * one batch must be ordered (same stream or synchronised). */
 smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *const *xs, const void *betas,
                               void *const *ys, void *stream);
 

@@ -441,6 +441,8 @@ smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *co
     const double a = b->dtype == SMAT_F64 ? ((const double *)alphas)[i] : (double)((const float *)alphas)[i];
     const double c = b->dtype == SMAT_F64 ? ((const double *)betas)[i] : (double)((const float *)betas)[i];
     if ((M.m > 0 && !ys[i]) || (M.n > 0 && M.m > 0 && !xs[i])) return SMAT_ERR_INVALID_ARG;
+    // ELL and DIA members read x and write y with 16-byte vector accesses
+    if (M.kind != KIND_CSR && (((uintptr_t)xs[i] | (uintptr_t)ys[i]) & 15u) != 0) return SMAT_ERR_INVALID_ARG;
     if (M.x != xs[i] || M.y != ys[i] || M.alpha != a || M.beta != c) {
       M.x = xs[i]; M.y = ys[i]; M.alpha = a; M.beta = c;
       M.epi = epi_mode(a, c);

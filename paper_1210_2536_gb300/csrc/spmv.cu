@@ -584,6 +584,10 @@ int spmv_launch_count(const smat_s *h, int variant) {
 
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
                         void *y, cudaStream_t s) {
+  // ELL and DIA read x and write y with 16-byte vector accesses; vectors that
+  // are not 16-byte aligned take the CSR-scalar kernel instead.
+  if ((variant == SMAT_V_ELL || variant == SMAT_V_DIA) && (((uintptr_t)x | (uintptr_t)y) & 15u) != 0)
+    variant = SMAT_V_CSR_SCALAR;
   switch (h->dtype) {
     case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s);
     case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s);

@@ -189,3 +189,27 @@ def test_casts_bit_exact():
     torch.cuda.synchronize()
     assert np.array_equal(o32.cpu().numpy().view(np.uint32), v.astype(np.float32).view(np.uint32))
     assert np.array_equal(ob.cpu().numpy().view(np.uint16), oracle.round_bf16(v))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_misaligned_vectors_are_safe(dtype):
+    # x and y one element into their buffers: ELL / DIA plans fall back to a
+    # kernel without vector accesses; every variant still matches the oracle
+    A = synth.stencil3d7(12)
+    M, vals64 = make(A, dtype)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    x = synth.uniform(0, 1, A.n).astype(npdt)
+    y0 = synth.uniform(1, 1, A.m).astype(npdt)
+    ref, scale = reference(A, vals64, x, 1.5, -0.5, y0)
+    xb = torch.zeros(A.n + 1, dtype=torch.from_numpy(x).dtype, device=DEV)
+    yb = torch.zeros(A.m + 1, dtype=torch.from_numpy(x).dtype, device=DEV)
+    xb[1:] = torch.from_numpy(x).to(DEV)
+    for v in range(smat.SMAT_NUM_VARIANTS):
+        if not (M.features()["admissible"] >> v) & 1:
+            continue
+        yb[1:] = torch.from_numpy(y0).to(DEV)
+        M.spmv(xb[1:], yb[1:], 1.5, -0.5, variant=v)
+        torch.cuda.synchronize()
+        assert_close_rows(yb[1:].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
+                          f"misaligned {dtype} {smat.VARIANT_NAMES[v]}")
+    M.close()
