@@ -374,15 +374,26 @@ def run_ours(args):
         pinned.append((xh, yh))
     h2d = sum(xh.numel() * xh.element_size() for xh, _ in pinned)
     d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
+    # each product's copy in, kernel and copy out go to one of three streams,
+    # so transfers of one product overlap the kernels of the others; the step
+    # ends when every stream is done (y is then on the host)
+    streams = [torch.cuda.Stream() for _ in range(3)]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
+
+    def e2e_step():
+        for j, (p, (xh, yh)) in enumerate(zip(prods, pinned)):
+            p["M"].spmv_host_async(xh, yh, stream=streams[j % 3])
+        for st in streams:
+            st.synchronize()
+
+    e2e_step()
     E = max(1, args.e2e_steps)
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(E):
-        for p, (xh, yh) in zip(prods, pinned):
-            p["M"].spmv_host(xh, yh)
+        e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
 
@@ -410,7 +421,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * K,
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": E},
+                    "d2h_bytes_per_step": d2h, "steps": E,
+                    "how": "smat_spmv_host_async per product from pinned host x/y, 3 streams, all synced per step"},
             "cpu_baseline": cpu,
             "per_matrix": per,
         }

@@ -190,6 +190,15 @@ smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_h
  * than one tile; COO adds one for empty rows).  Writes 0 for v not built. */
 smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *launches);
 
+/* The same host-buffer product without the final synchronisation: the copy
+ * in, the product and the copy out are only enqueued on `stream`, so products
+ * of different handles on different streams overlap their transfers with each
+ * other's kernels.  x_host and y_host should be page-locked (pinned) for the
+ * copies to be asynchronous; y_host is valid once `stream` has finished.
+ * Calls on one handle share its staging buffers and must be ordered. */
+smat_status_t smat_spmv_host_async(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
+                                   void *y_host, void *stream);
+
 /* Feature parameters (computes them on `stream` = NULL if not yet done). */
 smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out);
 

@@ -88,6 +88,7 @@ _SIGS = {
     "smat_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_launches": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
@@ -184,6 +185,10 @@ def smat_spmv_variant(h, v, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
 
 def smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
     return lib().smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_spmv_host_async(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
+    return lib().smat_spmv_host_async(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
 
 
 def smat_spmv_launches(h, v) -> int:
@@ -461,6 +466,13 @@ class SpMatrix:
         a, b = self._scalars(alpha, beta)
         _check(smat_spmv_host(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
                               _stream_ptr(stream)), "smat_spmv_host")
+        return y
+
+    def spmv_host_async(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        """Enqueue the host-buffer product on `stream` without waiting (pinned x, y)."""
+        a, b = self._scalars(alpha, beta)
+        _check(smat_spmv_host_async(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
+                                    _stream_ptr(stream)), "smat_spmv_host_async")
         return y
 
     def features(self) -> dict:

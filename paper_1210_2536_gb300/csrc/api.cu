@@ -604,6 +604,24 @@ smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *a
   return SMAT_OK;
 }
 
+smat_status_t smat_spmv_host_async(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
+                                   void *y_host, void *stream) {
+  TRYS(check_handle(h));
+  if (!alpha || !beta || (h->m > 0 && !y_host) || (h->n > 0 && !x_host)) return SMAT_ERR_INVALID_ARG;
+  if (!variant_ready(h, h->variant)) return SMAT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ts = (size_t)tsize(h);
+  if (!h->stage_x && h->n > 0) TRY(dev_alloc(&h->stage_x, (size_t)h->n * ts));
+  if (!h->stage_y && h->m > 0) TRY(dev_alloc(&h->stage_y, (size_t)h->m * ts));
+  const bool beta_zero = h->dtype == SMAT_F64 ? *(const double *)beta == 0.0 : *(const float *)beta == 0.0f;
+  if (h->n > 0) TRY(cudaMemcpyAsync(h->stage_x, x_host, (size_t)h->n * ts, cudaMemcpyHostToDevice, s));
+  if (!beta_zero && h->m > 0)
+    TRY(cudaMemcpyAsync(h->stage_y, y_host, (size_t)h->m * ts, cudaMemcpyHostToDevice, s));
+  TRY(launch_spmv(h, h->variant, alpha, h->stage_x, beta, h->stage_y, s));
+  if (h->m > 0) TRY(cudaMemcpyAsync(y_host, h->stage_y, (size_t)h->m * ts, cudaMemcpyDeviceToHost, s));
+  return SMAT_OK;
+}
+
 smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
                              void *y_host, void *stream) {
   TRYS(check_handle(h));

@@ -213,3 +213,20 @@ def test_misaligned_vectors_are_safe(dtype):
         assert_close_rows(yb[1:].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
                           f"misaligned {dtype} {smat.VARIANT_NAMES[v]}")
     M.close()
+
+
+def test_async_host_products_on_several_streams():
+    mats = [synth.uniform_random(4000, 7.0, s) for s in range(4)]
+    hs = [make(A)[0] for A in mats]
+    xs = [torch.from_numpy(synth.uniform(i, 1, A.n)).pin_memory() for i, A in enumerate(mats)]
+    ys = [torch.zeros(A.m, dtype=torch.float64).pin_memory() for A in mats]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    for rep in range(2):
+        for i, M in enumerate(hs):
+            M.spmv_host_async(xs[i], ys[i], 2.0, 0.0, stream=streams[i % 2])
+        torch.cuda.synchronize()
+        for i, A in enumerate(mats):
+            ref, scale = reference(A, A.val, xs[i].numpy(), 2.0, 0.0, None)
+            assert_close_rows(ys[i].numpy(), ref, scale, TOL["f64"], f"async host product {i}")
+    for M in hs:
+        M.close()
