@@ -42,6 +42,7 @@ extern "C" {
 
 typedef struct smat_s *smat_handle_t;
 typedef struct smat_batch_s *smat_batch_t;
+typedef struct smat_segments_s *smat_segments_t;
 
 typedef enum {
   SMAT_OK = 0,
@@ -309,6 +310,31 @@ smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info);
 
 /* Free the batch (not its handles).  NULL is a no-op. */
 smat_status_t smat_batch_destroy(smat_batch_t b);
+
+/* ------------------------------------------------------------------------ */
+/* Per-segment plans (Sec. 6: the multi-threaded SMAT splits the nonzeros    */
+/* evenly over threads at whole rows and may choose a format per segment)    */
+/* ------------------------------------------------------------------------ */
+
+/* Split h's rows into `nseg` segments holding about NNZ/nseg stored entries
+ * each (boundaries at whole rows, rounded down to multiples of 8 rows; fewer
+ * segments when rows are too long to split), give every segment its own
+ * handle tuned with `opts` (NULL: as in smat_tune), and batch them.  h must
+ * stay alive while the segments exist.  Returns after `stream` is idle. */
+smat_status_t smat_segments_create(smat_segments_t *out, smat_handle_t h, int32_t nseg,
+                                   const smat_tune_opts_t *opts, void *stream);
+
+/* y = alpha*A*x + beta*y with every segment in its own format, one batched
+ * launch; x[n], y[m] DEVICE pointers of the compute type, alpha/beta HOST
+ * scalars.  Vectors that are not 16-byte aligned take h's own plan. */
+smat_status_t smat_segments_spmv(smat_segments_t s, const void *alpha, const void *x, const void *beta, void *y,
+                                 void *stream);
+
+/* Number of segments, each segment's variant (variants[nseg]) and row starts
+ * (row_starts[nseg + 1]); the arrays may be NULL. */
+smat_status_t smat_segments_info(smat_segments_t s, int32_t *nseg, int32_t *variants, int64_t *row_starts);
+
+smat_status_t smat_segments_destroy(smat_segments_t s);
 
 /* ------------------------------------------------------------------------ */
 /* Mixed-precision conjugate gradients (iterative refinement)               */

@@ -112,6 +112,11 @@ _SIGS = {
     "smat_batch_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_batch_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(smat_batch_info_t)]),
     "smat_batch_destroy": (ctypes.c_int, [_VP]),
+    "smat_segments_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I32, ctypes.POINTER(smat_tune_opts_t),
+                                            _VP]),
+    "smat_segments_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_segments_info": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "smat_segments_destroy": (ctypes.c_int, [_VP]),
     "smat_cg_opts_default": (None, [ctypes.POINTER(smat_cg_opts_t)]),
     "smat_cg_mixed": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(smat_cg_opts_t),
                                      ctypes.POINTER(smat_cg_info_t), _VP]),
@@ -316,6 +321,49 @@ class Batch:
         if getattr(self, "b", None):
             lib().smat_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Segments:
+    """Per-segment plans of one SpMatrix (Sec. 6): nonzero-balanced row segments,
+    each tuned to its own format, run as one batched launch."""
+
+    def __init__(self, M: "SpMatrix", nseg: int, mode="exhaustive", stream=None, **kw):
+        o = smat_tune_opts_default()
+        o.mode = {"learned": SMAT_TUNE_LEARNED, "exhaustive": SMAT_TUNE_EXHAUSTIVE, "rules": SMAT_TUNE_RULES}[mode]
+        for k, v in kw.items():
+            setattr(o, k, v)
+        s = _VP()
+        _check(lib().smat_segments_create(ctypes.byref(s), M.h, int(nseg), ctypes.byref(o), _stream_ptr(stream)),
+               "smat_segments_create")
+        self.s, self.M = s.value, M
+
+    def info(self):
+        n = ctypes.c_int32()
+        lib().smat_segments_info(self.s, ctypes.byref(n), None, None)
+        v = np.zeros(n.value, np.int32)
+        r = np.zeros(n.value + 1, np.int64)
+        _check(lib().smat_segments_info(self.s, ctypes.byref(n), v.ctypes.data, r.ctypes.data), "smat_segments_info")
+        return {"variants": [VARIANT_NAMES[i] for i in v], "row_starts": r.tolist()}
+
+    def spmv(self, x, y=None, alpha=1.0, beta=0.0, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty(self.M.m, dtype=self.M.compute_dtype, device=x.device)
+        a, b = self.M._scalars(alpha, beta)
+        _check(lib().smat_segments_spmv(self.s, ctypes.addressof(a), x.data_ptr(), ctypes.addressof(b), y.data_ptr(),
+                                        _stream_ptr(stream)), "smat_segments_spmv")
+        return y
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().smat_segments_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:
