@@ -231,6 +231,50 @@ void free_format(smat_s *h, int fmt) {
   }
 }
 
+// Kernel search for ELL / DIA (the paper's per-format implementation choice,
+// Sec. 3): time the candidate batch widths once on zero vectors, keep the
+// faster.  Run when the format is built.
+smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
+  int cand[2];
+  const int nc = batch_width_candidates(h, variant, cand);
+  int &slot = variant == SMAT_V_DIA ? h->dia_u : h->ell_u;
+  if (nc == 1) {
+    slot = cand[0];
+    return SMAT_OK;
+  }
+  DevBuf x, y;
+  const size_t xs = (size_t)std::max<int64_t>(h->n, 1) * tsize(h), ys = (size_t)std::max<int64_t>(h->m, 1) * tsize(h);
+  TRY(x.alloc(xs));
+  TRY(y.alloc(ys));
+  TRY(cudaMemsetAsync(x.p, 0, xs, s));
+  const double one = 1.0, zero = 0.0;
+  const float onef = 1.0f, zerof = 0.0f;
+  const void *a = h->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
+  const void *b = h->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
+  cudaEvent_t e0, e1;
+  TRY(cudaEventCreate(&e0));
+  TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_u = cand[0];
+  for (int c = 0; c < nc; ++c) {
+    for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, cand[c], a, x.p, b, y.p, s));
+    float ms[5];
+    for (int r = 0; r < 5; ++r) {
+      TRY(cudaEventRecord(e0, s));
+      TRY(launch_spmv_width(h, variant, cand[c], a, x.p, b, y.p, s));
+      TRY(cudaEventRecord(e1, s));
+      TRY(cudaEventSynchronize(e1));
+      TRY(cudaEventElapsedTime(&ms[r], e0, e1));
+    }
+    std::sort(ms, ms + 5);
+    if (ms[2] < best) { best = ms[2]; best_u = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  slot = best_u;
+  return SMAT_OK;
+}
+
 smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
   if (fmt == SMAT_FMT_CSR) return SMAT_OK;
   if (!h->have_features) TRYS(compute_features(h, s));
@@ -243,9 +287,9 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     TRY(dev_alloc(&c, (size_t)(K * h->P) * 4));
     cudaError_t e = dev_alloc(&v, (size_t)(K * h->P) * h->esz);
     if (e != cudaSuccess) { dev_free(c); return st_of(e); }
-    h->ell_col = (int32_t *)c; h->ell_val = v; h->ell_K = K;
+    h->ell_col = (int32_t *)c; h->ell_val = v; h->ell_K = K; h->ell_u = 0;
     TRY(launch_to_ell(h, K, h->ell_col, h->ell_val, s));
-    return SMAT_OK;
+    return measure_batch_width(h, SMAT_V_ELL, s);
   }
   if (fmt == SMAT_FMT_DIA) {
     if (h->dia_val) return SMAT_OK;
@@ -259,7 +303,8 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     TRY(cudaMemcpyAsync(h->dia_off, h->dia_offsets.data(), (size_t)nd * 4, cudaMemcpyHostToDevice, s));
     TRY(launch_to_dia(h, h->dia_off, nd, h->dia_val, s));
     TRY(cudaStreamSynchronize(s));  // the host offsets buffer must outlive the copy
-    return SMAT_OK;
+    h->dia_u = 0;
+    return measure_batch_width(h, SMAT_V_DIA, s);
   }
   if (fmt == SMAT_FMT_COO) {
     if (h->coo_row || h->coo_empty) return SMAT_OK;

@@ -15,8 +15,8 @@ namespace smat {
 inline int elem_size(smat_dtype_t t) { return t == SMAT_F64 ? 8 : (t == SMAT_F32 ? 4 : 2); }
 inline int64_t pitch_of(int64_t m) { return (m + 31) / 32 * 32; }
 
-// Device allocation with a host-side failure hook: SMAT_TEST_FAIL_ALLOC_AFTER=k
-// makes the k-th allocation of the process (1-based) fail, for error-path tests.
+// Device allocation with a host-side failure hook (smat_test_fail_alloc_after)
+// that makes a chosen allocation fail, for error-path tests.
 cudaError_t dev_alloc(void **p, size_t bytes);
 void dev_free(void *p);
 
@@ -69,6 +69,7 @@ struct smat_s {
 
   // ELL
   int64_t ell_K = 0;
+  int ell_u = 0, dia_u = 0;  // measured batch widths (0: not measured yet)
   int32_t *ell_col = nullptr;
   void *ell_val = nullptr;
   // DIA
@@ -116,6 +117,11 @@ cudaError_t launch_to_dia(const smat_s *h, const int32_t *d_off, int64_t nd, voi
 size_t carry_bytes_needed(const smat_s *h, int variant);
 // Kernel launches one product through `variant` issues.
 int spmv_launch_count(const smat_s *h, int variant);
+// Candidate batch widths of an ELL / DIA product (returns how many: 1 or 2).
+int batch_width_candidates(const smat_s *h, int variant, int out[2]);
+// ELL / DIA product with an explicit batch width (for measuring it).
+cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, const void *alpha, const void *x,
+                              const void *beta, void *y, cudaStream_t s);
 // SpMV through one variant; alpha/beta are host scalars of the compute type.
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,
                         const void *beta, void *y, cudaStream_t s);

@@ -426,14 +426,14 @@ __global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long co
 // padding (column -1) gathers x[0] and is dropped by a select, so no load
 // sits behind a branch.
 // ---------------------------------------------------------------------------
-template <typename V, int R, int MODE>
+template <typename V, int R, int MODE, int U>
 __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
                                                   long long P, long long K,
                                                   const typename Compute<V>::T *__restrict__ x,
                                                   Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m) {
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) ell_group<V, R, MODE>(ecol, eval, P, K, x, ep, y, m, i0);
+  if (i0 < m) ell_group<V, R, MODE, U>(ecol, eval, P, K, x, ep, y, m, i0);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ec
 // computation decided by zero filling); positions whose column falls outside
 // the matrix gather x[0] and are dropped by a select.
 // ---------------------------------------------------------------------------
-template <typename V, int R, int MODE>
+template <typename V, int R, int MODE, int U>
 __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ off, int nd,
                                                   const V *__restrict__ dval, long long P,
                                                   const typename Compute<V>::T *__restrict__ x,
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ of
   for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
   __syncthreads();
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) dia_group<V, R, MODE>(s_off, nd, dval, P, x, ep, y, m, n, i0);
+  if (i0 < m) dia_group<V, R, MODE, U>(s_off, nd, dval, P, x, ep, y, m, n, i0);
 }
 
 int grid_for(long long work, int block, int max_blocks) {
@@ -473,9 +473,53 @@ constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 #endif
 constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 
+// ELL / DIA launches with a batch width U chosen at run time from 1..16/R.
+template <typename V, int MODE, int U>
+void launch_ell_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
+                  typename Compute<V>::T *y, cudaStream_t s) {
+  constexpr int R = 16 / (int)sizeof(V);
+  const long long m = h->m;
+  ell_kernel<V, R, MODE, U><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
+      h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, ep, y, m);
+}
+
+template <typename V, int MODE, int U>
+void launch_dia_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
+                  typename Compute<V>::T *y, cudaStream_t s) {
+  constexpr int R = 16 / (int)sizeof(V);
+  const long long m = h->m;
+  dia_kernel<V, R, MODE, U><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
+      h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, ep, y, m, h->n);
+}
+
+template <typename V, int MODE, bool DIA>
+void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
+                    typename Compute<V>::T *y, cudaStream_t s, int u_req) {
+  constexpr int UMAX = 16 / (16 / (int)sizeof(V));  // 16 / R
+  const int u_tuned = DIA ? h->dia_u : h->ell_u;
+  const int u = u_req > 0 ? u_req : (u_tuned > 0 ? u_tuned : batch_width(DIA ? h->dia_nd : h->ell_K, UMAX));
+#define SMAT_UCASE(k)                                                      \
+  case k:                                                                  \
+    if constexpr (k <= UMAX) {                                             \
+      if (DIA) launch_dia_u<V, MODE, k>(h, x, ep, y, s);                   \
+      else launch_ell_u<V, MODE, k>(h, x, ep, y, s);                       \
+    }                                                                      \
+    break;
+  switch (u) {
+    SMAT_UCASE(1) SMAT_UCASE(2) SMAT_UCASE(3) SMAT_UCASE(4) SMAT_UCASE(5) SMAT_UCASE(6) SMAT_UCASE(7)
+    default:
+      if constexpr (UMAX >= 8) {
+        if (DIA) launch_dia_u<V, MODE, 8>(h, x, ep, y, s);
+        else launch_ell_u<V, MODE, 8>(h, x, ep, y, s);
+      }
+      break;
+  }
+#undef SMAT_UCASE
+}
+
 template <typename V, int MODE>
 cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha, const void *x_p,
-                      typename Compute<V>::T beta, void *y_p, cudaStream_t s) {
+                      typename Compute<V>::T beta, void *y_p, cudaStream_t s, int u_req) {
   typedef typename Compute<V>::T T;
   const Epi<T, MODE> ep{alpha, beta};
   const T *x = (const T *)x_p;
@@ -511,16 +555,12 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       if (tiles > 1)
         carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
     } break;
-    case SMAT_V_ELL: {
-      constexpr int R = 16 / (int)sizeof(V);
-      ell_kernel<V, R, MODE><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
-          h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, ep, y, m);
-    } break;
-    case SMAT_V_DIA: {
-      constexpr int R = 16 / (int)sizeof(V);
-      dia_kernel<V, R, MODE><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
-          h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, ep, y, m, h->n);
-    } break;
+    case SMAT_V_ELL:
+      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, u_req);
+      break;
+    case SMAT_V_DIA:
+      launch_ell_dia<V, MODE, true>(h, x, ep, y, s, u_req);
+      break;
     case SMAT_V_COO: {
       if (h->coo_nempty > 0) {
         scale_rows_kernel<T, MODE><<<grid_for(h->coo_nempty, 256, 152 * 8), 256, 0, s>>>(h->coo_empty, h->coo_nempty,
@@ -547,14 +587,14 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
 
 template <typename V>
 cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p, const void *beta_p,
-                       void *y_p, cudaStream_t s) {
+                       void *y_p, cudaStream_t s, int u_req) {
   typedef typename Compute<V>::T T;
   const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
   if (h->m == 0) return cudaSuccess;
   switch (epi_mode((double)alpha, (double)beta)) {
-    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s);
-    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s);
-    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s);
+    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s, u_req);
+    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s, u_req);
+    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s, u_req);
   }
 }
 
@@ -589,9 +629,26 @@ cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const v
   if ((variant == SMAT_V_ELL || variant == SMAT_V_DIA) && (((uintptr_t)x | (uintptr_t)y) & 15u) != 0)
     variant = SMAT_V_CSR_SCALAR;
   switch (h->dtype) {
-    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s);
-    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s);
-    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s);
+    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, 0);
+    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, 0);
+    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, 0);
+  }
+}
+
+int batch_width_candidates(const smat_s *h, int variant, int out[2]) {
+  const int umax = 16 / (16 / elem_size(h->dtype));
+  const long long count = variant == SMAT_V_DIA ? h->dia_nd : h->ell_K;
+  out[0] = umax;                      // full width (dead slots when count < umax)
+  out[1] = batch_width(count, umax);  // fewest dead slots
+  return out[1] != out[0] ? 2 : 1;
+}
+
+cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, const void *alpha, const void *x, const void *beta,
+                              void *y, cudaStream_t s) {
+  switch (h->dtype) {
+    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, u);
+    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, u);
+    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, u);
   }
 }
 

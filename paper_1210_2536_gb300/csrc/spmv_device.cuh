@@ -49,6 +49,20 @@ __device__ __forceinline__ float madd(float acc, float v, float x) { return fmaf
 // EXACT rounds beta*y_i and the sum separately; otherwise they are fused.
 enum : int { EPI_COPY = 0, EPI_SCALE = 1, EPI_AXPBY = 2 };
 
+// Batch width for `count` slots (ELL) or diagonals (DIA) with at most umax per
+// batch: all of them when they fit, else the width in [umax/2, umax] that
+// leaves the fewest unused slots in the last batch (the wider on ties).
+inline int batch_width(long long count, int umax) {
+  if (count <= umax) return count < 1 ? 1 : (int)count;
+  int best = umax;
+  long long waste = (count + umax - 1) / umax * umax - count;
+  for (int u = umax - 1; u >= umax / 2 && u >= 1; --u) {
+    const long long w = (count + u - 1) / u * u - count;
+    if (w < waste) { waste = w; best = u; }
+  }
+  return best;
+}
+
 inline int epi_mode(double alpha, double beta) {
   return beta != 0.0 ? EPI_AXPBY : (alpha != 1.0 ? EPI_SCALE : EPI_COPY);
 }
@@ -152,15 +166,16 @@ __device__ __forceinline__ void write_rows(T *__restrict__ y, long long i0, long
 }
 
 // One thread's R consecutive rows [i0, i0 + R) of an ELL product
-// (column-major, pitch P, K slots).  16/R slots are loaded before their
-// gathers are issued; padding (column -1) is dropped.
-template <typename V, int R, int MODE>
+// (column-major, pitch P, K slots).  U slots are loaded before their gathers
+// are issued (U <= 16/R; the host picks U so that few batch slots go unused,
+// since an unused slot still issues its multiply-adds); padding (column -1)
+// is dropped.
+template <typename V, int R, int MODE, int U = 16 / R>
 __device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, const V *__restrict__ eval, long long P,
                                           long long K, const typename Compute<V>::T *__restrict__ x,
                                           const Epi<typename Compute<V>::T, MODE> &ep,
                                           typename Compute<V>::T *__restrict__ y, long long m, long long i0) {
   typedef typename Compute<V>::T T;
-  constexpr int U = 16 / R;
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0;
@@ -193,17 +208,17 @@ __device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, cons
 }
 
 // One thread's R consecutive rows of a DIA product; `off` holds the nd
-// ascending diagonal offsets (shared or global memory).  Fill zeros are
+// ascending diagonal offsets (shared or global memory), U diagonals per batch
+// (chosen on the host as for ELL).  Fill zeros are
 // multiplied like stored values; positions whose column falls outside the
 // matrix are dropped.
-template <typename V, int R, int MODE>
+template <typename V, int R, int MODE, int U = 16 / R>
 __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *__restrict__ dval, long long P,
                                           const typename Compute<V>::T *__restrict__ x,
                                           const Epi<typename Compute<V>::T, MODE> &ep,
                                           typename Compute<V>::T *__restrict__ y, long long m, long long n,
                                           long long i0) {
   typedef typename Compute<V>::T T;
-  constexpr int U = 16 / R;
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0;
