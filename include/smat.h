@@ -397,9 +397,10 @@ smat_status_t smat_cast_f64_to_bf16(const double *in, uint16_t *out, int64_t n, 
  * pointers, and alpha/beta as HOST pointers to one scalar of the compute type
  * (FP64 for SMAT_F64, FP32 otherwise).  The input must be canonical CSR; it is
  * not validated.
- * The kernel's only scratch, one carry per tile of 2048 merge items, lives in
- * a fixed 768 KiB array in the library's device memory, held by every GPU
- * that loads the library until the process exits.  Limit: ceil((m + nnz) /
+ * The kernels' only scratch, one carry and one merge-path coordinate per
+ * tile of 2048 merge items, lives in a fixed 1.25 MiB array in the library's
+ * device memory, held by every GPU that loads the library until the process
+ * exits.  Limit: ceil((m + nnz) /
  * 2048) <= 65536, i.e. m + nnz <= 134,217,728; larger inputs return
  * SMAT_ERR_UNSUPPORTED without launching anything.  The first call on each
  * device looks up the array's address (cudaGetSymbolAddress); make that first

@@ -343,6 +343,7 @@ smat_status_t ensure_scratch(smat_s *h, int variant) {
 
 bool variant_ready(const smat_s *h, int v) {
   int fmt = variant_format(v);
+  if (v == SMAT_V_CSR_MERGE && h->m > 0 && !h->merge_coords) return false;
   if (fmt == SMAT_FMT_ELL && !h->ell_val) return false;
   if (fmt == SMAT_FMT_DIA && !h->dia_val) return false;
   if (fmt == SMAT_FMT_COO && !h->coo_row && !(h->nnz == 0)) return false;
@@ -357,6 +358,12 @@ smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
   if (fmt != SMAT_FMT_CSR && !h->have_features) TRYS(compute_features(h, s));
   TRYS(build_format(h, fmt, s));
   TRYS(ensure_scratch(h, v));
+  if (v == SMAT_V_CSR_MERGE && !h->merge_coords && h->m > 0) {
+    void *p = nullptr;
+    TRY(dev_alloc(&p, (size_t)(merge_tiles(h->m, h->nnz) + 1) * 8));
+    h->merge_coords = p;
+    TRY(launch_merge_partition(h->rowptr, h->m, h->nnz, h->merge_coords, s));
+  }
   return SMAT_OK;
 }
 
@@ -553,7 +560,7 @@ smat_status_t smat_destroy(smat_handle_t h) {
   if (!h) return SMAT_OK;
   dev_free(h->rowptr); dev_free(h->colidx); dev_free(h->val);
   free_format(h, SMAT_FMT_ELL); free_format(h, SMAT_FMT_DIA); free_format(h, SMAT_FMT_COO);
-  dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y);
+  dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y); dev_free(h->merge_coords);
   delete h;
   return SMAT_OK;
 }

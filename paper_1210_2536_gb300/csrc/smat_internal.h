@@ -81,6 +81,8 @@ struct smat_s {
   int32_t *coo_empty = nullptr;  // list of empty rows (y = beta*y there)
   int64_t coo_nempty = 0;
 
+  // merge-path tile coordinates (int2 per tile boundary), computed once
+  void *merge_coords = nullptr;
   // scratch for merge-path and COO carries
   void *carry = nullptr;
   size_t carry_bytes = 0;
@@ -113,6 +115,11 @@ cudaError_t launch_to_ell(const smat_s *h, int64_t K, int32_t *col, void *val, c
 cudaError_t launch_to_dia(const smat_s *h, const int32_t *d_off, int64_t nd, void *val,
                           cudaStream_t s);
 
+// Merge-path tiles of an m x ? matrix with nnz entries, and the kernel that
+// writes their (ntiles + 1) boundary coordinates (int2) to `coords`.
+long long merge_tiles(long long m, long long nnz);
+cudaError_t launch_merge_partition(const int32_t *rowptr, long long m, long long nnz, void *coords,
+                                   cudaStream_t s);
 // Size in bytes of the carry scratch a variant needs (0 if none).
 size_t carry_bytes_needed(const smat_s *h, int variant);
 // Kernel launches one product through `variant` issues.

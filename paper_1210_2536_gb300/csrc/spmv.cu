@@ -211,6 +211,19 @@ __device__ __forceinline__ void merge_search(const int32_t *__restrict__ rowptr,
 
 // s_v[j] = val[b0 + j], s_x[j] = x[col[b0 + j]] for j < cnt: IPT coalesced
 // items per thread, every index and value load issued before the gathers.
+// Merge-path coordinates (a, b) of every tile boundary d = t*tile, t = 0..ntiles
+// (the last one clamped to m + nnz): one thread per boundary.
+__global__ void merge_partition_kernel(const int32_t *__restrict__ rowptr, long long m, long long nnz, long long tile,
+                                       long long ntiles, int2 *__restrict__ coords) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long d = t * tile < m + nnz ? t * tile : m + nnz;
+    long long a, b;
+    merge_search(rowptr, m, nnz, d, &a, &b);
+    coords[t] = make_int2((int)a, (int)b);
+  }
+}
+
 template <typename V, typename T, int NT, int IPT>
 __device__ __forceinline__ void stage_pairs(const int32_t *__restrict__ col, const V *__restrict__ val,
                                             const T *__restrict__ x, long long b0, int cnt, T *s_v, T *s_x) {
@@ -239,22 +252,17 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
                                                        const int32_t *__restrict__ col,
                                                        const V *__restrict__ val, const T *__restrict__ x,
                                                        Epi<T, MODE> ep, T *__restrict__ y, long long m,
-                                                       long long nnz, int32_t *carry_row, T *carry_val) {
+                                                       long long nnz, const int2 *__restrict__ coords,
+                                                       int32_t *carry_row, T *carry_val) {
   constexpr int TILE = NT * IPT;
   __shared__ int32_t s_rowend[TILE + 1];
   __shared__ T s_v[TILE], s_x[TILE];
-  __shared__ long long s_coord[4];
   const long long total = m + nnz;
   const long long d0 = (long long)blockIdx.x * TILE;
   const long long d1 = d0 + TILE < total ? d0 + TILE : total;
-  if (threadIdx.x < 2) {
-    long long a, b;
-    merge_search(rowptr, m, nnz, threadIdx.x == 0 ? d0 : d1, &a, &b);
-    s_coord[2 * threadIdx.x] = a;
-    s_coord[2 * threadIdx.x + 1] = b;
-  }
-  __syncthreads();
-  const long long a0 = s_coord[0], b0 = s_coord[1], a1 = s_coord[2], b1 = s_coord[3];
+  // the tile's merge-path coordinates, computed once per matrix
+  const int2 c0 = __ldg(coords + blockIdx.x), c1 = __ldg(coords + blockIdx.x + 1);
+  const long long a0 = c0.x, b0 = c0.y, a1 = c1.x, b1 = c1.y;
   const int nrows = (int)(a1 - a0), nnzs = (int)(b1 - b0);
   for (int i = threadIdx.x; i < nrows; i += NT) s_rowend[i] = __ldg(rowptr + a0 + 1 + i);
   stage_pairs<V, T, NT, IPT>(col, val, x, b0, nnzs, s_v, s_x);
@@ -549,7 +557,7 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       int32_t *crow = (int32_t *)h->carry;
       T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
       csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
-          h->rowptr, h->colidx, val, x, ep, y, m, h->nnz, crow, cval);
+          h->rowptr, h->colidx, val, x, ep, y, m, h->nnz, (const int2 *)h->merge_coords, crow, cval);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       if (tiles > 1)
@@ -599,6 +607,15 @@ cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const 
 }
 
 }  // namespace
+
+long long merge_tiles(long long m, long long nnz) { return (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT); }
+
+cudaError_t launch_merge_partition(const int32_t *rowptr, long long m, long long nnz, void *coords, cudaStream_t s) {
+  const long long tiles = merge_tiles(m, nnz);
+  merge_partition_kernel<<<grid_for(tiles + 1, 256, 152 * 8), 256, 0, s>>>(rowptr, m, nnz, MERGE_NT * MERGE_IPT,
+                                                                          tiles, (int2 *)coords);
+  return cudaGetLastError();
+}
 
 size_t carry_bytes_needed(const smat_s *h, int variant) {
   long long tiles = 0;
@@ -663,12 +680,13 @@ cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, const void *a
 // once its time-critical loop has started.  For them this entry point keeps
 // the only scratch the kernel needs -- one carry (row, partial sum) per tile
 // -- in a fixed array in the library's own device memory.  Every GPU that
-// loads the library holds that array (768 KiB) until the process exits.
+// loads the library holds that array (1.25 MiB) until the process exits.
 // The array's address is looked up once per device, on the first call made
 // with that device current; make that first call before any stream capture.
 // All calls share the array, so calls whose kernels overlap on the GPU race:
 // order them on one stream, or synchronise between them.  Nothing in the
-// array has to start at zero: each call writes every carry it later reads.
+// array has to start at zero: each call writes every carry and tile
+// coordinate it later reads.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -678,7 +696,10 @@ namespace {
 constexpr long long NOALLOC_MAX_TILES = 65536;
 // per tile: an int32 row (256 KiB in all) and a value of up to 8 bytes (512 KiB)
 constexpr size_t NOALLOC_ROW_BYTES = NOALLOC_MAX_TILES * 4;
-constexpr size_t NOALLOC_BYTES = NOALLOC_ROW_BYTES + NOALLOC_MAX_TILES * 8;
+// then a value of up to 8 bytes per tile (512 KiB), then the tile boundaries'
+// merge-path coordinates, 8 bytes each (512 KiB + 8)
+constexpr size_t NOALLOC_COORD_OFFSET = NOALLOC_ROW_BYTES + NOALLOC_MAX_TILES * 8;
+constexpr size_t NOALLOC_BYTES = NOALLOC_COORD_OFFSET + (NOALLOC_MAX_TILES + 1) * 8;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -711,9 +732,12 @@ cudaError_t merge_noalloc_mode(long long m, long long nnz, const int32_t *rowptr
   const long long tiles = (m + nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
   int32_t *crow = (int32_t *)scratch;
   T *cval = (T *)(scratch + NOALLOC_ROW_BYTES);
+  int2 *coords = (int2 *)(scratch + NOALLOC_COORD_OFFSET);
+  cudaError_t e = launch_merge_partition(rowptr, m, nnz, coords, s);
+  if (e != cudaSuccess) return e;
   csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
-      rowptr, colidx, (const V *)vals, (const T *)x_p, ep, (T *)y_p, m, nnz, crow, cval);
-  cudaError_t e = cudaGetLastError();
+      rowptr, colidx, (const V *)vals, (const T *)x_p, ep, (T *)y_p, m, nnz, coords, crow, cval);
+  e = cudaGetLastError();
   if (e != cudaSuccess || tiles <= 1) return e;
   carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, (T *)y_p);
   return cudaGetLastError();
