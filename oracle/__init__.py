@@ -10,6 +10,8 @@ Every function restates a definition of the paper:
   spmv_csr_threads  the same on T threads, nonzero-balanced row split (Sec. 6)
   features        Table "Feature parameters of a sparse matrix" (Sec. 4)
   to_ell/to_dia/to_coo  the four basic storage formats (Sec. 2.1)
+  to_hyb/sell_layout/to_sell/to_bcsr  further GPU formats left to future work
+                  in Sec. 8 (HYB, SELL-C-sigma, BCSR; published definitions)
   mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
 Readings taken where the paper is silent are listed in ``oracle.c``.
 """
@@ -65,6 +67,17 @@ def lib():
         L.oracle_dia_offsets.restype = i64
         L.oracle_to_dia.argtypes = [i64, vp, vp, vp, i64, vp, i64, i64, vp]
         L.oracle_to_coo.argtypes = [i64, vp, vp]
+        L.oracle_hyb_width.argtypes = [i64, vp]
+        L.oracle_hyb_width.restype = i64
+        L.oracle_to_hyb.argtypes = [i64, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+        L.oracle_to_hyb.restype = i64
+        L.oracle_sell_layout.argtypes = [i64, vp, i64, i64, vp, vp, vp]
+        L.oracle_sell_layout.restype = i64
+        L.oracle_to_sell.argtypes = [i64, vp, vp, vp, i64, i64, vp, vp, vp, vp, vp]
+        L.oracle_to_bcsr.argtypes = [i64, i64, vp, vp, vp, i64, i64, vp, vp, vp]
+        L.oracle_to_bcsr.restype = i64
+        L.oracle_bcsr_choose.argtypes = [i64, i64, vp, vp, i64, vp]
+        L.oracle_bcsr_choose.restype = i64
         L.oracle_round_bf16.argtypes = [i64, vp, vp]
         L.oracle_bf16_to_double.argtypes = [i64, vp, vp]
         L.oracle_mlp_param_count.restype = i64
@@ -212,6 +225,84 @@ def to_coo(m, rowptr):
     row = np.empty(nnz, dtype=np.int32)
     lib().oracle_to_coo(m, prp, row.ctypes.data)
     return row
+
+
+def hyb_width(m, rowptr) -> int:
+    """HYB's ELL width K: the largest k with 3 * #{rows with >= k entries} >= M."""
+    rp, prp = _c(rowptr, np.int32)
+    return int(lib().oracle_hyb_width(m, prp))
+
+
+def to_hyb(m, rowptr, colidx, val, K=None, P=None):
+    """HYB = ELL part (K x P, column-major) + COO part (row, col, val) of the
+    entries past each row's first K.  Returns (ell_col, ell_val, coo_row,
+    coo_col, coo_val, K, P)."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    K = hyb_width(m, rp) if K is None else K
+    P = pitch(m) if P is None else P
+    ncoo = int(lib().oracle_to_hyb(m, prp, pci, v.ctypes.data, v.itemsize, K, P, None, None, None, None, None))
+    ecol = np.empty(K * P, dtype=np.int32)
+    ev = np.empty(K * P, dtype=v.dtype)
+    crow = np.empty(ncoo, dtype=np.int32)
+    ccol = np.empty(ncoo, dtype=np.int32)
+    cv = np.empty(ncoo, dtype=v.dtype)
+    lib().oracle_to_hyb(m, prp, pci, v.ctypes.data, v.itemsize, K, P, ecol.ctypes.data, ev.ctypes.data,
+                        crow.ctypes.data, ccol.ctypes.data, cv.ctypes.data)
+    return ecol, ev, crow, ccol, cv, K, P
+
+
+SELL_C = 32
+
+
+def sell_layout(m, rowptr, sigma, C=SELL_C):
+    """SELL-C-sigma slice structure: (perm[Mp], width[Mp/C], slice_ptr[Mp/C + 1])."""
+    rp, prp = _c(rowptr, np.int32)
+    mp = (m + C - 1) // C * C
+    perm = np.empty(mp, dtype=np.int32)
+    width = np.empty(mp // C, dtype=np.int32)
+    sptr = np.empty(mp // C + 1, dtype=np.int64)
+    lib().oracle_sell_layout(m, prp, C, sigma, perm.ctypes.data, width.ctypes.data, sptr.ctypes.data)
+    return perm, width, sptr
+
+
+def to_sell(m, rowptr, colidx, val, sigma, C=SELL_C):
+    """SELL-C-sigma arrays: (perm, width, slice_ptr, col, val)."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    perm, width, sptr = sell_layout(m, rp, sigma, C)
+    slots = int(sptr[-1])
+    col = np.empty(slots, dtype=np.int32)
+    out = np.empty(slots, dtype=v.dtype)
+    lib().oracle_to_sell(m, prp, pci, v.ctypes.data, v.itemsize, C, perm.ctypes.data, width.ctypes.data,
+                         sptr.ctypes.data, col.ctypes.data, out.ctypes.data)
+    return perm, width, sptr, col, out
+
+
+def to_bcsr(m, n, rowptr, colidx, val, b):
+    """BCSR with b x b blocks: (browptr[ceil(M/b)+1], bcol[nb], bval[nb*b*b])."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    mb = (m + b - 1) // b
+    brp = np.empty(mb + 1, dtype=np.int32)
+    nb = int(lib().oracle_to_bcsr(m, n, prp, pci, None, v.itemsize, b, brp.ctypes.data, None, None))
+    bcol = np.empty(nb, dtype=np.int32)
+    bval = np.empty(nb * b * b, dtype=v.dtype)
+    lib().oracle_to_bcsr(m, n, prp, pci, v.ctypes.data, v.itemsize, b, brp.ctypes.data, bcol.ctypes.data,
+                         bval.ctypes.data)
+    return brp, bcol, bval
+
+
+def bcsr_choose(m, n, rowptr, colidx, elem_size):
+    """(b, nblocks) for the b in {2, 4, 8} with the fewest BCSR bytes."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    nb = np.zeros(1, dtype=np.int64)
+    b = int(lib().oracle_bcsr_choose(m, n, prp, pci, elem_size, nb.ctypes.data))
+    return b, int(nb[0])
 
 
 # ---------------------------------------------------------------------------

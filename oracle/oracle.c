@@ -303,6 +303,206 @@ void oracle_to_coo(int64_t m, const int32_t *rowptr, int32_t *row) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Further GPU formats.  Sec. 2.1 covers DIA, ELL, CSR and COO; Sec. 1 and    */
+/* Sec. 8 leave more formats to future work.  The three below follow the      */
+/* published methods named beside each; the layouts are this library's.       */
+/* ------------------------------------------------------------------------ */
+
+/* HYB (Bell & Garland, 2009): an ELL part of width K plus a COO part holding
+ * each row's entries past its first K.  K is the largest k >= 0 for which at
+ * least a third of the rows hold k or more entries (3 * #{i : rd_i >= k} >= M);
+ * K = 0 when M = 0. */
+int64_t oracle_hyb_width(int64_t m, const int32_t *rowptr) {
+  if (m <= 0) return 0;
+  int64_t maxrd = oracle_max_rd(m, rowptr);
+  int64_t *hist = (int64_t *)calloc((size_t)maxrd + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < m; ++i) hist[rowptr[i + 1] - rowptr[i]] += 1;
+  int64_t rows_ge = 0, K = 0;
+  for (int64_t k = maxrd; k >= 1; --k) {
+    rows_ge += hist[k];               /* rows with k or more entries */
+    if (3 * rows_ge >= m) { K = k; break; }
+  }
+  free(hist);
+  return K;
+}
+
+/* ELL part: slot s < min(rd_i, K) of row i, at s*P + i, holds the row's s-th
+ * entry; every other slot (and rows M..P-1) holds column -1 / value +0.
+ * COO part: the entries of each row past its first K, rows ascending and
+ * columns ascending within a row.  Returns the COO part's length; the COO
+ * arrays may be NULL to count only, the ELL arrays NULL to skip them. */
+int64_t oracle_to_hyb(int64_t m, const int32_t *rowptr, const int32_t *colidx, const void *val,
+                      int64_t elem_size, int64_t K, int64_t P, int32_t *ell_col, void *ell_val,
+                      int32_t *coo_row, int32_t *coo_col, void *coo_val) {
+  const unsigned char *iv = (const unsigned char *)val;
+  if (ell_col && ell_val) {
+    unsigned char *ev = (unsigned char *)ell_val;
+    for (int64_t s = 0; s < K; ++s)
+      for (int64_t i = 0; i < P; ++i) {
+        int64_t pos = s * P + i;
+        int64_t rd = (i < m) ? (int64_t)rowptr[i + 1] - rowptr[i] : 0;
+        if (s < rd) {
+          ell_col[pos] = colidx[rowptr[i] + s];
+          memcpy(ev + pos * elem_size, iv + (rowptr[i] + s) * elem_size, (size_t)elem_size);
+        } else {
+          ell_col[pos] = -1;
+          memset(ev + pos * elem_size, 0, (size_t)elem_size);
+        }
+      }
+  }
+  int64_t c = 0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t k = (int64_t)rowptr[i] + K; k < rowptr[i + 1]; ++k) {
+      if (coo_row) {
+        coo_row[c] = (int32_t)i;
+        coo_col[c] = colidx[k];
+        memcpy((unsigned char *)coo_val + c * elem_size, iv + k * elem_size, (size_t)elem_size);
+      }
+      ++c;
+    }
+  return c;
+}
+
+/* SELL-C-sigma (Kreutzer, Hager, Wellein, Fehske & Bishop, 2014).  Rows are
+ * sorted by decreasing length inside windows of sigma consecutive rows (equal
+ * lengths keep their row order); the sorted sequence, padded with empty
+ * positions to Mp = M rounded up to C, is cut into slices of C positions, and
+ * each slice is a C-row column-major ELL block as wide as its longest row.
+ *   perm[p]       row at sorted position p (-1 for positions M..Mp-1)
+ *   width[s]      longest row length in slice s
+ *   slice_ptr[s]  sum over slices t < s of C * width[t]  (nslices + 1 values)
+ * Entry j of the row at position s*C + l is slot slice_ptr[s] + j*C + l;
+ * slots past the row's length hold column -1 / value +0.  sigma must be a
+ * positive multiple of C.  Returns the number of slots; perm, width and
+ * slice_ptr must hold Mp, Mp/C and Mp/C + 1 values. */
+typedef struct { int64_t len, row; } sell_key;
+static int sell_key_cmp(const void *a, const void *b) {
+  const sell_key *x = (const sell_key *)a, *y = (const sell_key *)b;
+  if (x->len != y->len) return x->len > y->len ? -1 : 1;   /* longer first */
+  return x->row < y->row ? -1 : (x->row > y->row ? 1 : 0);  /* then row order */
+}
+int64_t oracle_sell_layout(int64_t m, const int32_t *rowptr, int64_t C, int64_t sigma, int32_t *perm,
+                           int32_t *width, int64_t *slice_ptr) {
+  const int64_t Mp = (m + C - 1) / C * C, ns = Mp / C;
+  sell_key *keys = (sell_key *)malloc((size_t)(sigma > 0 ? sigma : 1) * sizeof(sell_key));
+  for (int64_t w0 = 0; w0 < m; w0 += sigma) {
+    int64_t cnt = (m - w0 < sigma) ? m - w0 : sigma;
+    for (int64_t q = 0; q < cnt; ++q) {
+      keys[q].row = w0 + q;
+      keys[q].len = (int64_t)rowptr[w0 + q + 1] - rowptr[w0 + q];
+    }
+    qsort(keys, (size_t)cnt, sizeof(sell_key), sell_key_cmp);
+    for (int64_t q = 0; q < cnt; ++q) perm[w0 + q] = (int32_t)keys[q].row;
+  }
+  free(keys);
+  for (int64_t p = m; p < Mp; ++p) perm[p] = -1;
+  slice_ptr[0] = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t wmax = 0;
+    for (int64_t l = 0; l < C; ++l) {
+      int32_t r = perm[s * C + l];
+      int64_t len = r >= 0 ? (int64_t)rowptr[r + 1] - rowptr[r] : 0;
+      if (len > wmax) wmax = len;
+    }
+    width[s] = (int32_t)wmax;
+    slice_ptr[s + 1] = slice_ptr[s] + C * wmax;
+  }
+  return slice_ptr[ns];
+}
+
+void oracle_to_sell(int64_t m, const int32_t *rowptr, const int32_t *colidx, const void *val, int64_t elem_size,
+                    int64_t C, const int32_t *perm, const int32_t *width, const int64_t *slice_ptr,
+                    int32_t *sell_col, void *sell_val) {
+  const int64_t ns = (m + C - 1) / C;
+  const unsigned char *iv = (const unsigned char *)val;
+  unsigned char *ov = (unsigned char *)sell_val;
+  for (int64_t s = 0; s < ns; ++s)
+    for (int64_t j = 0; j < width[s]; ++j)
+      for (int64_t l = 0; l < C; ++l) {
+        int64_t slot = slice_ptr[s] + j * C + l;
+        int32_t r = perm[s * C + l];
+        int64_t len = r >= 0 ? (int64_t)rowptr[r + 1] - rowptr[r] : 0;
+        if (j < len) {
+          sell_col[slot] = colidx[rowptr[r] + j];
+          memcpy(ov + slot * elem_size, iv + (rowptr[r] + j) * elem_size, (size_t)elem_size);
+        } else {
+          sell_col[slot] = -1;
+          memset(ov + slot * elem_size, 0, (size_t)elem_size);
+        }
+      }
+}
+
+/* BCSR with b x b blocks (block compressed sparse row, the register-blocked
+ * format of Im & Yelick).  Block row I covers rows I*b .. I*b+b-1; its blocks
+ * are the distinct block columns J = col / b of those rows' entries, in
+ * ascending order.  Block k stores a(I*b + r, J*b + c) at k*b*b + r*b + c and
+ * +0 where nothing is stored (also past the last row or column).  browptr
+ * holds ceil(M/b) + 1 values.  Returns the number of blocks; bcol and bval may
+ * be NULL to count only (browptr is still filled). */
+static int int_cmp(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+int64_t oracle_to_bcsr(int64_t m, int64_t n, const int32_t *rowptr, const int32_t *colidx, const void *val,
+                       int64_t elem_size, int64_t b, int32_t *browptr, int32_t *bcol, void *bval) {
+  const int64_t mb = (m + b - 1) / b, nbc = (n + b - 1) / b;
+  int64_t *stamp = (int64_t *)malloc((size_t)(nbc > 0 ? nbc : 1) * sizeof(int64_t));
+  int32_t *list = (int32_t *)malloc((size_t)(nbc > 0 ? nbc : 1) * sizeof(int32_t));
+  for (int64_t J = 0; J < nbc; ++J) stamp[J] = -1;
+  const unsigned char *iv = (const unsigned char *)val;
+  unsigned char *ov = (unsigned char *)bval;
+  int64_t nb = 0;
+  browptr[0] = 0;
+  for (int64_t I = 0; I < mb; ++I) {
+    int64_t cnt = 0;
+    for (int64_t i = I * b; i < I * b + b && i < m; ++i)
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        int32_t J = colidx[k] / (int32_t)b;
+        if (stamp[J] != I) { stamp[J] = I; list[cnt++] = J; }
+      }
+    qsort(list, (size_t)cnt, sizeof(int32_t), int_cmp);
+    if (bcol && bval) {
+      for (int64_t q = 0; q < cnt; ++q) bcol[nb + q] = list[q];
+      memset(ov + nb * b * b * elem_size, 0, (size_t)(cnt * b * b * elem_size));
+      for (int64_t i = I * b; i < I * b + b && i < m; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+          int32_t J = colidx[k] / (int32_t)b;
+          int64_t lo = 0, hi = cnt;  /* block q with list[q] == J */
+          while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (list[mid] < J) lo = mid + 1; else hi = mid;
+          }
+          int64_t pos = (nb + lo) * b * b + (i - I * b) * b + (colidx[k] - (int64_t)J * b);
+          memcpy(ov + pos * elem_size, iv + k * elem_size, (size_t)elem_size);
+        }
+    }
+    nb += cnt;
+    browptr[I + 1] = (int32_t)nb;
+  }
+  free(stamp);
+  free(list);
+  return nb;
+}
+
+/* Block size: the b in {2, 4, 8} whose BCSR moves the fewest bytes,
+ * nblocks(b) * (b*b*elem_size + 4) + 4 * (ceil(M/b) + 1); ties go to the
+ * smaller b.  Returns b and writes the block count. */
+int64_t oracle_bcsr_choose(int64_t m, int64_t n, const int32_t *rowptr, const int32_t *colidx, int64_t elem_size,
+                           int64_t *nblocks) {
+  int64_t best_b = 0, best_nb = 0;
+  double best_bytes = 0.0;
+  int32_t *brp = (int32_t *)malloc((size_t)(m / 2 + 2) * sizeof(int32_t));
+  for (int64_t b = 2; b <= 8; b *= 2) {
+    int64_t nb = oracle_to_bcsr(m, n, rowptr, colidx, NULL, elem_size, b, brp, NULL, NULL);
+    double bytes = (double)nb * (double)(b * b * elem_size + 4) + 4.0 * (double)((m + b - 1) / b + 1);
+    if (best_b == 0 || bytes < best_bytes) { best_b = b; best_nb = nb; best_bytes = bytes; }
+  }
+  free(brp);
+  *nblocks = best_nb;
+  return best_b;
+}
+
+/* ------------------------------------------------------------------------ */
 /* BF16 storage: round-to-nearest-even of an FP64 value to the bfloat16 grid */
 /* (1 sign, 8 exponent, 7 fraction bits; IEEE 754 rounding), written from    */
 /* the definition on the FP64 bit pattern.  Returns the 16-bit pattern.      */

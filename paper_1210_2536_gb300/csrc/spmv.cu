@@ -348,8 +348,11 @@ __device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full,
 // accumulates them with one fused multiply-add each.  A row ends at entry k
 // when row[k+1] differs.  CH chunks per thread amortise the tile's fixed work
 // (carry resolution, barriers) over more entries.
+#ifndef SMAT_COO_MINB
+#define SMAT_COO_MINB 1
+#endif
 template <typename V, typename T, int NT, int CH, int MODE>
-__global__ void __launch_bounds__(NT) coo_kernel(const int32_t *__restrict__ row,
+__global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *__restrict__ row,
                                                  const int32_t *__restrict__ col,
                                                  const V *__restrict__ val, const T *__restrict__ x,
                                                  Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
