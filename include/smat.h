@@ -59,8 +59,14 @@ typedef enum {
 
 typedef enum { SMAT_F64 = 0, SMAT_F32 = 1, SMAT_BF16 = 2 } smat_dtype_t;
 
-/* Storage formats (Sec. 2.1: the four basic formats). */
-typedef enum { SMAT_FMT_CSR = 0, SMAT_FMT_ELL = 1, SMAT_FMT_DIA = 2, SMAT_FMT_COO = 3 } smat_format_t;
+/* Storage formats: the four basic formats of Sec. 2.1, then three GPU formats
+ * of the kind Sec. 8 leaves to future work (HYB: Bell & Garland's ELL + COO
+ * split; SELL: Kreutzer et al.'s SELL-C-sigma with C = 32; BCSR: b x b blocks,
+ * b in {2, 4, 8}). */
+typedef enum {
+  SMAT_FMT_CSR = 0, SMAT_FMT_ELL = 1, SMAT_FMT_DIA = 2, SMAT_FMT_COO = 3,
+  SMAT_FMT_HYB = 4, SMAT_FMT_SELL = 5, SMAT_FMT_BCSR = 6
+} smat_format_t;
 
 /* Kernel variants the selector chooses among (the paper's kernel library maps
  * each format to its best implementation, Sec. 3).  On the GPU the CSR format
@@ -80,7 +86,13 @@ typedef enum {
    * definition.  In FP64 its result is bitwise reproducible against a plain
    * sequential implementation; it costs two FP64 operations per nonzero
    * instead of one.  Only smat_spmv_variant runs it. */
-  SMAT_V_CSR_SCALAR_EXACT = 8
+  SMAT_V_CSR_SCALAR_EXACT = 8,
+  /* Further formats (not classes of the learned selector, whose 8 classes
+   * are fixed; the search times them beside its pick, see smat_tune). */
+  SMAT_V_HYB = 9,        /* ELL part + COO tail                               */
+  SMAT_V_SELL = 10,      /* SELL-32-sigma, a warp per slice                   */
+  SMAT_V_BCSR = 11,      /* b x b blocks, b lanes per block row               */
+  SMAT_NUM_ALL_VARIANTS = 12
 } smat_variant_t;
 
 /* Feature parameters (Sec. 4, Table "Feature parameters of a sparse matrix").
@@ -94,7 +106,11 @@ typedef enum {
  *   r = -slope of the least-squares line through (ln k, ln h[k]) over row
  *       degrees k >= 1 with h[k] > 0 (P(k) ~ k^-R); r_valid = 0 and r = 0 when
  *       fewer than two degrees occur.
- * Ratios whose denominator is 0 are 0. */
+ * Ratios whose denominator is 0 are 0.
+ * `admissible` bits 9-11 (HYB, SELL, BCSR) are set once the format's layout
+ * has been measured (by smat_tune, smat_convert or a product through it):
+ * each needs its stored slots (fill included) <= fill_ratio_max * NNZ and its
+ * bytes <= bytes_cap * CSR bytes; HYB also an ELL width K >= 1. */
 typedef struct {
   int64_t m, n, nnz;
   int64_t max_rd, min_rd, empty_rows;
@@ -130,6 +146,12 @@ typedef struct {
   double trial_budget_ms;  /* stop trialling further variants past this       */
   uint32_t allowed;        /* bit mask over smat_variant_t (0 = all)           */
   int32_t keep_formats;    /* 1: keep every converted format after tuning      */
+  int32_t sell_sigma;      /* SELL sort window in rows: a multiple of 32 in
+                              [32, 8192] (default 1024)                        */
+  int32_t trial_extended;  /* learned mode: also time HYB / SELL / BCSR when
+                              they move at most 1.25x the matrix bytes of the
+                              selector's pick (BCSR only for max_RD <= 64);
+                              default 1                                       */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */
@@ -163,7 +185,11 @@ smat_status_t smat_destroy(smat_handle_t h);
 /* Run-time stage of Sec. 6: extract features (Sec. 4) if not done yet, choose
  * a variant by opts->mode (NULL: learned when a model is loaded, otherwise
  * exhaustive), convert CSR to its format (Sec. 2.1) and store the plan.  Work
- * is issued on `stream`; the call returns after synchronising it. */
+ * is issued on `stream`; the call returns after synchronising it.
+ * Exhaustive mode times every admissible variant, HYB / SELL / BCSR included;
+ * learned mode times the further formats beside the selector's pick when
+ * opts->trial_extended is set (see smat_tune_opts_t); rules mode never picks
+ * them; fixed mode accepts them. */
 smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts, void *stream);
 
 /* y = alpha*A*x + beta*y through the handle's plan.  x[n] and y[m] are DEVICE
@@ -213,23 +239,37 @@ smat_status_t smat_get_feature_vector(smat_handle_t h, float out[12]);
 smat_status_t smat_get_plan(smat_handle_t h, int32_t *variant, double *tune_ms, float *confidence,
                             int32_t *trialled);
 
-/* Median trial time per variant in ms from the last smat_tune (-1 = not run). */
-smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_VARIANTS]);
+/* Median trial time per variant in ms from the last smat_tune (-1 = not run),
+ * for all SMAT_NUM_ALL_VARIANTS variants. */
+smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_ALL_VARIANTS]);
 
-/* Build format `fmt` on the device now (ELL, DIA or COO; CSR is always there).
- * UNSUPPORTED if the format is not admissible (fill or byte cap). */
+/* Build format `fmt` on the device now (CSR is always there).  UNSUPPORTED if
+ * the format is not admissible (fill or byte cap).  SELL uses the sort window
+ * of the last smat_tune (1024 before any). */
 smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream);
 
 /* Layout of a built format:
  *   ELL: dims = {K = max_RD, P = pitch}, arrays col int32[K*P], val[K*P]
  *   DIA: dims = {Ndiags, P},             arrays offsets int32[Ndiags], val[Ndiags*P]
  *   COO: dims = {NNZ, 0},                arrays row int32[NNZ] (col and val are CSR's)
+ *   HYB: dims = {K, Ncoo}: ELL part col/val[K*P] (as ELL, width K = the
+ *        largest k with 3 * #{rows with >= k entries} >= M), then the COO part
+ *        row[Ncoo], col[Ncoo], val[Ncoo] of each row's entries past its first K
+ *   SELL: dims = {Nslices, Nslots}: perm int32[32*Nslices] (row at each sorted
+ *        position, -1 past M), width int32[Nslices], col/val[Nslots]; entry j
+ *        of position 32s + l at sum_{t<s} 32*width[t] + 32j + l
+ *   BCSR: dims = {b, Nblocks}: browptr int32[ceil(M/b)+1], bcol int32[Nblocks],
+ *        val[Nblocks*b*b] row-major per block
  * P is M rounded up to a multiple of 32; padding holds column -1 / value +0. */
 smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[2]);
 
 /* Copy a built format to caller memory (host or device, detected):
  *   ELL: idx <- col, val <- val;  DIA: idx <- offsets, val <- val;
- *   COO: idx <- row (val unused).  Sizes as in smat_format_dims. */
+ *   COO: idx <- row (val unused);
+ *   HYB: idx <- ELL col, COO row, COO col; val <- ELL val, COO val;
+ *   SELL: idx <- perm, width, col; val <- val;
+ *   BCSR: idx <- browptr, bcol; val <- val.
+ * Arrays are concatenated in the order listed.  Sizes as in smat_format_dims. */
 smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *idx, void *val);
 
 /* ------------------------------------------------------------------------ */

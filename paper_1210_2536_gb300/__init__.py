@@ -23,13 +23,15 @@ LIB_PATH = os.path.join(_PKG, "libsmat.so")
 SMAT_OK, SMAT_ERR_INVALID_ARG, SMAT_ERR_INVALID_CSR, SMAT_ERR_ALLOC, SMAT_ERR_CUDA, \
     SMAT_ERR_UNSUPPORTED, SMAT_ERR_MODEL, SMAT_ERR_NOT_CONVERGED = range(8)
 SMAT_F64, SMAT_F32, SMAT_BF16 = range(3)
-SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO = range(4)
+SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO, SMAT_FMT_HYB, SMAT_FMT_SELL, SMAT_FMT_BCSR = range(7)
 (SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32, SMAT_V_CSR_MERGE, SMAT_V_ELL,
  SMAT_V_DIA, SMAT_V_COO) = range(8)
 SMAT_NUM_VARIANTS = 8
 SMAT_V_CSR_SCALAR_EXACT = 8
+SMAT_V_HYB, SMAT_V_SELL, SMAT_V_BCSR = 9, 10, 11
+SMAT_NUM_ALL_VARIANTS = 12
 VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo",
-                 "csr_scalar_exact"]
+                 "csr_scalar_exact", "hyb", "sell", "bcsr"]
 SMAT_TUNE_LEARNED, SMAT_TUNE_EXHAUSTIVE, SMAT_TUNE_RULES, SMAT_TUNE_FIXED = range(4)
 SMAT_MLP_PARAMS = 5512
 DTYPES = {"f64": SMAT_F64, "f32": SMAT_F32, "bf16": SMAT_BF16}
@@ -54,7 +56,8 @@ class smat_tune_opts_t(ctypes.Structure):
                 ("fallback_topk", ctypes.c_int32), ("tau_num", ctypes.c_int32), ("tau_den", ctypes.c_int32),
                 ("fill_ratio_max", ctypes.c_int32), ("bytes_cap", ctypes.c_double), ("trial_reps", ctypes.c_int32),
                 ("trial_warmup", ctypes.c_int32), ("trial_budget_ms", ctypes.c_double),
-                ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32)]
+                ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32), ("sell_sigma", ctypes.c_int32),
+                ("trial_extended", ctypes.c_int32)]
 
 
 class smat_cg_opts_t(ctypes.Structure):
@@ -222,7 +225,7 @@ def smat_get_plan(h):
 
 
 def smat_get_timings(h) -> np.ndarray:
-    out = np.zeros(SMAT_NUM_VARIANTS, dtype=np.float32)
+    out = np.zeros(SMAT_NUM_ALL_VARIANTS, dtype=np.float32)
     _check(lib().smat_get_timings(h, out.ctypes.data), "smat_get_timings")
     return out
 
@@ -524,8 +527,21 @@ class SpMatrix:
         return y
 
     def features(self) -> dict:
+        """Feature parameters, plus the sizes of the built HYB / SELL / BCSR
+        formats (hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b, bcsr_nb)."""
         f = smat_get_features(self.h)
-        return {n: getattr(f, n) for n, _ in smat_features_t._fields_}
+        out = {n: getattr(f, n) for n, _ in smat_features_t._fields_}
+        out.update(self.layout())
+        return out
+
+    def layout(self) -> dict:
+        out = {}
+        for fmt, keys in ((SMAT_FMT_HYB, ("hyb_K", "hyb_ncoo")), (SMAT_FMT_SELL, ("sell_ns", "sell_slots")),
+                          (SMAT_FMT_BCSR, ("bcsr_b", "bcsr_nb"))):
+            st, d0, d1 = smat_format_dims(self.h, fmt)
+            if st == SMAT_OK:
+                out[keys[0]], out[keys[1]] = d0, d1
+        return out
 
     def feature_vector(self) -> np.ndarray:
         return smat_get_feature_vector(self.h)
@@ -549,15 +565,37 @@ class SpMatrix:
         st, d0, d1 = smat_format_dims(self.h, fmt)
         _check(st, "smat_format_dims")
         vdt = {"f64": np.float64, "f32": np.float32, "bf16": np.uint16}[self.dtype]
+        P = (self.m + 31) // 32 * 32
         if fmt == SMAT_FMT_ELL:
             idx, val = np.empty(d0 * d1, np.int32), np.empty(d0 * d1, vdt)
         elif fmt == SMAT_FMT_DIA:
             idx, val = np.empty(d0, np.int32), np.empty(d0 * d1, vdt)
+        elif fmt == SMAT_FMT_HYB:
+            idx, val = np.empty(d0 * P + 2 * d1, np.int32), np.empty(d0 * P + d1, vdt)
+        elif fmt == SMAT_FMT_SELL:
+            idx, val = np.empty(33 * d0 + d1, np.int32), np.empty(d1, vdt)
+        elif fmt == SMAT_FMT_BCSR:
+            mb = (self.m + d0 - 1) // d0
+            idx, val = np.empty(mb + 1 + d1, np.int32), np.empty(d1 * d0 * d0, vdt)
         else:
             idx, val = np.empty(d0, np.int32), None
         _check(smat_export_format(self.h, fmt, idx.ctypes.data, None if val is None else val.ctypes.data),
                "smat_export_format")
         return idx, val, d0, d1
+
+    def export_parts(self, fmt) -> dict:
+        """A built HYB / SELL / BCSR format split into its named arrays."""
+        idx, val, d0, d1 = self.export(fmt)
+        if fmt == SMAT_FMT_HYB:
+            ne = d0 * ((self.m + 31) // 32 * 32)
+            return {"K": d0, "ell_col": idx[:ne], "ell_val": val[:ne], "coo_row": idx[ne:ne + d1],
+                    "coo_col": idx[ne + d1:], "coo_val": val[ne:]}
+        if fmt == SMAT_FMT_SELL:
+            return {"perm": idx[:32 * d0], "width": idx[32 * d0:33 * d0], "col": idx[33 * d0:], "val": val}
+        if fmt == SMAT_FMT_BCSR:
+            mb = (self.m + d0 - 1) // d0
+            return {"b": d0, "browptr": idx[:mb + 1], "bcol": idx[mb + 1:], "val": val}
+        raise ValueError(fmt)
 
 
 def _ptr(a):

@@ -78,12 +78,43 @@ int variant_format(int v) {
   if (v == SMAT_V_ELL) return SMAT_FMT_ELL;
   if (v == SMAT_V_DIA) return SMAT_FMT_DIA;
   if (v == SMAT_V_COO) return SMAT_FMT_COO;
+  if (v == SMAT_V_HYB) return SMAT_FMT_HYB;
+  if (v == SMAT_V_SELL) return SMAT_FMT_SELL;
+  if (v == SMAT_V_BCSR) return SMAT_FMT_BCSR;
   return SMAT_FMT_CSR;
 }
+
+constexpr uint32_t ALL_VARIANTS = ((1u << SMAT_NUM_ALL_VARIANTS) - 1) & ~(1u << SMAT_V_CSR_SCALAR_EXACT);
 
 double csr_bytes(const smat_s *h) { return (double)(h->esz + 4) * h->nnz + 4.0 * (h->m + 1); }
 double ell_bytes(const smat_s *h) { return (double)(h->esz + 4) * h->f.max_rd * h->P; }
 double dia_bytes(const smat_s *h) { return (double)h->esz * h->f.ndiags * h->P + 4.0 * h->f.ndiags; }
+
+// Matrix bytes one product through `v` reads (x and y are common to all).
+double variant_bytes(const smat_s *h, int v) {
+  switch (v) {
+    case SMAT_V_ELL: return ell_bytes(h);
+    case SMAT_V_DIA: return dia_bytes(h);
+    case SMAT_V_COO: return (double)(h->esz + 8) * h->nnz;
+    case SMAT_V_HYB: case SMAT_V_SELL: case SMAT_V_BCSR: return h->ext_bytes[v - SMAT_V_HYB];
+    default: return csr_bytes(h);
+  }
+}
+
+// HYB / SELL / BCSR: admissible once their layout is measured, under the
+// same two limits as ELL and DIA (stored slots <= fill_ratio_max x NNZ,
+// bytes <= bytes_cap x CSR bytes); HYB also needs an ELL part.
+uint32_t ext_bits(const smat_s *h) {
+  uint32_t mask = 0;
+  const double cap = h->bytes_cap * std::max(csr_bytes(h), 1.0);
+  const double lim = (double)h->fill_ratio_max * (double)h->nnz;
+  for (int e = 0; e < 3; ++e) {
+    if (!h->ext_known[e] || h->nnz == 0 || h->m == 0) continue;
+    if (e == 0 && h->hyb_K < 1) continue;
+    if (h->ext_slots[e] <= lim && h->ext_bytes[e] <= cap) mask |= 1u << (SMAT_V_HYB + e);
+  }
+  return mask;
+}
 
 // ---------------------------------------------------------------------------
 // Feature extraction (Sec. 4): integer passes on the GPU, then the doubles
@@ -124,7 +155,7 @@ void update_admissible(smat_s *h) {
   if (f.m > 0 && f.ndiags > 0 && f.ndiags <= 8192 && h->dia_offsets_complete && (__int128)f.ndiags * f.m <= lim &&
       dia_bytes(h) <= cap)
     mask |= 1u << SMAT_V_DIA;
-  f.admissible = mask;
+  f.admissible = mask | ext_bits(h);
 }
 
 smat_status_t compute_features(smat_s *h, cudaStream_t s) {
@@ -228,7 +259,111 @@ void free_format(smat_s *h, int fmt) {
   } else if (fmt == SMAT_FMT_COO) {
     dev_free(h->coo_row); dev_free(h->coo_empty);
     h->coo_row = nullptr; h->coo_empty = nullptr; h->coo_nempty = 0;
+  } else if (fmt == SMAT_FMT_HYB) {
+    dev_free(h->hyb_ecol); dev_free(h->hyb_eval); dev_free(h->hyb_crow); dev_free(h->hyb_ccol); dev_free(h->hyb_cval);
+    h->hyb_ecol = h->hyb_crow = h->hyb_ccol = nullptr; h->hyb_eval = h->hyb_cval = nullptr; h->hyb_built = false;
+  } else if (fmt == SMAT_FMT_SELL) {  // the layout (perm, width, slice pointers) stays
+    dev_free(h->sell_col); dev_free(h->sell_val);
+    h->sell_col = nullptr; h->sell_val = nullptr;
+  } else if (fmt == SMAT_FMT_BCSR) {  // the 64-bit block row starts stay
+    dev_free(h->bcsr_rowptr); dev_free(h->bcsr_col); dev_free(h->bcsr_val);
+    h->bcsr_rowptr = h->bcsr_col = nullptr; h->bcsr_val = nullptr;
   }
+}
+
+void free_sell_layout(smat_s *h) {
+  free_format(h, SMAT_FMT_SELL);
+  dev_free(h->sell_perm); dev_free(h->sell_width); dev_free(h->sell_ptr);
+  h->sell_perm = h->sell_width = nullptr; h->sell_ptr = nullptr; h->sell_ns = h->sell_slots = 0;
+  h->ext_known[SMAT_V_SELL - SMAT_V_HYB] = false;
+}
+
+void free_ext_layouts(smat_s *h) {
+  free_format(h, SMAT_FMT_HYB);
+  free_sell_layout(h);
+  free_format(h, SMAT_FMT_BCSR);
+  dev_free(h->bcsr_brp64);
+  h->bcsr_brp64 = nullptr;
+}
+
+// Layout of a further format -- sizes without the values: HYB's width K and
+// tail length from the row-degree histogram; SELL's sorted order, slice widths
+// and slice pointers; BCSR's block size (the b in {2, 4, 8} with the fewest
+// bytes; ties to the smaller) and block row starts.  Sets the admissibility bit.
+smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
+  const int e = v - SMAT_V_HYB;
+  if (!h->have_features) TRYS(compute_features(h, s));
+  if (v == SMAT_V_SELL && h->ext_known[e] && sigma != h->sell_sigma) free_sell_layout(h);
+  if (h->ext_known[e]) return SMAT_OK;
+  if (v == SMAT_V_SELL) h->sell_sigma = sigma;
+  const int esz = h->esz;
+  if (h->m > 0 && h->nnz > 0) {
+    if (v == SMAT_V_HYB) {
+      int64_t rows_ge = 0, K = 0;
+      for (int64_t k = (int64_t)h->hist.size() - 1; k >= 1; --k) {
+        rows_ge += h->hist[(size_t)k];
+        if (3 * rows_ge >= h->m) { K = k; break; }
+      }
+      int64_t ncoo = 0;
+      for (int64_t k = K + 1; k < (int64_t)h->hist.size(); ++k) ncoo += h->hist[(size_t)k] * (k - K);
+      h->hyb_K = K;
+      h->hyb_ncoo = ncoo;
+      h->ext_slots[e] = (double)K * h->m + (double)ncoo;
+      h->ext_bytes[e] = (double)(esz + 4) * K * h->P + (double)(esz + 8) * ncoo;
+    } else if (v == SMAT_V_SELL) {
+      free_sell_layout(h);  // drop what an earlier, failed attempt left
+      const int64_t mp = (h->m + 31) / 32 * 32, ns = mp / 32;
+      void *perm = nullptr, *width = nullptr, *ptr = nullptr;
+      DevBuf cnt;
+      TRY(dev_alloc(&perm, (size_t)mp * 4));
+      h->sell_perm = (int32_t *)perm;
+      TRY(dev_alloc(&width, (size_t)ns * 4));
+      h->sell_width = (int32_t *)width;
+      TRY(dev_alloc(&ptr, (size_t)(ns + 1) * 8));
+      h->sell_ptr = (long long *)ptr;
+      TRY(cnt.alloc((size_t)ns * 8));
+      TRY(launch_sell_layout(h, sigma, h->sell_perm, h->sell_width, cnt.as<long long>(), s));
+      TRY(exclusive_scan(cnt.as<long long>(), ns, h->sell_ptr, s));
+      long long slots = 0;
+      TRY(cudaMemcpy(&slots, h->sell_ptr + ns, 8, cudaMemcpyDeviceToHost));
+      h->sell_ns = ns;
+      h->sell_slots = slots;
+      h->ext_slots[e] = (double)slots;
+      h->ext_bytes[e] = (double)(esz + 4) * slots + 4.0 * mp + 12.0 * ns + 8.0;
+    } else {
+      free_format(h, SMAT_FMT_BCSR);
+      dev_free(h->bcsr_brp64);
+      h->bcsr_brp64 = nullptr;
+      h->bcsr_b = 0;
+      double best_bytes = 0.0;
+      for (int b = 2; b <= 8; b *= 2) {
+        const int64_t mb = (h->m + b - 1) / b;
+        DevBuf cnt;
+        void *brp = nullptr;
+        TRY(cnt.alloc((size_t)mb * 8));
+        TRY(dev_alloc(&brp, (size_t)(mb + 1) * 8));
+        cudaError_t err = launch_bcsr_count(h, b, cnt.as<long long>(), s);
+        if (err == cudaSuccess) err = exclusive_scan(cnt.as<long long>(), mb, (long long *)brp, s);
+        long long nb = 0;
+        if (err == cudaSuccess) err = cudaMemcpy(&nb, (long long *)brp + mb, 8, cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) { dev_free(brp); return st_of(err); }
+        const double bytes = (double)nb * (double)(b * b * esz + 4) + 4.0 * (double)(mb + 1);
+        if (h->bcsr_b == 0 || bytes < best_bytes) {
+          dev_free(h->bcsr_brp64);
+          h->bcsr_brp64 = (long long *)brp;
+          h->bcsr_b = b; h->bcsr_mb = mb; h->bcsr_nb = nb;
+          best_bytes = bytes;
+        } else {
+          dev_free(brp);
+        }
+      }
+      h->ext_slots[e] = (double)h->bcsr_nb * h->bcsr_b * h->bcsr_b;
+      h->ext_bytes[e] = best_bytes;
+    }
+  }
+  h->ext_known[e] = true;
+  update_admissible(h);
+  return SMAT_OK;
 }
 
 // Kernel search for ELL / DIA (the paper's per-format implementation choice,
@@ -327,6 +462,47 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     }
     return SMAT_OK;
   }
+  if (fmt == SMAT_FMT_HYB || fmt == SMAT_FMT_SELL || fmt == SMAT_FMT_BCSR) {
+    const int v = fmt == SMAT_FMT_HYB ? SMAT_V_HYB : (fmt == SMAT_FMT_SELL ? SMAT_V_SELL : SMAT_V_BCSR);
+    TRYS(ext_layout(h, v, h->sell_sigma, s));
+    if (!(h->f.admissible & (1u << v))) return SMAT_ERR_UNSUPPORTED;
+    struct Undo {  // a failed build leaves no half-built format behind
+      smat_s *h; int fmt; bool armed = true;
+      ~Undo() { if (armed) free_format(h, fmt); }
+    } undo{h, fmt};
+    void *p = nullptr;
+    if (fmt == SMAT_FMT_HYB) {
+      if (h->hyb_built) { undo.armed = false; return SMAT_OK; }
+      const int64_t K = h->hyb_K, nc = h->hyb_ncoo;
+      TRY(dev_alloc(&p, (size_t)(K * h->P) * 4)); h->hyb_ecol = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)(K * h->P) * h->esz)); h->hyb_eval = p;
+      TRY(dev_alloc(&p, (size_t)nc * 4)); h->hyb_crow = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)nc * 4)); h->hyb_ccol = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)nc * h->esz)); h->hyb_cval = p;
+      DevBuf cnt, off;
+      TRY(cnt.alloc((size_t)h->m * 8));
+      TRY(off.alloc((size_t)(h->m + 1) * 8));
+      TRY(launch_hyb_tail_counts(h, K, cnt.as<long long>(), s));
+      TRY(exclusive_scan(cnt.as<long long>(), h->m, off.as<long long>(), s));
+      TRY(launch_to_hyb(h, K, off.as<long long>(), h->hyb_ecol, h->hyb_eval, h->hyb_crow, h->hyb_ccol, h->hyb_cval, s));
+      TRY(cudaStreamSynchronize(s));
+      h->hyb_built = true;
+    } else if (fmt == SMAT_FMT_SELL) {
+      if (h->sell_val) { undo.armed = false; return SMAT_OK; }
+      TRY(dev_alloc(&p, (size_t)h->sell_slots * 4)); h->sell_col = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)h->sell_slots * h->esz)); h->sell_val = p;
+      TRY(launch_to_sell(h, s));
+    } else {
+      if (h->bcsr_val) { undo.armed = false; return SMAT_OK; }
+      const int64_t bb = (int64_t)h->bcsr_b * h->bcsr_b;
+      TRY(dev_alloc(&p, (size_t)(h->bcsr_mb + 1) * 4)); h->bcsr_rowptr = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)h->bcsr_nb * 4)); h->bcsr_col = (int32_t *)p;
+      TRY(dev_alloc(&p, (size_t)(h->bcsr_nb * bb) * h->esz)); h->bcsr_val = p;
+      TRY(launch_to_bcsr(h, h->bcsr_brp64, s));
+    }
+    undo.armed = false;
+    return SMAT_OK;
+  }
   return SMAT_ERR_INVALID_ARG;
 }
 
@@ -348,12 +524,15 @@ bool variant_ready(const smat_s *h, int v) {
   if (fmt == SMAT_FMT_DIA && !h->dia_val) return false;
   if (fmt == SMAT_FMT_COO && !h->coo_row && !(h->nnz == 0)) return false;
   if (fmt == SMAT_FMT_COO && h->f.empty_rows > 0 && !h->coo_empty) return false;
+  if (fmt == SMAT_FMT_HYB && !h->hyb_built) return false;
+  if (fmt == SMAT_FMT_SELL && !h->sell_val) return false;
+  if (fmt == SMAT_FMT_BCSR && !h->bcsr_val) return false;
   if (carry_bytes_needed(h, v) > h->carry_bytes) return false;
   return true;
 }
 
 smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
-  if (v < 0 || v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
+  if (v < 0 || v >= SMAT_NUM_ALL_VARIANTS) return SMAT_ERR_INVALID_ARG;
   int fmt = variant_format(v);
   if (fmt != SMAT_FMT_CSR && !h->have_features) TRYS(compute_features(h, s));
   TRYS(build_format(h, fmt, s));
@@ -415,7 +594,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     }
     if (!o.keep_formats) {
       // drop a trialled format right away unless it is the best so far
-      for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_COO; ++fmt)
+      for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_BCSR; ++fmt)
         if (fmt != variant_format(*best)) free_format(h, fmt);
     }
   }
@@ -492,6 +671,8 @@ void smat_tune_opts_default(smat_tune_opts_t *o) {
   o->trial_budget_ms = 2000.0;
   o->allowed = 0;
   o->keep_formats = 0;
+  o->sell_sigma = 1024;
+  o->trial_extended = 1;
 }
 
 const char *smat_status_string(smat_status_t s) {
@@ -560,6 +741,7 @@ smat_status_t smat_destroy(smat_handle_t h) {
   if (!h) return SMAT_OK;
   dev_free(h->rowptr); dev_free(h->colidx); dev_free(h->val);
   free_format(h, SMAT_FMT_ELL); free_format(h, SMAT_FMT_DIA); free_format(h, SMAT_FMT_COO);
+  free_ext_layouts(h);
   dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y); dev_free(h->merge_coords);
   delete h;
   return SMAT_OK;
@@ -572,6 +754,8 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   if (opts_in) o = *opts_in; else { smat_tune_opts_default(&o); if (!model().loaded) o.mode = SMAT_TUNE_EXHAUSTIVE; }
   if (o.mode < SMAT_TUNE_LEARNED || o.mode > SMAT_TUNE_FIXED) return SMAT_ERR_INVALID_ARG;
   if (o.tau_den <= 0 || o.tau_num < 0 || o.fill_ratio_max <= 0) return SMAT_ERR_INVALID_ARG;
+  if (o.sell_sigma == 0) o.sell_sigma = 1024;
+  if (o.sell_sigma < 32 || o.sell_sigma > 8192 || o.sell_sigma % 32 != 0) return SMAT_ERR_INVALID_ARG;
   const double t0 = now_ms();
   if (!h->have_features || o.tau_num != h->tau_num || o.tau_den != h->tau_den ||
       o.fill_ratio_max != h->fill_ratio_max) {
@@ -583,7 +767,19 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
     update_admissible(h);
   }
   for (auto &t : h->timings) t = -1.0f;
-  const uint32_t allowed = o.allowed ? o.allowed : 0xFFu;
+  const uint32_t allowed = (o.allowed ? o.allowed : ALL_VARIANTS) & ALL_VARIANTS;
+  // layouts of the further formats the chosen mode may use
+  for (int e = SMAT_V_HYB; e <= SMAT_V_BCSR; ++e) {
+    if (!((allowed >> e) & 1u)) continue;
+    const bool want = o.mode == SMAT_TUNE_EXHAUSTIVE || (o.mode == SMAT_TUNE_FIXED && o.fixed_variant == e) ||
+                      (o.mode == SMAT_TUNE_LEARNED && o.trial_extended &&
+                       (e != SMAT_V_BCSR || h->f.max_rd <= 64));
+    if (want) {
+      smat_status_t es = ext_layout(h, e, o.sell_sigma, s);
+      if (es == SMAT_ERR_ALLOC) continue;  // an unaffordable layout is not a candidate
+      TRYS(es);
+    }
+  }
   const uint32_t ok = h->f.admissible & allowed;
   if (!ok) return SMAT_ERR_UNSUPPORTED;
   int v = SMAT_V_CSR_SCALAR;
@@ -593,9 +789,14 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   for (int c : {SMAT_V_DIA, SMAT_V_ELL, SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32,
                 SMAT_V_CSR_MERGE, SMAT_V_COO})
     if ((ok >> c) & 1u) cands.push_back(c);
+  std::vector<int> ext;
+  for (int c = SMAT_V_HYB; c <= SMAT_V_BCSR; ++c)
+    if ((ok >> c) & 1u) ext.push_back(c);
   switch (o.mode) {
     case SMAT_TUNE_FIXED:
-      if (o.fixed_variant < 0 || o.fixed_variant >= SMAT_NUM_VARIANTS) return SMAT_ERR_INVALID_ARG;
+      if (o.fixed_variant < 0 || o.fixed_variant >= SMAT_NUM_ALL_VARIANTS ||
+          o.fixed_variant == SMAT_V_CSR_SCALAR_EXACT)
+        return SMAT_ERR_INVALID_ARG;
       if (!((ok >> o.fixed_variant) & 1u)) return SMAT_ERR_UNSUPPORTED;
       v = o.fixed_variant;
       break;
@@ -603,6 +804,8 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
       v = rules_select(h->f, ok);
       break;
     case SMAT_TUNE_EXHAUSTIVE:
+      cands.insert(cands.end(), ext.begin(), ext.end());
+      if (cands.empty()) return SMAT_ERR_UNSUPPORTED;
       TRYS(trial(h, cands, o, s, &v));
       h->trialled = 1;
       break;
@@ -613,12 +816,27 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
       int arg = -1;
       for (int c = 0; c < SMAT_NUM_VARIANTS; ++c)
         if (((ok >> c) & 1u) && (arg < 0 || p[c] > p[arg])) arg = c;
+      if (arg < 0) {  // only further formats are allowed: time them
+        TRYS(trial(h, ext, o, s, &v));
+        h->trialled = 1;
+        break;
+      }
       v = arg;
       h->confidence = p[arg];
+      std::vector<int> top{arg};
       if (p[arg] < o.conf_threshold) {
-        std::vector<int> top(cands);
+        top = cands;
         std::sort(top.begin(), top.end(), [&](int a, int b) { return p[a] > p[b]; });
         if (o.fallback_topk > 0 && (int)top.size() > o.fallback_topk) top.resize((size_t)o.fallback_topk);
+      }
+      // the selector's classes do not include the further formats: time those
+      // that move at most 1.25x the matrix bytes of its pick beside it (their
+      // access patterns can beat a format that moves a little less)
+      bool more = false;
+      if (o.trial_extended)
+        for (int c : ext)
+          if (variant_bytes(h, c) <= 1.25 * variant_bytes(h, arg)) { top.push_back(c); more = true; }
+      if (top.size() > 1 || more) {
         TRYS(trial(h, top, o, s, &v));
         h->trialled = 1;
       }
@@ -626,7 +844,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   }
   TRYS(prepare_variant(h, v, s));
   if (!o.keep_formats)
-    for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_COO; ++fmt)
+    for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_BCSR; ++fmt)
       if (fmt != variant_format(v)) free_format(h, fmt);
   TRY(cudaStreamSynchronize(s));
   h->variant = v;
@@ -647,7 +865,7 @@ smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *a
                                 const void *beta, void *y, void *stream) {
   TRYS(check_handle(h));
   if (!alpha || !beta || (h->m > 0 && !y) || (h->n > 0 && !x)) return SMAT_ERR_INVALID_ARG;
-  if ((int)v < 0 || (int)v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
+  if ((int)v < 0 || (int)v >= SMAT_NUM_ALL_VARIANTS) return SMAT_ERR_INVALID_ARG;
   if (!variant_ready(h, v)) {
     TRYS(prepare_variant(h, v, (cudaStream_t)stream));
     if (!variant_ready(h, v)) return SMAT_ERR_UNSUPPORTED;
@@ -695,7 +913,7 @@ smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_h
 
 smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *launches) {
   TRYS(check_handle(h));
-  if (!launches || (int)v < 0 || (int)v > SMAT_V_CSR_SCALAR_EXACT) return SMAT_ERR_INVALID_ARG;
+  if (!launches || (int)v < 0 || (int)v >= SMAT_NUM_ALL_VARIANTS) return SMAT_ERR_INVALID_ARG;
   *launches = variant_ready(h, v) ? spmv_launch_count(h, v) : 0;
   return SMAT_OK;
 }
@@ -726,16 +944,16 @@ smat_status_t smat_get_plan(smat_handle_t h, int32_t *variant, double *tune_ms, 
   return SMAT_OK;
 }
 
-smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_VARIANTS]) {
+smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_ALL_VARIANTS]) {
   TRYS(check_handle(h));
   if (!ms) return SMAT_ERR_INVALID_ARG;
-  for (int v = 0; v < SMAT_NUM_VARIANTS; ++v) ms[v] = h->timings[v];
+  for (int v = 0; v < SMAT_NUM_ALL_VARIANTS; ++v) ms[v] = h->timings[v];
   return SMAT_OK;
 }
 
 smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream) {
   TRYS(check_handle(h));
-  if (fmt < SMAT_FMT_CSR || fmt > SMAT_FMT_COO) return SMAT_ERR_INVALID_ARG;
+  if (fmt < SMAT_FMT_CSR || fmt > SMAT_FMT_BCSR) return SMAT_ERR_INVALID_ARG;
   TRYS(build_format(h, fmt, (cudaStream_t)stream));
   TRY(cudaStreamSynchronize((cudaStream_t)stream));
   return SMAT_OK;
@@ -749,6 +967,9 @@ smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[
     case SMAT_FMT_DIA: if (!h->dia_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->dia_nd; dims[1] = h->P; break;
     case SMAT_FMT_COO: if (!h->coo_row && h->nnz > 0) return SMAT_ERR_UNSUPPORTED; dims[0] = h->nnz; dims[1] = 0; break;
     case SMAT_FMT_CSR: dims[0] = h->m; dims[1] = h->nnz; break;
+    case SMAT_FMT_HYB: if (!h->hyb_built) return SMAT_ERR_UNSUPPORTED; dims[0] = h->hyb_K; dims[1] = h->hyb_ncoo; break;
+    case SMAT_FMT_SELL: if (!h->sell_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->sell_ns; dims[1] = h->sell_slots; break;
+    case SMAT_FMT_BCSR: if (!h->bcsr_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->bcsr_b; dims[1] = h->bcsr_nb; break;
     default: return SMAT_ERR_INVALID_ARG;
   }
   return SMAT_OK;
@@ -773,6 +994,30 @@ smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *id
       if (!idx) return SMAT_ERR_INVALID_ARG;
       if (h->nnz > 0) TRY(cudaMemcpy(idx, h->coo_row, (size_t)h->nnz * 4, cudaMemcpyDefault));
       break;
+    case SMAT_FMT_HYB: {
+      if (!idx || !val) return SMAT_ERR_INVALID_ARG;
+      const size_t ne = (size_t)(h->hyb_K * h->P), nc = (size_t)h->hyb_ncoo;
+      if (ne) TRY(cudaMemcpy(idx, h->hyb_ecol, ne * 4, cudaMemcpyDefault));
+      if (nc) TRY(cudaMemcpy(idx + ne, h->hyb_crow, nc * 4, cudaMemcpyDefault));
+      if (nc) TRY(cudaMemcpy(idx + ne + nc, h->hyb_ccol, nc * 4, cudaMemcpyDefault));
+      if (ne) TRY(cudaMemcpy(val, h->hyb_eval, ne * h->esz, cudaMemcpyDefault));
+      if (nc) TRY(cudaMemcpy((char *)val + ne * h->esz, h->hyb_cval, nc * h->esz, cudaMemcpyDefault));
+    } break;
+    case SMAT_FMT_SELL: {
+      if (!idx || !val) return SMAT_ERR_INVALID_ARG;
+      const size_t ns = (size_t)h->sell_ns, sl = (size_t)h->sell_slots;
+      if (ns) TRY(cudaMemcpy(idx, h->sell_perm, ns * 32 * 4, cudaMemcpyDefault));
+      if (ns) TRY(cudaMemcpy(idx + ns * 32, h->sell_width, ns * 4, cudaMemcpyDefault));
+      if (sl) TRY(cudaMemcpy(idx + ns * 33, h->sell_col, sl * 4, cudaMemcpyDefault));
+      if (sl) TRY(cudaMemcpy(val, h->sell_val, sl * h->esz, cudaMemcpyDefault));
+    } break;
+    case SMAT_FMT_BCSR: {
+      if (!idx || !val) return SMAT_ERR_INVALID_ARG;
+      const size_t mb = (size_t)h->bcsr_mb, nb = (size_t)h->bcsr_nb, bb = (size_t)h->bcsr_b * h->bcsr_b;
+      TRY(cudaMemcpy(idx, h->bcsr_rowptr, (mb + 1) * 4, cudaMemcpyDefault));
+      if (nb) TRY(cudaMemcpy(idx + mb + 1, h->bcsr_col, nb * 4, cudaMemcpyDefault));
+      if (nb) TRY(cudaMemcpy(val, h->bcsr_val, nb * bb * h->esz, cudaMemcpyDefault));
+    } break;
     default:
       return SMAT_ERR_INVALID_ARG;
   }

@@ -81,6 +81,28 @@ struct smat_s {
   int32_t *coo_empty = nullptr;  // list of empty rows (y = beta*y there)
   int64_t coo_nempty = 0;
 
+  // HYB: ELL part (K x P) + COO part
+  int64_t hyb_K = 0, hyb_ncoo = 0;
+  int32_t *hyb_ecol = nullptr, *hyb_crow = nullptr, *hyb_ccol = nullptr;
+  void *hyb_eval = nullptr, *hyb_cval = nullptr;
+  bool hyb_built = false;
+  // SELL-32-sigma: layout (perm, width, slice pointers) then col / val
+  int32_t sell_sigma = 1024;
+  int64_t sell_ns = 0, sell_slots = 0;
+  int32_t *sell_perm = nullptr, *sell_width = nullptr, *sell_col = nullptr;
+  long long *sell_ptr = nullptr;
+  void *sell_val = nullptr;
+  // BCSR: block size, block rows, blocks; 64-bit block row starts until filled
+  int32_t bcsr_b = 0;
+  int64_t bcsr_mb = 0, bcsr_nb = 0;
+  long long *bcsr_brp64 = nullptr;
+  int32_t *bcsr_rowptr = nullptr, *bcsr_col = nullptr;
+  void *bcsr_val = nullptr;
+  // measured layouts of HYB / SELL / BCSR (index v - SMAT_V_HYB): stored
+  // slots (fill included) and bytes, for their admissibility bits
+  bool ext_known[3] = {false, false, false};
+  double ext_slots[3] = {0, 0, 0}, ext_bytes[3] = {0, 0, 0};
+
   // merge-path tile coordinates (int2 per tile boundary), computed once
   void *merge_coords = nullptr;
   // scratch for merge-path and COO carries
@@ -95,7 +117,7 @@ struct smat_s {
   double tune_ms = 0.0;
   float confidence = -1.0f;
   int32_t trialled = 0;
-  float timings[SMAT_NUM_VARIANTS];
+  float timings[SMAT_NUM_ALL_VARIANTS];
 };
 
 namespace smat {
@@ -114,6 +136,21 @@ cudaError_t launch_empty_rows(const smat_s *h, int32_t *list, int *d_count, cuda
 cudaError_t launch_to_ell(const smat_s *h, int64_t K, int32_t *col, void *val, cudaStream_t s);
 cudaError_t launch_to_dia(const smat_s *h, const int32_t *d_off, int64_t nd, void *val,
                           cudaStream_t s);
+
+// Further formats (formats_ext.cu).  exclusive_scan writes out[0..n] and
+// synchronises `s`.
+cudaError_t exclusive_scan(const long long *in, long long n, long long *out, cudaStream_t s);
+cudaError_t launch_hyb_tail_counts(const smat_s *h, int64_t K, long long *cnt, cudaStream_t s);
+cudaError_t launch_to_hyb(const smat_s *h, int64_t K, const long long *off, int32_t *ecol, void *eval,
+                          int32_t *crow, int32_t *ccol, void *cval, cudaStream_t s);
+cudaError_t launch_sell_layout(const smat_s *h, int sigma, int32_t *perm, int32_t *width, long long *cnt,
+                               cudaStream_t s);
+cudaError_t launch_to_sell(const smat_s *h, cudaStream_t s);
+cudaError_t launch_bcsr_count(const smat_s *h, int b, long long *cnt, cudaStream_t s);
+cudaError_t launch_to_bcsr(const smat_s *h, const long long *brp, cudaStream_t s);
+// SELL / BCSR products (HYB runs through the ELL and COO kernels of spmv.cu).
+cudaError_t launch_spmv_ext(const smat_s *h, int variant, const void *alpha, const void *x,
+                            const void *beta, void *y, cudaStream_t s);
 
 // Merge-path tiles of an m x ? matrix with nnz entries, and the kernel that
 // writes their (ntiles + 1) boundary coordinates (int2) to `coords`.

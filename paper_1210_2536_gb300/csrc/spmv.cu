@@ -485,13 +485,20 @@ constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 
 // ELL / DIA launches with a batch width U chosen at run time from 1..16/R.
+// The ELL arrays are passed in: the handle's ELL format, or HYB's ELL part.
+struct EllPart {
+  const int32_t *col;
+  const void *val;
+  long long K;
+};
+
 template <typename V, int MODE, int U>
-void launch_ell_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
-                  typename Compute<V>::T *y, cudaStream_t s) {
+void launch_ell_u(const smat_s *h, const EllPart &e, const typename Compute<V>::T *x,
+                  const Epi<typename Compute<V>::T, MODE> &ep, typename Compute<V>::T *y, cudaStream_t s) {
   constexpr int R = 16 / (int)sizeof(V);
   const long long m = h->m;
   ell_kernel<V, R, MODE, U><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
-      h->ell_col, (const V *)h->ell_val, h->P, h->ell_K, x, ep, y, m);
+      e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
 }
 
 template <typename V, int MODE, int U>
@@ -505,15 +512,16 @@ void launch_dia_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<ty
 
 template <typename V, int MODE, bool DIA>
 void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
-                    typename Compute<V>::T *y, cudaStream_t s, int u_req) {
+                    typename Compute<V>::T *y, cudaStream_t s, int u_req, const EllPart *part = nullptr) {
   constexpr int UMAX = 16 / (16 / (int)sizeof(V));  // 16 / R
-  const int u_tuned = DIA ? h->dia_u : h->ell_u;
-  const int u = u_req > 0 ? u_req : (u_tuned > 0 ? u_tuned : batch_width(DIA ? h->dia_nd : h->ell_K, UMAX));
+  const EllPart e = part ? *part : EllPart{h->ell_col, h->ell_val, h->ell_K};
+  const int u_tuned = part ? 0 : (DIA ? h->dia_u : h->ell_u);
+  const int u = u_req > 0 ? u_req : (u_tuned > 0 ? u_tuned : batch_width(DIA ? h->dia_nd : e.K, UMAX));
 #define SMAT_UCASE(k)                                                      \
   case k:                                                                  \
     if constexpr (k <= UMAX) {                                             \
       if (DIA) launch_dia_u<V, MODE, k>(h, x, ep, y, s);                   \
-      else launch_ell_u<V, MODE, k>(h, x, ep, y, s);                       \
+      else launch_ell_u<V, MODE, k>(h, e, x, ep, y, s);                    \
     }                                                                      \
     break;
   switch (u) {
@@ -521,7 +529,7 @@ void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<
     default:
       if constexpr (UMAX >= 8) {
         if (DIA) launch_dia_u<V, MODE, 8>(h, x, ep, y, s);
-        else launch_ell_u<V, MODE, 8>(h, x, ep, y, s);
+        else launch_ell_u<V, MODE, 8>(h, e, x, ep, y, s);
       }
       break;
   }
@@ -590,6 +598,24 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       if (tiles > 1)
         carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
     } break;
+    case SMAT_V_HYB: {
+      // the ELL part writes every row (y = alpha*part + beta*y), then the COO
+      // tail adds alpha*(its sums): y = alpha*acc + 1*y
+      const EllPart part{h->hyb_ecol, h->hyb_eval, h->hyb_K};
+      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, 0, &part);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess || h->hyb_ncoo == 0) return e;
+      const Epi<T, EPI_AXPBY> add{alpha, (T)1};
+      long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+      int32_t *crow = (int32_t *)h->carry;
+      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+      coo_kernel<V, T, COO_NT, COO_CH, EPI_AXPBY><<<(unsigned)tiles, COO_NT, 0, s>>>(
+          h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y, h->hyb_ncoo, crow, cval);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (tiles > 1)
+        carry_fixup_kernel<T, EPI_AXPBY><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, add, y);
+    } break;
     default:
       return cudaErrorInvalidValue;
   }
@@ -624,6 +650,7 @@ size_t carry_bytes_needed(const smat_s *h, int variant) {
   long long tiles = 0;
   if (variant == SMAT_V_CSR_MERGE) tiles = (h->m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
   else if (variant == SMAT_V_COO) tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  else if (variant == SMAT_V_HYB) tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
   else return 0;
   size_t tsz = h->dtype == SMAT_F64 ? 8 : 4;
   return (size_t)((tiles * 4 + 15) / 16) * 16 + (size_t)tiles * tsz;
@@ -639,15 +666,24 @@ int spmv_launch_count(const smat_s *h, int variant) {
     long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
     return (h->coo_nempty > 0) + (h->nnz > 0) + (tiles > 1);
   }
+  if (variant == SMAT_V_HYB) {
+    long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    return 1 + (h->hyb_ncoo > 0) + (tiles > 1);
+  }
+  if (variant == SMAT_V_SELL) return h->sell_ns > 0;
+  if (variant == SMAT_V_BCSR) return h->bcsr_mb > 0;
   return 1;
 }
 
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
                         void *y, cudaStream_t s) {
-  // ELL and DIA read x and write y with 16-byte vector accesses; vectors that
-  // are not 16-byte aligned take the CSR-scalar kernel instead.
-  if ((variant == SMAT_V_ELL || variant == SMAT_V_DIA) && (((uintptr_t)x | (uintptr_t)y) & 15u) != 0)
+  // ELL, DIA and HYB read x and write y, and BCSR reads x, with vector
+  // accesses of up to 16 bytes; vectors that are not 16-byte aligned take the
+  // CSR-scalar kernel instead.
+  if ((variant == SMAT_V_ELL || variant == SMAT_V_DIA || variant == SMAT_V_HYB || variant == SMAT_V_BCSR) &&
+      (((uintptr_t)x | (uintptr_t)y) & 15u) != 0)
     variant = SMAT_V_CSR_SCALAR;
+  if (variant == SMAT_V_SELL || variant == SMAT_V_BCSR) return launch_spmv_ext(h, variant, alpha, x, beta, y, s);
   switch (h->dtype) {
     case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, 0);
     case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, 0);

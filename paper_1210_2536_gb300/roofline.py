@@ -9,7 +9,14 @@ y written once (plus read when beta != 0):
   ELL                            (s_v + 4) K M            (pad slots counted)
   DIA                            s_v Ndiags M + 4 Ndiags  (fill counted)
   COO                            (s_v + 8) NNZ
+  HYB                            (s_v + 4) K M + (s_v + 8) Ncoo
+  SELL                           (s_v + 4) slots + 4 Mp + 12 Nslices + 8
+                                 (perm 4 B / position, width and pointer per slice)
+  BCSR                           (s_v b^2 + 4) Nblocks + 4 (ceil(M/b) + 1)
   every variant                  + s_x N + s_y M (1 + [beta != 0])
+
+The HYB / SELL / BCSR sizes come from the built format (SpMatrix.features()
+adds hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b and bcsr_nb once built).
 
 GFLOP/s counts 2 NNZ flops per product (true nonzeros only).
 
@@ -20,8 +27,9 @@ by the FP64 pipe instead of HBM; ``bound`` picks whichever roof binds.
 from __future__ import annotations
 
 ELEM = {"f64": 8, "f32": 4, "bf16": 2}
-CSR_VARIANTS = (0, 1, 2, 3, 4)
+CSR_VARIANTS = (0, 1, 2, 3, 4, 8)
 V_ELL, V_DIA, V_COO = 5, 6, 7
+V_HYB, V_SELL, V_BCSR = 9, 10, 11
 
 
 def algorithmic_bytes(f: dict, variant: int, dtype: str, beta_nonzero: bool = False) -> float:
@@ -36,6 +44,13 @@ def algorithmic_bytes(f: dict, variant: int, dtype: str, beta_nonzero: bool = Fa
         mat = sv * f["ndiags"] * m + 4 * f["ndiags"]
     elif variant == V_COO:
         mat = (sv + 8) * nnz
+    elif variant == V_HYB:
+        mat = (sv + 4) * f["hyb_K"] * m + (sv + 8) * f["hyb_ncoo"]
+    elif variant == V_SELL:
+        mat = (sv + 4) * f["sell_slots"] + 4 * 32 * f["sell_ns"] + 12 * f["sell_ns"] + 8
+    elif variant == V_BCSR:
+        b = f["bcsr_b"]
+        mat = (sv * b * b + 4) * f["bcsr_nb"] + 4 * ((m + b - 1) // b + 1)
     else:
         raise ValueError(variant)
     return float(mat + sx * n + sx * m * (2 if beta_nonzero else 1))
@@ -60,6 +75,12 @@ def fp64_ops(f: dict, variant: int) -> float:
         return float(f["max_rd"] * f["m"])
     if variant == V_DIA:
         return float(f["ndiags"] * f["m"])
+    if variant == V_HYB:
+        return float(f["hyb_K"] * f["m"] + f["hyb_ncoo"])
+    if variant == V_SELL:
+        return float(f["sell_slots"])
+    if variant == V_BCSR:
+        return float(f["bcsr_nb"] * f["bcsr_b"] ** 2)
     return float(f["nnz"])
 
 

@@ -71,9 +71,15 @@ def main():
     except Exception:
         pass
     names = smat.VARIANT_NAMES
-    vs = [v for v in range(8) if (f["admissible"] >> v) & 1] if a.variant == "all" else [names.index(a.variant)]
+    vs = [v for v in range(8) if (f["admissible"] >> v) & 1] + [9, 10, 11] if a.variant == "all" \
+        else [names.index(a.variant)]
     out = {"matrix": A.name, "m": A.m, "nnz": A.nnz, "dtype": a.dtype, "variants": {}}
     for v in vs:
+        try:
+            M.spmv(x, y, variant=v)   # builds the format; further formats may not be admissible
+        except smat.SmatError:
+            continue
+        f = M.features()
         for _ in range(a.warmup):
             M.spmv(x, y, variant=v)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]

@@ -97,11 +97,11 @@ def test_learned_mode_selects_an_admissible_variant():
     try:
         A = synth.stencil3d7(30)
         M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
-        M.tune("learned", conf_threshold=0.0)        # trust the network: no trials
+        M.tune("learned", conf_threshold=0.0, trial_extended=0)   # trust the network: no trials
         plan = M.plan()
         adm = M.features()["admissible"]
         assert (adm >> plan["variant"]) & 1 and 0.0 < plan["confidence"] <= 1.0 and plan["trialled"] == 0
-        M.tune("learned", conf_threshold=1.01, fallback_topk=2)   # always fall back to measuring the top 2
+        M.tune("learned", conf_threshold=1.01, fallback_topk=2, trial_extended=0)  # always measure the top 2
         plan = M.plan()
         assert plan["trialled"] == 1 and (adm >> plan["variant"]) & 1
         assert int(np.sum(M.timings() > 0)) == 2
