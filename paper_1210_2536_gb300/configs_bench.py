@@ -4,10 +4,13 @@
          latency (the matrix lives in L2: a latency case, not a roofline one)
   cfg4   27-point hierarchy 192^3..12^3 + 64 mixed matrices, FP64: one batched
          graph launch vs per-matrix launches (plain and graph-captured)
+  cfg4g  Galerkin AMG hierarchy (smoothed aggregation, P^T A P) of the 27-point
+         operator on 128^3, FP64 and FP32: each level's own plan, one batched
+         launch vs per-matrix launches, every level checked against the oracle
   cfg5   power-law n = 8e6 with FP64 / FP32 / BF16 values (error vs FP64), and
          mixed-precision CG on the 3-D 7-point 256^3 Laplacian
 
-  python -m paper_1210_2536_gb300.configs_bench cfg1|cfg4|cfg5|all [--out results.jsonl]
+  python -m paper_1210_2536_gb300.configs_bench cfg1|cfg4|cfg4g|cfg5|all [--out results.jsonl]
 
 Each prints one JSON line.  The oracle (imported only here, for the error
 columns) is the CPU checker, not part of the measured path.
@@ -69,10 +72,14 @@ def cfg1():
     scale = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(A.val), np.abs(x.cpu().numpy()))
     lat = {}
     err = {}
-    for v in range(8):
-        if not (f["admissible"] >> v) & 1:
+    for v in list(range(8)) + [smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR]:
+        if v < 8 and not (f["admissible"] >> v) & 1:
             continue
         y = torch.empty(A.m, dtype=torch.float64, device=dev)
+        try:
+            M.spmv(x, y, variant=v)   # builds a further format if it is admissible
+        except smat.SmatError:
+            continue
         lat[smat.VARIANT_NAMES[v]] = round(_time(lambda: M.spmv(x, y, variant=v), 50) * 1e3, 2)
         err[smat.VARIANT_NAMES[v]] = float(np.max(np.abs(y.cpu().numpy() - ref) / scale))
     fo = oracle.features(A.m, A.n, A.rowptr, A.colidx)
@@ -138,11 +145,70 @@ def cfg4():
            "small_64_only": {"per_matrix_launches_ms": round(t_small_loop, 4), "batched_ms": round(t_small_batch, 4),
                              "info": Bs.info()},
            "batch_info": info, "batch_tune_s": round(tune_s, 2),
-           "picks": {smat.VARIANT_NAMES[v]: sum(1 for M in hs if M.plan()["variant"] == v) for v in range(8)}}
+           "picks": {smat.VARIANT_NAMES[v]: sum(1 for M in hs if M.plan()["variant"] == v)
+                     for v in range(smat.SMAT_NUM_ALL_VARIANTS)}}
     Bs.close()
     B.close()
     for M in hs:
         M.close()
+    return out
+
+
+def cfg4g(m_fine=128):
+    import torch
+
+    import oracle
+    import paper_1210_2536_gb300 as smat
+    from . import synth
+    from .roofline import algorithmic_bytes
+    dev = torch.device("cuda:0")
+    select = _select()
+    t0 = time.perf_counter()
+    mats = synth.galerkin_hierarchy(m_fine, 5)
+    gen_s = time.perf_counter() - t0
+    threads = os.cpu_count() or 1
+    peak = _peak()
+    out = {"config": f"Galerkin AMG hierarchy (smoothed aggregation) of the 27-point operator on {m_fine}^3",
+           "selector": select, "generate_s": round(gen_s, 1),
+           "levels": [{"name": A.name, "m": A.m, "nnz": A.nnz, "max_rd": int(np.diff(A.rowptr).max())} for A in mats]}
+    for dt in ("f64", "f32"):
+        npdt = np.float64 if dt == "f64" else np.float32
+        hs, xs, ys, per_level = [], [], [], []
+        for i, A in enumerate(mats):
+            vals = A.val if dt == "f64" else A.val.astype(np.float32)
+            M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                              torch.from_numpy(vals).to(dev), dt)
+            M.tune(select)
+            x = synth.uniform(60 + i, 1, A.n).astype(npdt)
+            xd = torch.from_numpy(x).to(dev)
+            y = M.spmv(xd)
+            ms = _time(lambda: M.spmv(xd, y), 20)
+            v64 = np.asarray(vals, dtype=np.float64)
+            ref = oracle.spmv_csr(A.m, A.rowptr, A.colidx, v64, x.astype(np.float64), threads=threads)
+            sc = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(v64), np.abs(x.astype(np.float64)), threads=threads)
+            err = float(np.max(np.abs(y.double().cpu().numpy() - ref) / np.maximum(sc, 1e-300)))
+            b = algorithmic_bytes(M.features(), M.plan()["variant"], dt)
+            per_level.append({"level": i, "pick": M.plan()["name"], "ms": round(ms, 4),
+                              "gflops": round(2 * A.nnz / ms / 1e6, 1), "hbm_frac": round(b / ms / 1e6 / peak, 4),
+                              "max_err_normalized": err})
+            hs.append(M)
+            xs.append(xd)
+            ys.append(torch.zeros(A.m, dtype=xd.dtype, device=dev))
+        nnz = sum(A.nnz for A in mats)
+        B = smat.Batch(hs).tune()
+
+        def per_matrix():
+            for M, x, y in zip(hs, xs, ys):
+                M.spmv(x, y)
+
+        t_loop = _time(per_matrix, 20)
+        t_batch = _time(lambda: B.spmv(xs, ys), 20)
+        out[dt] = {"per_level": per_level, "per_matrix_launches_ms": round(t_loop, 4),
+                   "batched_ms": round(t_batch, 4), "batched_gflops": round(2 * nnz / t_batch / 1e6, 1),
+                   "per_matrix_gflops": round(2 * nnz / t_loop / 1e6, 1), "batch_info": B.info()}
+        B.close()
+        for M in hs:
+            M.close()
     return out
 
 
@@ -219,14 +285,14 @@ def cfg5(cg_total=500, cg_cap=5000):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["cfg1", "cfg4", "cfg5", "all"])
+    ap.add_argument("which", choices=["cfg1", "cfg4", "cfg4g", "cfg5", "all"])
     ap.add_argument("--out")
     a = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
-    todo = ["cfg1", "cfg4", "cfg5"] if a.which == "all" else [a.which]
+    todo = ["cfg1", "cfg4", "cfg4g", "cfg5"] if a.which == "all" else [a.which]
     for w in todo:
-        res = {"cfg1": cfg1, "cfg4": cfg4, "cfg5": cfg5}[w]()
+        res = {"cfg1": cfg1, "cfg4": cfg4, "cfg4g": cfg4g, "cfg5": cfg5}[w]()
         line = json.dumps(res)
         print(line, flush=True)
         if a.out:

@@ -4,9 +4,11 @@
 // are different sparse matrices used one after another (Sec. 1): no single
 // format fits all levels, and the coarse levels are far too small to fill a
 // GPU on their own.  Here every matrix keeps the format its own tuning chose
-// (CSR with 1/4/8/32 lanes per row, ELL or DIA); the products are cut into row
-// tiles, sorted largest first into one work table, and a persistent grid
-// takes tiles from an atomic counter until the table is empty.  The counter
+// (CSR with 1/4/8/32 lanes per row, ELL, DIA or SELL; HYB and BCSR members
+// run through their fastest measured CSR kernel); the products are cut into
+// row (SELL: slice) tiles, sorted largest first into one work table per
+// format kind, and persistent grids take tiles from atomic counters until
+// the tables are empty.  The counter
 // reset and the kernel are captured once in a CUDA graph, so one product of
 // the whole batch is one graph launch.  An autotuner picks the tile size and
 // the number of resident CTAs per SM by timing the captured graph.
@@ -22,7 +24,7 @@
 namespace smat {
 namespace {
 
-enum : int { KIND_CSR = 0, KIND_ELL = 1, KIND_DIA = 2 };
+enum : int { KIND_CSR = 0, KIND_ELL = 1, KIND_DIA = 2, KIND_SELL = 3, NKIND = 4 };
 
 struct BatchMat {
   int kind, W, nd, epi;
@@ -33,6 +35,9 @@ struct BatchMat {
   const void *eval;
   const int32_t *doff;
   const void *dval;
+  const long long *sptr;
+  const int32_t *swidth, *sperm, *scol;
+  const void *sval;
   const void *x;
   void *y;
   double alpha, beta;
@@ -97,6 +102,10 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
   } else if (KIND == KIND_DIA) {
     for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
       dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
+  } else if (KIND == KIND_SELL) {  // row0 / row1 are slice indices; a warp per slice
+    for (long long sl = tl.row0 + threadIdx.x / 32; sl < tl.row1; sl += BNT / 32)
+      sell_slice<V, MODE, 8>(M.sptr, M.swidth, M.sperm, M.scol, (const V *)M.sval, (const T *)M.x, ep, (T *)M.y, sl,
+                             threadIdx.x & 31);
   } else {
     switch (M.W) {
       case 1: csr_rows<V, T, 1, MODE>(M, ep, tl.row0, tl.row1); break;
@@ -146,6 +155,7 @@ cudaError_t launch_batch_kernel(int kind, smat_dtype_t dt, int grid, const Batch
                                 int ntiles, unsigned int *counter, cudaStream_t s) {
   if (kind == KIND_ELL) return launch_kind<KIND_ELL>(dt, grid, mats, tiles, ntiles, counter, s);
   if (kind == KIND_DIA) return launch_kind<KIND_DIA>(dt, grid, mats, tiles, ntiles, counter, s);
+  if (kind == KIND_SELL) return launch_kind<KIND_SELL>(dt, grid, mats, tiles, ntiles, counter, s);
   return launch_kind<KIND_CSR>(dt, grid, mats, tiles, ntiles, counter, s);
 }
 
@@ -157,14 +167,15 @@ struct smat_batch_s {
   smat_dtype_t dtype = SMAT_F64;
   std::vector<smat::BatchMat> mats;        // host copy of the descriptors
   std::vector<std::vector<int32_t>> rowptrs;  // CSR members: row pointers for nnz-balanced tiles
+  std::vector<std::vector<long long>> sptrs;  // SELL members: slice pointers for slot-balanced tiles
   smat::BatchMat *d_mats = nullptr;
   smat::BatchTile *d_tiles = nullptr;
   unsigned int *d_counter = nullptr;  // one tile counter per format kind
   int ntiles = 0, grid = 0, tile_scale = 0, ctas_per_sm = 0;
-  int kind_tiles[3] = {0, 0, 0}, kind_first[3] = {0, 0, 0}, kind_grid[3] = {0, 0, 0};
+  int kind_tiles[smat::NKIND] = {}, kind_first[smat::NKIND] = {}, kind_grid[smat::NKIND] = {};
   double tuned_ms = -1.0;
-  cudaStream_t cap = nullptr, fork[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  cudaStream_t cap = nullptr, fork[smat::NKIND - 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[smat::NKIND - 1] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ready = false;
@@ -235,6 +246,17 @@ std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
         v.push_back({{(int)i, (int)r0, (int)r1, 0}, (long long)rp[r1] - rp[r0] + (r1 - r0)});
         r0 = r1;
       }
+    } else if (M.kind == KIND_SELL) {
+      const std::vector<long long> &sp = b->sptrs[i];
+      const long long ns = (long long)sp.size() - 1, target = 2048LL * scale, cap_sl = 8LL * 8 * scale;
+      long long s0 = 0;
+      while (s0 < ns) {
+        long long s1 = s0;
+        while (s1 < ns && sp[s1] - sp[s0] < target && s1 - s0 < cap_sl) ++s1;
+        if (s1 == s0) ++s1;
+        v.push_back({{(int)i, (int)s0, (int)s1, 0}, sp[s1] - sp[s0] + 32 * (s1 - s0)});
+        s0 = s1;
+      }
     } else {
       const long long rows = (long long)BNT * R * scale;
       const long long per_row = M.kind == KIND_ELL ? M.K : M.nd;
@@ -244,7 +266,7 @@ std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
       }
     }
   }
-  // grouped by format kind (CSR, ELL, DIA), each group largest first
+  // grouped by format kind (CSR, ELL, DIA, SELL), each group largest first
   std::stable_sort(v.begin(), v.end(), [&](const Est &a, const Est &c) {
     const int ka = b->mats[(size_t)a.t.mat].kind, kc = b->mats[(size_t)c.t.mat].kind;
     return ka != kc ? ka < kc : a.w > c.w;
@@ -261,11 +283,10 @@ smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
   b->d_tiles = nullptr;
   std::vector<BatchTile> tiles = make_tiles(b, scale);
   b->ntiles = (int)tiles.size();
-  for (int k = 0; k < 3; ++k) b->kind_tiles[k] = 0;
+  for (int k = 0; k < NKIND; ++k) b->kind_tiles[k] = 0;
   for (const BatchTile &t : tiles) ++b->kind_tiles[b->mats[(size_t)t.mat].kind];
   b->kind_first[0] = 0;
-  b->kind_first[1] = b->kind_tiles[0];
-  b->kind_first[2] = b->kind_tiles[0] + b->kind_tiles[1];
+  for (int k = 1; k < NKIND; ++k) b->kind_first[k] = b->kind_first[k - 1] + b->kind_tiles[k - 1];
   if (b->ntiles > 0) {
     void *p = nullptr;
     BTRY(dev_alloc(&p, tiles.size() * sizeof(BatchTile)));
@@ -276,24 +297,24 @@ smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < NKIND; ++k) {
     b->kind_grid[k] = b->kind_tiles[k] > 0 ? std::min(sms * ctas_per_sm, b->kind_tiles[k]) : 0;
     b->grid += b->kind_grid[k];
   }
   b->tile_scale = scale;
   b->ctas_per_sm = ctas_per_sm;
-  // capture: reset the three tile counters, then one persistent kernel per
-  // format kind on parallel branches of the graph
+  // capture: reset the tile counters, then one persistent kernel per format
+  // kind on parallel branches of the graph
   BTRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t err = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(unsigned int), b->cap);
+  cudaError_t err = cudaMemsetAsync(b->d_counter, 0, NKIND * sizeof(unsigned int), b->cap);
   if (err == cudaSuccess) err = cudaEventRecord(b->ev_fork, b->cap);
-  cudaStream_t st[3] = {b->cap, b->fork[0], b->fork[1]};
-  for (int k = 1; k < 3 && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(st[k], b->ev_fork, 0);
-  for (int k = 0; k < 3 && err == cudaSuccess; ++k)
+  cudaStream_t st[NKIND] = {b->cap, b->fork[0], b->fork[1], b->fork[2]};
+  for (int k = 1; k < NKIND && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(st[k], b->ev_fork, 0);
+  for (int k = 0; k < NKIND && err == cudaSuccess; ++k)
     if (b->kind_tiles[k] > 0)
       err = launch_batch_kernel(k, b->dtype, b->kind_grid[k], b->d_mats, b->d_tiles + b->kind_first[k],
                                 b->kind_tiles[k], b->d_counter + k, st[k]);
-  for (int k = 1; k < 3 && err == cudaSuccess; ++k) {
+  for (int k = 1; k < NKIND && err == cudaSuccess; ++k) {
     err = cudaEventRecord(b->ev_join[k - 1], st[k]);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, b->ev_join[k - 1], 0);
   }
@@ -325,12 +346,14 @@ smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int3
   b->dtype = hs[0]->dtype;
   auto fail = [&](smat_status_t s) { smat_batch_destroy(b); return s; };
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking);
+  for (int k = 0; k < NKIND - 1 && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  for (int k = 0; k < NKIND - 1 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(SMAT_ERR_CUDA);
   void *p = nullptr;
-  if ((e = dev_alloc(&p, 3 * sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
+  if ((e = dev_alloc(&p, NKIND * sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
   b->d_counter = (unsigned int *)p;
   if ((e = dev_alloc(&p, sizeof(BatchMat) * (size_t)count)) != cudaSuccess) return fail(st_of(e));
   b->d_mats = (BatchMat *)p;
@@ -345,7 +368,7 @@ smat_status_t smat_batch_destroy(smat_batch_t b) {
   dev_free(b->d_tiles);
   dev_free(b->d_mats);
   dev_free(b->d_counter);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NKIND - 1; ++k) {
     if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
     if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
   }
@@ -363,6 +386,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
   const int n = (int)b->hs.size();
   b->mats.assign((size_t)n, BatchMat{});
   b->rowptrs.assign((size_t)n, {});
+  b->sptrs.assign((size_t)n, {});
   const int tsz = b->dtype == SMAT_F64 ? 8 : 4;
   // per-matrix descriptors from each handle's plan, with scratch x / y for timing
   std::vector<void *> tmp;
@@ -375,6 +399,11 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
       M.kind = KIND_ELL; M.ecol = h->ell_col; M.eval = h->ell_val; M.K = h->ell_K;
     } else if (h->variant == SMAT_V_DIA && h->dia_val) {
       M.kind = KIND_DIA; M.doff = h->dia_off; M.dval = h->dia_val; M.nd = (int)h->dia_nd;
+    } else if (h->variant == SMAT_V_SELL && h->sell_val) {
+      M.kind = KIND_SELL; M.sptr = h->sell_ptr; M.swidth = h->sell_width; M.sperm = h->sell_perm;
+      M.scol = h->sell_col; M.sval = h->sell_val;
+      b->sptrs[(size_t)i].resize((size_t)h->sell_ns + 1);
+      BTRY(cudaMemcpy(b->sptrs[(size_t)i].data(), h->sell_ptr, (size_t)(h->sell_ns + 1) * 8, cudaMemcpyDeviceToHost));
     } else {
       M.kind = KIND_CSR; M.W = csr_width(h); M.rowptr = h->rowptr; M.colidx = h->colidx; M.val = h->val;
       b->rowptrs[(size_t)i].resize((size_t)h->m + 1);
@@ -442,7 +471,8 @@ smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *co
     const double c = b->dtype == SMAT_F64 ? ((const double *)betas)[i] : (double)((const float *)betas)[i];
     if ((M.m > 0 && !ys[i]) || (M.n > 0 && M.m > 0 && !xs[i])) return SMAT_ERR_INVALID_ARG;
     // ELL and DIA members read x and write y with 16-byte vector accesses
-    if (M.kind != KIND_CSR && (((uintptr_t)xs[i] | (uintptr_t)ys[i]) & 15u) != 0) return SMAT_ERR_INVALID_ARG;
+    if ((M.kind == KIND_ELL || M.kind == KIND_DIA) && (((uintptr_t)xs[i] | (uintptr_t)ys[i]) & 15u) != 0)
+      return SMAT_ERR_INVALID_ARG;
     if (M.x != xs[i] || M.y != ys[i] || M.alpha != a || M.beta != c) {
       M.x = xs[i]; M.y = ys[i]; M.alpha = a; M.beta = c;
       M.epi = epi_mode(a, c);

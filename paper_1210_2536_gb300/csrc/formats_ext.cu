@@ -287,9 +287,7 @@ __global__ void to_bcsr_kernel(const int32_t *__restrict__ rowptr, const int32_t
 }
 
 // ---------------------------------------------------------------------------
-// SELL SpMV: a warp per slice, a lane per row; U slots loaded before their
-// gathers.  The slice width is uniform over the warp, so no lane diverges;
-// padding (column -1) gathers x[0] and is dropped by a select.
+// SELL SpMV: a warp per slice (sell_slice), a lane per row.
 // ---------------------------------------------------------------------------
 template <typename V, int MODE, int U>
 __global__ void __launch_bounds__(256) sell_kernel(const long long *__restrict__ sptr, const int32_t *__restrict__ width,
@@ -297,29 +295,9 @@ __global__ void __launch_bounds__(256) sell_kernel(const long long *__restrict__
                                                    const V *__restrict__ sval, const typename Compute<V>::T *__restrict__ x,
                                                    Epi<typename Compute<V>::T, MODE> ep,
                                                    typename Compute<V>::T *__restrict__ y, long long ns) {
-  typedef typename Compute<V>::T T;
   const long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / SELL_C;
   if (sl >= ns) return;
-  const int lane = threadIdx.x & 31;
-  const long long base = __ldg(sptr + sl) + lane;
-  const int w = __ldg(width + sl);
-  T acc = 0;
-  for (int j = 0; j < w; j += U) {
-    int c[U];
-    T v[U], xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool on = j + u < w;
-      c[u] = on ? ld_idx(scol + base + (long long)(j + u) * SELL_C) : -1;
-      v[u] = on ? (T)ld_val(sval + base + (long long)(j + u) * SELL_C) : (T)0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + (c[u] > 0 ? c[u] : 0));
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc = fused(acc, v[u], c[u] >= 0 ? xv[u] : (T)0);
-  }
-  const int r = __ldg(perm + sl * SELL_C + lane);
-  if (r >= 0) y[r] = ep(acc, y, (long long)r);
+  sell_slice<V, MODE, U>(sptr, width, perm, scol, sval, x, ep, y, sl, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

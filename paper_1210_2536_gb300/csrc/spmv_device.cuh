@@ -253,5 +253,38 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
   write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
 
+
+// One SELL-32 slice: lane l computes the row at sorted position 32*sl + l over
+// the slice's `w` slots, U slots loaded before their gathers.  w is uniform
+// over the warp, so no lane diverges; padding (column -1) gathers x[0] and is
+// dropped by a select.
+template <typename V, int MODE, int U>
+__device__ __forceinline__ void sell_slice(const long long *__restrict__ sptr, const int32_t *__restrict__ width,
+                                           const int32_t *__restrict__ perm, const int32_t *__restrict__ scol,
+                                           const V *__restrict__ sval, const typename Compute<V>::T *__restrict__ x,
+                                           const Epi<typename Compute<V>::T, MODE> &ep,
+                                           typename Compute<V>::T *__restrict__ y, long long sl, int lane) {
+  typedef typename Compute<V>::T T;
+  const long long base = __ldg(sptr + sl) + lane;
+  const int w = __ldg(width + sl);
+  T acc = 0;
+  for (int j = 0; j < w; j += U) {
+    int c[U];
+    T v[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool on = j + u < w;
+      c[u] = on ? ld_idx(scol + base + (long long)(j + u) * 32) : -1;
+      v[u] = on ? (T)ld_val(sval + base + (long long)(j + u) * 32) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + (c[u] > 0 ? c[u] : 0));
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = fused(acc, v[u], c[u] >= 0 ? xv[u] : (T)0);
+  }
+  const int r = __ldg(perm + sl * 32 + lane);
+  if (r >= 0) y[r] = ep(acc, y, (long long)r);
+}
+
 }  // namespace
 }  // namespace smat

@@ -236,6 +236,49 @@ def amg_like_hierarchy(top: int = 192):
     return [stencil3d27(top >> lvl) for lvl in range(5)]
 
 
+def aggregation_prolongator(m: int, A: CSR, omega: float = 2.0 / 3.0) -> "scipy.sparse.csr_matrix":
+    """Smoothed-aggregation prolongator of an m x m x m grid operator A (points
+    ordered x fastest): the tentative P0 maps each point to its 2 x 2 x 2 box
+    aggregate ((x//2) + mc (y//2) + mc^2 (z//2), mc = ceil(m/2)) with weight 1,
+    and one damped-Jacobi step smooths it: P = (I - omega D^-1 A) P0."""
+    import scipy.sparse as sp
+    mc = (m + 1) // 2
+    i = np.arange(A.m, dtype=np.int64)
+    x, y, z = i % m, (i // m) % m, i // (m * m)
+    agg = (x // 2) + mc * (y // 2) + mc * mc * (z // 2)
+    P0 = sp.csr_matrix((np.ones(A.m), (i, agg)), shape=(A.m, mc ** 3))
+    As = sp.csr_matrix((A.val, A.colidx, A.rowptr), shape=(A.m, A.n))
+    dinv = 1.0 / As.diagonal()
+    return (P0 - omega * sp.diags(dinv) @ (As @ P0)).tocsr()
+
+
+def galerkin_hierarchy(m: int = 96, levels: int = 5, omega: float = 2.0 / 3.0):
+    """An algebraic-multigrid hierarchy with Galerkin coarse operators: level 0
+    is the 27-point operator (26 / -1) on m^3; level l+1 is P^T A_l P with the
+    smoothed-aggregation prolongator of level l (``aggregation_prolongator``).
+    Each coarse stencil is wider than the last (125 points on level 1 where
+    the grid allows, then wider still), so the levels differ in structure the
+    way the operators of an AMG solve do.  Host-side input generation
+    (scipy.sparse products), FP64 values, canonical CSR."""
+    import scipy.sparse as sp
+    A = stencil3d27(m)
+    out = [A]
+    g = m
+    for lvl in range(1, levels):
+        if g < 2:
+            break
+        P = aggregation_prolongator(g, A, omega)
+        As = sp.csr_matrix((A.val, A.colidx, A.rowptr), shape=(A.m, A.n))
+        Ac = (P.T.tocsr() @ (As @ P)).tocsr()
+        Ac.sum_duplicates()
+        Ac.sort_indices()
+        g = (g + 1) // 2
+        A = CSR(Ac.shape[0], Ac.shape[1], Ac.indptr.astype(np.int32), Ac.indices.astype(np.int32),
+                Ac.data.astype(np.float64), f"galerkin_L{lvl}_{g}^3_from_27pt_{m}^3")
+        out.append(A)
+    return out
+
+
 def mixed_batch(count: int = 64, n_lo: float = 1e3, n_hi: float = 1e6, base_seed: int = 0):
     """``count`` independent matrices, n log-uniform on [n_lo, n_hi], structure
     cycling through uniform random, power-law, block diagonal and 3-D 7-point."""

@@ -76,3 +76,30 @@ def test_batch_rejects_mixed_dtypes_and_untuned_use():
         B.spmv([x], [y])  # not tuned yet
     B.close()
     h64.close(), h32.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_galerkin_hierarchy(dtype):
+    # the AMG setting: Galerkin coarse operators (P^T A P, smoothed
+    # aggregation) of a 27-point operator, every level planned on its own and
+    # all levels in one batched launch
+    pytest.importorskip("scipy")
+    mats = synth.galerkin_hierarchy(24, 5)
+    hs = _handles(mats, dtype)
+    B = smat.Batch(hs).tune(trial_reps=3)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    xs = [torch.from_numpy(synth.uniform(40 + i, 1, A.n).astype(npdt)).to(DEV) for i, A in enumerate(mats)]
+    y0 = [synth.uniform(50 + i, 2, A.m).astype(npdt) for i, A in enumerate(mats)]
+    ys = [torch.from_numpy(v.copy()).to(DEV) for v in y0]
+    B.spmv(xs, ys, [1.0] * len(mats), [0.5] * len(mats))
+    torch.cuda.synchronize()
+    for i, A in enumerate(mats):
+        _, v64 = stored_values(A, dtype)
+        ref, scale = reference(A, v64, xs[i].cpu().numpy(), 1.0, 0.5, y0[i])
+        assert_close_rows(ys[i].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype], f"level {i} ({A.name})")
+        single = hs[i].spmv(xs[i]).cpu().numpy().astype(np.float64)
+        ref1, scale1 = reference(A, v64, xs[i].cpu().numpy(), 1.0, 0.0, None)
+        assert_close_rows(single, ref1, scale1, TOL[dtype], f"level {i} ({A.name}) own plan {hs[i].plan()['name']}")
+    B.close()
+    for M in hs:
+        M.close()
