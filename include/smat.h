@@ -359,13 +359,18 @@ smat_status_t smat_batch_destroy(smat_batch_t b);
 /* Split h's rows into `nseg` segments holding about NNZ/nseg stored entries
  * each (boundaries at whole rows, rounded down to multiples of 8 rows; fewer
  * segments when rows are too long to split), give every segment its own
- * handle tuned with `opts` (NULL: as in smat_tune), and batch them.  h must
- * stay alive while the segments exist.  Returns after `stream` is idle. */
+ * handle tuned with `opts` (NULL: as in smat_tune), and batch them when every
+ * segment's plan is one the batched kernel runs natively (CSR-scalar /
+ * vector, ELL, DIA, SELL); otherwise give each segment a stream of its own.
+ * h must stay alive while the segments exist.  Returns after `stream` is
+ * idle. */
 smat_status_t smat_segments_create(smat_segments_t *out, smat_handle_t h, int32_t nseg,
                                    const smat_tune_opts_t *opts, void *stream);
 
-/* y = alpha*A*x + beta*y with every segment in its own format, one batched
- * launch; x[n], y[m] DEVICE pointers of the compute type, alpha/beta HOST
+/* y = alpha*A*x + beta*y with every segment in its own format: one batched
+ * launch, or each segment's own kernels on its own stream (forked from
+ * `stream` by an event and joined back to it, so the call stays ordered on
+ * `stream`); x[n], y[m] DEVICE pointers of the compute type, alpha/beta HOST
  * scalars.  Vectors that are not 16-byte aligned take h's own plan. */
 smat_status_t smat_segments_spmv(smat_segments_t s, const void *alpha, const void *x, const void *beta, void *y,
                                  void *stream);

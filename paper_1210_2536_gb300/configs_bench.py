@@ -7,10 +7,13 @@
   cfg4g  Galerkin AMG hierarchy (smoothed aggregation, P^T A P) of the 27-point
          operator on 128^3, FP64 and FP32: each level's own plan, one batched
          launch vs per-matrix launches, every level checked against the oracle
+  cfgseg per-segment plans (Sec. 6) on the 7-point 128^3 stencil stacked over
+         a 2e6-row power-law graph, FP64 and FP32: the whole-matrix plan
+         against 2, 4 and 8 nonzero-balanced segments, each with its own format
   cfg5   power-law n = 8e6 with FP64 / FP32 / BF16 values (error vs FP64), and
          mixed-precision CG on the 3-D 7-point 256^3 Laplacian
 
-  python -m paper_1210_2536_gb300.configs_bench cfg1|cfg4|cfg4g|cfg5|all [--out results.jsonl]
+  python -m paper_1210_2536_gb300.configs_bench cfg1|cfg4|cfg4g|cfgseg|cfg5|all [--out results.jsonl]
 
 Each prints one JSON line.  The oracle (imported only here, for the error
 columns) is the CPU checker, not part of the measured path.
@@ -212,6 +215,51 @@ def cfg4g(m_fine=128):
     return out
 
 
+def cfgseg(m=128):
+    import torch
+
+    import oracle
+    import paper_1210_2536_gb300 as smat
+    from . import synth
+    dev = torch.device("cuda:0")
+    select = _select()
+    A = synth.stencil_over_powerlaw(m)
+    threads = os.cpu_count() or 1
+    out = {"config": f"per-segment plans: {A.name}", "m": A.m, "nnz": A.nnz, "selector": select}
+    for dt in ("f64", "f32"):
+        npdt = np.float64 if dt == "f64" else np.float32
+        vals = A.val if dt == "f64" else A.val.astype(np.float32)
+        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                          torch.from_numpy(vals).to(dev), dt)
+        M.tune(select)
+        x = synth.uniform(0, 1, A.n).astype(npdt)
+        xd = torch.from_numpy(x).to(dev)
+        y = torch.zeros(A.m, dtype=xd.dtype, device=dev)
+        v64 = np.asarray(vals, dtype=np.float64)
+        ref = oracle.spmv_csr(A.m, A.rowptr, A.colidx, v64, x.astype(np.float64), threads=threads)
+        sc = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(v64), np.abs(x.astype(np.float64)), threads=threads)
+
+        def err_of(yy):
+            return float(np.max(np.abs(yy.double().cpu().numpy() - ref) / np.maximum(sc, 1e-300)))
+
+        M.spmv(xd, y)
+        whole = {"pick": M.plan()["name"], "ms": round(_time(lambda: M.spmv(xd, y), 20), 4), "max_err": err_of(y)}
+        segs = {}
+        for k in (2, 4, 8):
+            t0 = time.perf_counter()
+            S = smat.Segments(M, k, select)
+            build_s = time.perf_counter() - t0
+            S.spmv(xd, y)
+            segs[str(k)] = {"picks": S.info()["variants"], "ms": round(_time(lambda: S.spmv(xd, y), 20), 4),
+                            "max_err": err_of(y), "build_s": round(build_s, 2)}
+            S.close()
+        out[dt] = {"whole": whole, "segments": segs,
+                   "gflops_whole": round(2 * A.nnz / whole["ms"] / 1e6, 1),
+                   "gflops_best_segments": round(2 * A.nnz / min(v["ms"] for v in segs.values()) / 1e6, 1)}
+        M.close()
+    return out
+
+
 def cfg5(cg_total=500, cg_cap=5000):
     import torch
 
@@ -285,14 +333,14 @@ def cfg5(cg_total=500, cg_cap=5000):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["cfg1", "cfg4", "cfg4g", "cfg5", "all"])
+    ap.add_argument("which", choices=["cfg1", "cfg4", "cfg4g", "cfgseg", "cfg5", "all"])
     ap.add_argument("--out")
     a = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
-    todo = ["cfg1", "cfg4", "cfg4g", "cfg5"] if a.which == "all" else [a.which]
+    todo = ["cfg1", "cfg4", "cfg4g", "cfgseg", "cfg5"] if a.which == "all" else [a.which]
     for w in todo:
-        res = {"cfg1": cfg1, "cfg4": cfg4, "cfg4g": cfg4g, "cfg5": cfg5}[w]()
+        res = {"cfg1": cfg1, "cfg4": cfg4, "cfg4g": cfg4g, "cfgseg": cfgseg, "cfg5": cfg5}[w]()
         line = json.dumps(res)
         print(line, flush=True)
         if a.out:

@@ -6,9 +6,13 @@
 // changes from one part to another).
 //
 // Each segment becomes a handle of its own (a copy of its rows, row pointers
-// rebased to 0, all N columns), tuned by its own features; the segments run
-// together as one batched launch (batch.cu) that reads the shared x and
-// writes each segment's slice of y.
+// rebased to 0, all N columns), tuned by its own features.  When every
+// segment's plan is a kind the batched kernel runs natively (CSR with 1/4/8/32
+// lanes, ELL, DIA, SELL) the segments run together as one batched launch
+// (batch.cu); otherwise (COO, merge-path, HYB, BCSR) each segment runs its own
+// plan on a stream of its own, forked from and joined back to the caller's
+// stream, so the segments' kernels overlap.  Both read the shared x and write
+// each segment's slice of y.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -20,14 +24,32 @@ struct smat_segments_s {
   smat_handle_t parent = nullptr;
   std::vector<smat_handle_t> subs;
   std::vector<int64_t> starts;  // row starts, size nseg + 1
-  smat_batch_t batch = nullptr;
+  smat_batch_t batch = nullptr;  // when every plan is batch-native
+  std::vector<cudaStream_t> streams;  // otherwise: a stream per segment
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
 };
+
+namespace {
+
+bool batch_native(int v) {
+  return v == SMAT_V_CSR_SCALAR || v == SMAT_V_CSR_VEC4 || v == SMAT_V_CSR_VEC8 || v == SMAT_V_CSR_VEC32 ||
+         v == SMAT_V_ELL || v == SMAT_V_DIA || v == SMAT_V_SELL;
+}
+
+}  // namespace
 
 extern "C" {
 
 smat_status_t smat_segments_destroy(smat_segments_t s) {
   if (!s) return SMAT_OK;
   smat_batch_destroy(s->batch);
+  for (cudaStream_t st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t e : s->joins) cudaEventDestroy(e);
+  if (s->fork) cudaEventDestroy(s->fork);
   for (smat_handle_t h : s->subs) smat_destroy(h);
   delete s;
   return SMAT_OK;
@@ -70,9 +92,21 @@ smat_status_t smat_segments_create(smat_segments_t *out, smat_handle_t h, int32_
     s->subs.push_back(sub);
     if ((st = smat_tune(sub, opts, stream)) != SMAT_OK) return fail(st);
   }
-  smat_status_t st = smat_batch_create(&s->batch, s->subs.data(), (int32_t)s->subs.size());
-  if (st == SMAT_OK) st = smat_batch_tune(s->batch, nullptr, stream);
-  if (st != SMAT_OK) return fail(st);
+  bool native = true;
+  for (smat_handle_t sub : s->subs) native = native && batch_native(sub->variant);
+  if (native) {
+    smat_status_t st = smat_batch_create(&s->batch, s->subs.data(), (int32_t)s->subs.size());
+    if (st == SMAT_OK) st = smat_batch_tune(s->batch, nullptr, stream);
+    if (st != SMAT_OK) return fail(st);
+  } else {
+    s->streams.assign(s->subs.size(), nullptr);
+    s->joins.assign(s->subs.size(), nullptr);
+    if (cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess) return fail(SMAT_ERR_CUDA);
+    for (size_t k = 0; k < s->subs.size(); ++k)
+      if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s->joins[k], cudaEventDisableTiming) != cudaSuccess)
+        return fail(SMAT_ERR_CUDA);
+  }
   *out = s;
   return SMAT_OK;
 }
@@ -84,6 +118,19 @@ smat_status_t smat_segments_spmv(smat_segments_t s, const void *alpha, const voi
   const int tsz = s->parent->dtype == SMAT_F64 ? 8 : 4;
   if ((((uintptr_t)x | (uintptr_t)y) & 15u) != 0)  // segments with vector accesses need aligned vectors
     return smat_spmv(s->parent, alpha, x, beta, y, stream);
+  if (!s->batch) {  // each segment through its own plan, on its own stream
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (cudaEventRecord(s->fork, cs) != cudaSuccess) return SMAT_ERR_CUDA;
+    for (size_t k = 0; k < n; ++k) {
+      if (cudaStreamWaitEvent(s->streams[k], s->fork, 0) != cudaSuccess) return SMAT_ERR_CUDA;
+      smat_status_t st = smat_spmv(s->subs[k], alpha, x, beta, (char *)y + s->starts[k] * tsz, s->streams[k]);
+      if (st != SMAT_OK) return st;
+      if (cudaEventRecord(s->joins[k], s->streams[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(cs, s->joins[k], 0) != cudaSuccess)
+        return SMAT_ERR_CUDA;
+    }
+    return SMAT_OK;
+  }
   std::vector<const void *> xs(n, x);
   std::vector<void *> ys(n);
   std::vector<unsigned char> al(n * (size_t)tsz), be(n * (size_t)tsz);

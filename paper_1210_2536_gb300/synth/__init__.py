@@ -236,6 +236,18 @@ def amg_like_hierarchy(top: int = 192):
     return [stencil3d27(top >> lvl) for lvl in range(5)]
 
 
+def stencil_over_powerlaw(m: int = 128, kmax: int = 10000, seed: int = 5) -> CSR:
+    """The 3-D 7-point stencil on m^3 (banded) stacked over as many rows of a
+    power-law graph (Zipf(1.8) rows, uniform columns) on the same m^3 columns:
+    a matrix whose structure changes halfway down, the case per-segment
+    formats are for."""
+    top = stencil3d7(m)
+    bot = powerlaw(top.n, 1.8, kmax, seed)
+    rp = np.concatenate([top.rowptr[:-1].astype(np.int64), bot.rowptr.astype(np.int64) + top.nnz])
+    return CSR(top.m + bot.m, top.n, rp.astype(np.int32), np.concatenate([top.colidx, bot.colidx]),
+               np.concatenate([top.val, bot.val]), f"stencil3d7_{m}^3_over_powerlaw_cap{kmax}")
+
+
 def aggregation_prolongator(m: int, A: CSR, omega: float = 2.0 / 3.0) -> "scipy.sparse.csr_matrix":
     """Smoothed-aggregation prolongator of an m x m x m grid operator A (points
     ordered x fastest): the tentative P0 maps each point to its 2 x 2 x 2 box

@@ -7,7 +7,6 @@ import pytest
 import oracle
 import paper_1210_2536_gb300 as smat
 from paper_1210_2536_gb300 import synth
-from paper_1210_2536_gb300.synth import CSR
 from helpers import TOL, assert_close_rows, reference, stored_values
 
 torch = pytest.importorskip("torch")
@@ -16,11 +15,7 @@ DEV = "cuda:0"
 
 
 def _stacked():
-    top = synth.stencil3d7(24)                       # 13824 rows, banded
-    bot = synth.powerlaw(top.n, 1.8, 2000, 5)       # same column count, irregular
-    rp = np.concatenate([top.rowptr[:-1], bot.rowptr.astype(np.int64) + top.nnz]).astype(np.int32)
-    return CSR(top.m + bot.m, top.n, rp, np.concatenate([top.colidx, bot.colidx]),
-               np.concatenate([top.val, bot.val]), "stencil_over_powerlaw")
+    return synth.stencil_over_powerlaw(24, 2000, 5)   # 13824 banded rows over 13824 irregular ones
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
