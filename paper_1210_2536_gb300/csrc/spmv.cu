@@ -343,6 +343,55 @@ __device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full,
   }
 }
 
+// One chunk of up to IPT consecutive stored entries of a COO tile: each
+// product is one fused multiply-add into acc; where a row ends inside the
+// chunk (row[k+1] differs) its sum is written, except the thread's first row
+// end, which is held back in first_row / first_acc for the tile's carries.
+template <typename T, int IPT, int MODE>
+__device__ __forceinline__ void coo_chunk(const int (&r)[IPT], const int (&c)[IPT], const T (&v)[IPT], int r_next,
+                                          int valid, const T *__restrict__ x, const Epi<T, MODE> &ep, T *__restrict__ y,
+                                          T &acc, int &first_row, T &first_acc) {
+  T xv[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) xv[q] = q < valid ? __ldg(x + c[q]) : (T)0;
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    if (q < valid) {
+      acc = fused(acc, v[q], xv[q]);
+      const int rn = q + 1 < IPT ? r[q + 1] : r_next;
+      if (rn != r[q]) {  // last stored entry of row r[q]
+        if (first_row < 0) {
+          first_row = r[q];
+          first_acc = acc;
+        } else {
+          y[r[q]] = ep(acc, y, (long long)r[q]);
+        }
+        acc = 0;
+      }
+    }
+  }
+}
+
+// End of a COO tile [b0, tile_end): partial sums carried between the tile's
+// threads, the held-back first row ends, and the row left open at the tile's
+// end handed to the fix-up as (carry_row, carry_val)[tile].
+template <typename T, int NT, int MODE>
+__device__ __forceinline__ void coo_finish(long long tile_end, T acc, int first_row, T first_acc,
+                                           const Epi<T, MODE> &ep, T *__restrict__ y, long long nnz,
+                                           const int32_t *__restrict__ row, int32_t *carry_row, T *carry_val,
+                                           long long tile) {
+  T tile_open = 0;
+  const T incoming = tile_carries<T, NT>(first_row >= 0, acc, &tile_open);
+  if (first_row >= 0) y[first_row] = ep(incoming + first_acc, y, (long long)first_row);
+  if (threadIdx.x == NT - 1) {
+    // the row open at the end of the tile continues into the next tile
+    const long long kl = tile_end - 1;
+    const bool open = kl + 1 < nnz && __ldg(row + kl + 1) == __ldg(row + kl);
+    carry_row[tile] = open ? __ldg(row + kl) : -1;
+    carry_val[tile] = open ? tile_open : (T)0;
+  }
+}
+
 // K12: COO.  A CTA owns NT*CH*8 consecutive stored entries; thread t owns
 // CH*8 consecutive ones, read 8 at a time with 16-byte vector loads, and
 // accumulates them with one fused multiply-add each.  A row ends at entry k
@@ -362,47 +411,26 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
   const long long kt = b0 + (long long)threadIdx.x * (CH * IPT);
   T acc = 0, first_acc = 0;
   int first_row = -1;
+#ifdef SMAT_COO_UNROLL
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
   for (int ch = 0; ch < CH; ++ch) {
     const long long k0 = kt + ch * IPT;
     const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
     if (valid == 0) break;
     const bool full = valid == IPT;
     int r[IPT], c[IPT];
-    T v[IPT], xv[IPT];
+    T v[IPT];
     load_i32_run<IPT>(row + k0, full, valid, r, -1);
     load_i32_run<IPT>(col + k0, full, valid, c, 0);
     load_val_run<V, IPT>(val + k0, full, valid, v);
     const int r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) xv[q] = q < valid ? __ldg(x + c[q]) : (T)0;
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) {
-      if (q < valid) {
-        acc = fused(acc, v[q], xv[q]);
-        const int rn = q + 1 < IPT ? r[q + 1] : r_next;
-        if (rn != r[q]) {  // last stored entry of row r[q]
-          if (first_row < 0) {
-            first_row = r[q];
-            first_acc = acc;
-          } else {
-            y[r[q]] = ep(acc, y, (long long)r[q]);
-          }
-          acc = 0;
-        }
-      }
-    }
+    coo_chunk<T, IPT, MODE>(r, c, v, r_next, valid, x, ep, y, acc, first_row, first_acc);
   }
-  T tile_open = 0;
-  const T incoming = tile_carries<T, NT>(first_row >= 0, acc, &tile_open);
-  if (first_row >= 0) y[first_row] = ep(incoming + first_acc, y, (long long)first_row);
-  if (threadIdx.x == NT - 1) {
-    // the row open at the end of the tile continues into the next tile
-    const long long kl = min(b0 + TILE, nnz) - 1;
-    const bool open = kl + 1 < nnz && __ldg(row + kl + 1) == __ldg(row + kl);
-    carry_row[blockIdx.x] = open ? __ldg(row + kl) : -1;
-    carry_val[blockIdx.x] = open ? tile_open : (T)0;
-  }
+  coo_finish<T, NT, MODE>(min(b0 + TILE, nnz), acc, first_row, first_acc, ep, y, nnz, row, carry_row, carry_val,
+                          blockIdx.x);
 }
 
 // Fix-up: y[r] += alpha * (sum of the carries of row r), runs of equal rows
@@ -483,6 +511,19 @@ constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 #define SMAT_COO_CH 1
 #endif
 constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
+// A COO product over (row, col, val) of length nnz, then the carry fix-up.
+template <typename V, typename T, int MODE>
+cudaError_t launch_coo(const smat_s *h, const int32_t *row, const int32_t *col, const V *val, const T *x,
+                       const Epi<T, MODE> &ep, T *y, long long nnz, cudaStream_t s) {
+  const long long tiles = (nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  int32_t *crow = (int32_t *)h->carry;
+  T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+  coo_kernel<V, T, COO_NT, COO_CH, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(row, col, val, x, ep, y, nnz, crow, cval);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (tiles > 1) carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
+  return cudaGetLastError();
+}
 
 // ELL / DIA launches with a batch width U chosen at run time from 1..16/R.
 // The ELL arrays are passed in: the handle's ELL format, or HYB's ELL part.
@@ -588,16 +629,8 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
         if (e != cudaSuccess) return e;
       }
       if (h->nnz == 0) break;
-      long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-      int32_t *crow = (int32_t *)h->carry;
-      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
-      coo_kernel<V, T, COO_NT, COO_CH, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(
-          h->coo_row, h->colidx, val, x, ep, y, h->nnz, crow, cval);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      if (tiles > 1)
-        carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
-    } break;
+      return launch_coo<V, T, MODE>(h, h->coo_row, h->colidx, val, x, ep, y, h->nnz, s);
+    }
     case SMAT_V_HYB: {
       // the ELL part writes every row (y = alpha*part + beta*y), then the COO
       // tail adds alpha*(its sums): y = alpha*acc + 1*y
@@ -606,16 +639,9 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess || h->hyb_ncoo == 0) return e;
       const Epi<T, EPI_AXPBY> add{alpha, (T)1};
-      long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-      int32_t *crow = (int32_t *)h->carry;
-      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
-      coo_kernel<V, T, COO_NT, COO_CH, EPI_AXPBY><<<(unsigned)tiles, COO_NT, 0, s>>>(
-          h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y, h->hyb_ncoo, crow, cval);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      if (tiles > 1)
-        carry_fixup_kernel<T, EPI_AXPBY><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, add, y);
-    } break;
+      return launch_coo<V, T, EPI_AXPBY>(h, h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y,
+                                         h->hyb_ncoo, s);
+    }
     default:
       return cudaErrorInvalidValue;
   }

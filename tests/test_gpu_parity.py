@@ -230,3 +230,26 @@ def test_async_host_products_on_several_streams():
             assert_close_rows(ys[i].numpy(), ref, scale, TOL["f64"], f"async host product {i}")
     for M in hs:
         M.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_coo_full_and_partial_tiles(dtype):
+    # COO over many full 2048-entry tiles and a partial last one (long rows
+    # spanning tiles included): the oracle's product within the bars, and the
+    # same bits run after run
+    for A in (synth.powerlaw(60000, 1.8, 5000, 8), synth.uniform_random(20011, 7.0, 9), _long_row()):
+        M, vals64 = make(A, dtype)
+        x = vec(synth.uniform(0, 1, A.n), dtype)
+        y0 = vec(synth.uniform(1, 1, A.m), dtype)
+        ref, scale = reference(A, vals64, x, 1.25, -0.5, y0)
+        xd = torch.from_numpy(x).to(DEV)
+        outs = []
+        for _ in range(2):
+            y = torch.from_numpy(y0.copy()).to(DEV)
+            M.spmv(xd, y, 1.25, -0.5, variant=smat.SMAT_V_COO)
+            torch.cuda.synchronize()
+            outs.append(y.cpu().numpy().astype(np.float64))
+        assert_close_rows(outs[0], ref, scale, TOL[dtype], f"{A.name} {dtype} coo")
+        assert np.array_equal(outs[0], outs[1]), A.name
+        assert A.nnz % 2048 != 0   # a partial last tile is part of the case
+        M.close()
