@@ -160,9 +160,17 @@ def cpu_baseline(mats, xs, dtypes, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
+    # the serial oracle on one core: one full pass over the same products
+    t1 = time.perf_counter()
+    for A, v, x, y in prods:
+        oracle.spmv_csr_rows(A.rowptr, A.colidx, v, x, 0, A.m, 1.0, 0.0, y, 1)
+    st = time.perf_counter() - t1
+    sflops = flops
     return {"value": round(flops * passes / dt / 1e9, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{passes} full passes over the {len(prods)} products (all rows), FP64 accumulation, "
-                      f"{threads} threads, {dt:.1f} s"}
+                      f"{threads} threads, {dt:.1f} s",
+            "serial_1core": {"value": round(sflops / st / 1e9, 3), "unit": UNIT,
+                             "sample": f"one full pass over the {len(prods)} products, 1 thread, {st:.2f} s"}}
 
 
 def run_reference(args):

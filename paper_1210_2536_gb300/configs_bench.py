@@ -206,10 +206,20 @@ def cfg4g(m_fine=128):
 
         t_loop = _time(per_matrix, 20)
         t_batch = _time(lambda: B.spmv(xs, ys), 20)
+        info = B.info()
+        B.close()
+        # the selector on structures it was not trained on: regret of each
+        # level's pick against the exhaustive search's fastest variant
+        for lv, M, x, y in zip(per_level, hs, xs, ys):
+            if select == "learned":
+                M.tune("exhaustive", trial_reps=10)
+                best = _time(lambda: M.spmv(x, y), 20)
+                lv["exhaustive_pick"] = M.plan()["name"]
+                lv["exhaustive_ms"] = round(best, 4)
+                lv["regret"] = round(lv["ms"] / best - 1.0, 4)
         out[dt] = {"per_level": per_level, "per_matrix_launches_ms": round(t_loop, 4),
                    "batched_ms": round(t_batch, 4), "batched_gflops": round(2 * nnz / t_batch / 1e6, 1),
-                   "per_matrix_gflops": round(2 * nnz / t_loop / 1e6, 1), "batch_info": B.info()}
-        B.close()
+                   "per_matrix_gflops": round(2 * nnz / t_loop / 1e6, 1), "batch_info": info}
         for M in hs:
             M.close()
     return out
