@@ -147,7 +147,7 @@ typedef struct {
   uint32_t allowed;        /* bit mask over smat_variant_t (0 = all)           */
   int32_t keep_formats;    /* 1: keep every converted format after tuning      */
   int32_t sell_sigma;      /* SELL sort window in rows: a multiple of 32 in
-                              [32, 8192] (default 1024)                        */
+                              [32, 8192] (default 256)                         */
   int32_t trial_extended;  /* learned mode: also time HYB / SELL / BCSR when
                               they move at most 1.25x the matrix bytes of the
                               selector's pick (BCSR only for max_RD <= 64);
@@ -245,7 +245,7 @@ smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_ALL_VARIANTS])
 
 /* Build format `fmt` on the device now (CSR is always there).  UNSUPPORTED if
  * the format is not admissible (fill or byte cap).  SELL uses the sort window
- * of the last smat_tune (1024 before any). */
+ * of the last smat_tune (256 before any). */
 smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream);
 
 /* Layout of a built format:

@@ -671,7 +671,7 @@ void smat_tune_opts_default(smat_tune_opts_t *o) {
   o->trial_budget_ms = 2000.0;
   o->allowed = 0;
   o->keep_formats = 0;
-  o->sell_sigma = 1024;
+  o->sell_sigma = 256;
   o->trial_extended = 1;
 }
 
@@ -754,7 +754,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   if (opts_in) o = *opts_in; else { smat_tune_opts_default(&o); if (!model().loaded) o.mode = SMAT_TUNE_EXHAUSTIVE; }
   if (o.mode < SMAT_TUNE_LEARNED || o.mode > SMAT_TUNE_FIXED) return SMAT_ERR_INVALID_ARG;
   if (o.tau_den <= 0 || o.tau_num < 0 || o.fill_ratio_max <= 0) return SMAT_ERR_INVALID_ARG;
-  if (o.sell_sigma == 0) o.sell_sigma = 1024;
+  if (o.sell_sigma == 0) o.sell_sigma = 256;
   if (o.sell_sigma < 32 || o.sell_sigma > 8192 || o.sell_sigma % 32 != 0) return SMAT_ERR_INVALID_ARG;
   const double t0 = now_ms();
   if (!h->have_features || o.tau_num != h->tau_num || o.tau_den != h->tau_den ||

@@ -30,6 +30,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SELL_C = 32;
+#ifndef SMAT_SELL_U
+#define SMAT_SELL_U 8
+#endif
+constexpr int SELL_U = SMAT_SELL_U;  // slots loaded before their gathers
 
 template <int B> struct Raw;
 template <> struct Raw<8> { typedef unsigned long long T; };
@@ -441,7 +445,7 @@ cudaError_t ext_mode(const smat_s *h, int variant, typename Compute<V>::T alpha,
   if (variant == SMAT_V_SELL) {
     const long long ns = h->sell_ns;
     if (ns == 0) return cudaSuccess;
-    sell_kernel<V, MODE, 8><<<grid_for(ns * SELL_C, 256, INT_MAX), 256, 0, s>>>(
+    sell_kernel<V, MODE, SELL_U><<<grid_for(ns * SELL_C, 256, INT_MAX), 256, 0, s>>>(
         h->sell_ptr, h->sell_width, h->sell_perm, h->sell_col, (const V *)h->sell_val, x, ep, y, ns);
     return cudaGetLastError();
   }

@@ -87,7 +87,7 @@ struct smat_s {
   void *hyb_eval = nullptr, *hyb_cval = nullptr;
   bool hyb_built = false;
   // SELL-32-sigma: layout (perm, width, slice pointers) then col / val
-  int32_t sell_sigma = 1024;
+  int32_t sell_sigma = 256;
   int64_t sell_ns = 0, sell_slots = 0;
   int32_t *sell_perm = nullptr, *sell_width = nullptr, *sell_col = nullptr;
   long long *sell_ptr = nullptr;

@@ -59,8 +59,8 @@ def test_ext_conversions_bit_exact(case, dtype):
         assert np.array_equal(p["ell_col"], ecol) and _same_bytes(p["ell_val"], ev)
         assert np.array_equal(p["coo_row"], crow) and np.array_equal(p["coo_col"], ccol)
         assert _same_bytes(p["coo_val"], cv)
-    # SELL, the default window of 1024 rows
-    perm, width, sptr, scol, sval = oracle.to_sell(A.m, A.rowptr, A.colidx, vals, 1024)
+    # SELL, the default window of 256 rows
+    perm, width, sptr, scol, sval = oracle.to_sell(A.m, A.rowptr, A.colidx, vals, 256)
     ns = len(width)
     want = _expected_admissible(A, dtype, int(sptr[-1]), (esz + 4) * int(sptr[-1]) + 4 * 32 * ns + 12 * ns + 8)
     assert _convert(M, smat.SMAT_FMT_SELL) == want, name
