@@ -368,12 +368,14 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
 
 // Kernel search for ELL / DIA (the paper's per-format implementation choice,
 // Sec. 3): time the candidate batch widths once on zero vectors, keep the
-// faster.  Run when the format is built.
+// faster; for ELL then time the lane-striped row mapping at that width.  Run
+// when the format is built.
 smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   int cand[2];
   const int nc = batch_width_candidates(h, variant, cand);
   int &slot = variant == SMAT_V_DIA ? h->dia_u : h->ell_u;
-  if (nc == 1) {
+  const bool try_lane = variant == SMAT_V_ELL;
+  if (nc == 1 && !try_lane) {
     slot = cand[0];
     return SMAT_OK;
   }
@@ -389,24 +391,34 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   cudaEvent_t e0, e1;
   TRY(cudaEventCreate(&e0));
   TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_u = cand[0];
-  for (int c = 0; c < nc; ++c) {
-    for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, cand[c], a, x.p, b, y.p, s));
+  struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
+  auto time_it = [&](int u, int lane, float *med) -> smat_status_t {
+    for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
     float ms[5];
     for (int r = 0; r < 5; ++r) {
       TRY(cudaEventRecord(e0, s));
-      TRY(launch_spmv_width(h, variant, cand[c], a, x.p, b, y.p, s));
+      TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
       TRY(cudaEventRecord(e1, s));
       TRY(cudaEventSynchronize(e1));
       TRY(cudaEventElapsedTime(&ms[r], e0, e1));
     }
     std::sort(ms, ms + 5);
-    if (ms[2] < best) { best = ms[2]; best_u = cand[c]; }
+    *med = ms[2];
+    return SMAT_OK;
+  };
+  float best = 1e30f;
+  int best_u = cand[0];
+  for (int c = 0; c < nc; ++c) {
+    float med;
+    TRYS(time_it(cand[c], 0, &med));
+    if (med < best) { best = med; best_u = cand[c]; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   slot = best_u;
+  if (try_lane) {
+    float med;
+    TRYS(time_it(best_u, 1, &med));
+    h->ell_lane = med < best ? 1 : 0;
+  }
   return SMAT_OK;
 }
 
@@ -422,7 +434,7 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     TRY(dev_alloc(&c, (size_t)(K * h->P) * 4));
     cudaError_t e = dev_alloc(&v, (size_t)(K * h->P) * h->esz);
     if (e != cudaSuccess) { dev_free(c); return st_of(e); }
-    h->ell_col = (int32_t *)c; h->ell_val = v; h->ell_K = K; h->ell_u = 0;
+    h->ell_col = (int32_t *)c; h->ell_val = v; h->ell_K = K; h->ell_u = 0; h->ell_lane = 0;
     TRY(launch_to_ell(h, K, h->ell_col, h->ell_val, s));
     return measure_batch_width(h, SMAT_V_ELL, s);
   }

@@ -27,7 +27,7 @@ namespace {
 enum : int { KIND_CSR = 0, KIND_ELL = 1, KIND_DIA = 2, KIND_SELL = 3, NKIND = 4 };
 
 struct BatchMat {
-  int kind, W, nd, epi;
+  int kind, W, nd, epi, lane;
   long long m, n, K, P;
   const int32_t *rowptr, *colidx;
   const void *val;
@@ -96,12 +96,26 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
   typedef typename Compute<V>::T T;
   constexpr int R = 16 / (int)sizeof(V);
   const Epi<T, MODE> ep{(T)M.alpha, (T)M.beta};
+  // tiles of ELL / DIA members start at multiples of BNT*R rows, so the
+  // lane-striped mappings (32*R rows per warp) stay inside their tile
   if (KIND == KIND_ELL) {
-    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-      ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
+    if (M.lane) {
+      for (long long b = tl.row0 + (long long)(threadIdx.x >> 5) * 32 * R; b < tl.row1; b += (long long)BNT * R)
+        ell_lane_group<V, R, MODE, 16 / R>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, b,
+                                           threadIdx.x & 31);
+    } else {
+      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+        ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
+    }
   } else if (KIND == KIND_DIA) {
-    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-      dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
+    if (sizeof(V) == 8) {  // FP64: lane-striped rows, as the single-matrix DIA kernel
+      for (long long b = tl.row0 + (long long)(threadIdx.x >> 5) * 32 * R; b < tl.row1; b += (long long)BNT * R)
+        dia_lane_group<V, R, MODE, 16 / R>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m,
+                                           M.n, b, threadIdx.x & 31);
+    } else {
+      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+        dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
+    }
   } else if (KIND == KIND_SELL) {  // row0 / row1 are slice indices; a warp per slice
     for (long long sl = tl.row0 + threadIdx.x / 32; sl < tl.row1; sl += BNT / 32)
       sell_slice<V, MODE, 8>(M.sptr, M.swidth, M.sperm, M.scol, (const V *)M.sval, (const T *)M.x, ep, (T *)M.y, sl,
@@ -396,7 +410,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
     BatchMat &M = b->mats[(size_t)i];
     M.m = h->m; M.n = h->n; M.P = h->P;
     if (h->variant == SMAT_V_ELL && h->ell_val) {
-      M.kind = KIND_ELL; M.ecol = h->ell_col; M.eval = h->ell_val; M.K = h->ell_K;
+      M.kind = KIND_ELL; M.ecol = h->ell_col; M.eval = h->ell_val; M.K = h->ell_K; M.lane = h->ell_lane;
     } else if (h->variant == SMAT_V_DIA && h->dia_val) {
       M.kind = KIND_DIA; M.doff = h->dia_off; M.dval = h->dia_val; M.nd = (int)h->dia_nd;
     } else if (h->variant == SMAT_V_SELL && h->sell_val) {

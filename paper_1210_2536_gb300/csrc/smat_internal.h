@@ -70,6 +70,7 @@ struct smat_s {
   // ELL
   int64_t ell_K = 0;
   int ell_u = 0, dia_u = 0;  // measured batch widths (0: not measured yet)
+  int ell_lane = 0;          // measured ELL row mapping: 0 consecutive rows per thread, 1 lane-striped
   int32_t *ell_col = nullptr;
   void *ell_val = nullptr;
   // DIA
@@ -163,8 +164,10 @@ size_t carry_bytes_needed(const smat_s *h, int variant);
 int spmv_launch_count(const smat_s *h, int variant);
 // Candidate batch widths of an ELL / DIA product (returns how many: 1 or 2).
 int batch_width_candidates(const smat_s *h, int variant, int out[2]);
-// ELL / DIA product with an explicit batch width (for measuring it).
-cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, const void *alpha, const void *x,
+// ELL / DIA product with an explicit batch width and (ELL) row mapping
+// (lane: -1 the handle's, 0 consecutive rows per thread, 1 lane-striped), for
+// measuring them.
+cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, const void *alpha, const void *x,
                               const void *beta, void *y, cudaStream_t s);
 // SpMV through one variant; alpha/beta are host scalars of the compute type.
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,

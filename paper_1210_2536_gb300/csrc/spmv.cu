@@ -465,14 +465,19 @@ __global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long co
 // padding (column -1) gathers x[0] and is dropped by a select, so no load
 // sits behind a branch.
 // ---------------------------------------------------------------------------
-template <typename V, int R, int MODE, int U>
+template <typename V, int R, int MODE, int U, bool LANE>
 __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
                                                   long long P, long long K,
                                                   const typename Compute<V>::T *__restrict__ x,
                                                   Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m) {
-  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) ell_group<V, R, MODE, U>(ecol, eval, P, K, x, ep, y, m, i0);
+  if (LANE) {  // lane-striped rows (a per-handle measured choice)
+    const long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32LL * R);
+    if (base < m) ell_lane_group<V, R, MODE, U>(ecol, eval, P, K, x, ep, y, m, base, threadIdx.x & 31);
+  } else {
+    const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
+    if (i0 < m) ell_group<V, R, MODE, U>(ecol, eval, P, K, x, ep, y, m, i0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -492,8 +497,13 @@ __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ of
   extern __shared__ int32_t s_off[];
   for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
   __syncthreads();
-  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
-  if (i0 < m) dia_group<V, R, MODE, U>(s_off, nd, dval, P, x, ep, y, m, n, i0);
+  if (sizeof(V) == 8) {  // FP64: lane-striped rows (measured faster on every matrix tried)
+    const long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32LL * R);
+    if (base < m) dia_lane_group<V, R, MODE, U>(s_off, nd, dval, P, x, ep, y, m, n, base, threadIdx.x & 31);
+  } else {
+    const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * R;
+    if (i0 < m) dia_group<V, R, MODE, U>(s_off, nd, dval, P, x, ep, y, m, n, i0);
+  }
 }
 
 int grid_for(long long work, int block, int max_blocks) {
@@ -534,12 +544,15 @@ struct EllPart {
 };
 
 template <typename V, int MODE, int U>
-void launch_ell_u(const smat_s *h, const EllPart &e, const typename Compute<V>::T *x,
+void launch_ell_u(const smat_s *h, const EllPart &e, bool lane, const typename Compute<V>::T *x,
                   const Epi<typename Compute<V>::T, MODE> &ep, typename Compute<V>::T *y, cudaStream_t s) {
   constexpr int R = 16 / (int)sizeof(V);
   const long long m = h->m;
-  ell_kernel<V, R, MODE, U><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, 0, s>>>(
-      e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
+  const int g = grid_for((m + R - 1) / R, 256, 1 << 30);
+  if (lane)
+    ell_kernel<V, R, MODE, U, true><<<g, 256, 0, s>>>(e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
+  else
+    ell_kernel<V, R, MODE, U, false><<<g, 256, 0, s>>>(e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
 }
 
 template <typename V, int MODE, int U>
@@ -553,16 +566,18 @@ void launch_dia_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<ty
 
 template <typename V, int MODE, bool DIA>
 void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<typename Compute<V>::T, MODE> &ep,
-                    typename Compute<V>::T *y, cudaStream_t s, int u_req, const EllPart *part = nullptr) {
+                    typename Compute<V>::T *y, cudaStream_t s, int u_req, int lane_req,
+                    const EllPart *part = nullptr) {
   constexpr int UMAX = 16 / (16 / (int)sizeof(V));  // 16 / R
   const EllPart e = part ? *part : EllPart{h->ell_col, h->ell_val, h->ell_K};
+  const bool lane = lane_req >= 0 ? lane_req != 0 : (part ? false : h->ell_lane != 0);
   const int u_tuned = part ? 0 : (DIA ? h->dia_u : h->ell_u);
   const int u = u_req > 0 ? u_req : (u_tuned > 0 ? u_tuned : batch_width(DIA ? h->dia_nd : e.K, UMAX));
 #define SMAT_UCASE(k)                                                      \
   case k:                                                                  \
     if constexpr (k <= UMAX) {                                             \
       if (DIA) launch_dia_u<V, MODE, k>(h, x, ep, y, s);                   \
-      else launch_ell_u<V, MODE, k>(h, e, x, ep, y, s);                    \
+      else launch_ell_u<V, MODE, k>(h, e, lane, x, ep, y, s);              \
     }                                                                      \
     break;
   switch (u) {
@@ -570,7 +585,7 @@ void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<
     default:
       if constexpr (UMAX >= 8) {
         if (DIA) launch_dia_u<V, MODE, 8>(h, x, ep, y, s);
-        else launch_ell_u<V, MODE, 8>(h, e, x, ep, y, s);
+        else launch_ell_u<V, MODE, 8>(h, e, lane, x, ep, y, s);
       }
       break;
   }
@@ -579,7 +594,7 @@ void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<
 
 template <typename V, int MODE>
 cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha, const void *x_p,
-                      typename Compute<V>::T beta, void *y_p, cudaStream_t s, int u_req) {
+                      typename Compute<V>::T beta, void *y_p, cudaStream_t s, int u_req, int lane_req) {
   typedef typename Compute<V>::T T;
   const Epi<T, MODE> ep{alpha, beta};
   const T *x = (const T *)x_p;
@@ -616,10 +631,10 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
         carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
     } break;
     case SMAT_V_ELL:
-      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, u_req);
+      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, u_req, lane_req);
       break;
     case SMAT_V_DIA:
-      launch_ell_dia<V, MODE, true>(h, x, ep, y, s, u_req);
+      launch_ell_dia<V, MODE, true>(h, x, ep, y, s, u_req, lane_req);
       break;
     case SMAT_V_COO: {
       if (h->coo_nempty > 0) {
@@ -635,7 +650,7 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       // the ELL part writes every row (y = alpha*part + beta*y), then the COO
       // tail adds alpha*(its sums): y = alpha*acc + 1*y
       const EllPart part{h->hyb_ecol, h->hyb_eval, h->hyb_K};
-      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, 0, &part);
+      launch_ell_dia<V, MODE, false>(h, x, ep, y, s, 0, 0, &part);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess || h->hyb_ncoo == 0) return e;
       const Epi<T, EPI_AXPBY> add{alpha, (T)1};
@@ -650,14 +665,14 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
 
 template <typename V>
 cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p, const void *beta_p,
-                       void *y_p, cudaStream_t s, int u_req) {
+                       void *y_p, cudaStream_t s, int u_req, int lane_req) {
   typedef typename Compute<V>::T T;
   const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
   if (h->m == 0) return cudaSuccess;
   switch (epi_mode((double)alpha, (double)beta)) {
-    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s, u_req);
-    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s, u_req);
-    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s, u_req);
+    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
+    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
+    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
   }
 }
 
@@ -711,9 +726,9 @@ cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const v
     variant = SMAT_V_CSR_SCALAR;
   if (variant == SMAT_V_SELL || variant == SMAT_V_BCSR) return launch_spmv_ext(h, variant, alpha, x, beta, y, s);
   switch (h->dtype) {
-    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, 0);
-    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, 0);
-    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, 0);
+    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, 0, -1);
+    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, 0, -1);
+    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, 0, -1);
   }
 }
 
@@ -725,12 +740,12 @@ int batch_width_candidates(const smat_s *h, int variant, int out[2]) {
   return out[1] != out[0] ? 2 : 1;
 }
 
-cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, const void *alpha, const void *x, const void *beta,
-                              void *y, cudaStream_t s) {
+cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, const void *alpha, const void *x,
+                              const void *beta, void *y, cudaStream_t s) {
   switch (h->dtype) {
-    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, u);
-    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, u);
-    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, u);
+    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, u, lane);
+    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, u, lane);
+    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, u, lane);
   }
 }
 

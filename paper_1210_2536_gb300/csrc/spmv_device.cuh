@@ -207,6 +207,50 @@ __device__ __forceinline__ void ell_group(const int32_t *__restrict__ ecol, cons
   write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
 
+// ELL with lane-striped rows: lane l of a warp takes rows base + l + 32 r
+// (r < R), so each slot's column and value loads are contiguous 32-element
+// warp accesses.
+template <typename V, int R, int MODE, int U>
+__device__ __forceinline__ void ell_lane_group(const int32_t *__restrict__ ecol, const V *__restrict__ eval,
+                                               long long P, long long K, const typename Compute<V>::T *__restrict__ x,
+                                               const Epi<typename Compute<V>::T, MODE> &ep,
+                                               typename Compute<V>::T *__restrict__ y, long long m, long long base,
+                                               int lane) {
+  typedef typename Compute<V>::T T;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+  for (long long q = 0; q < K; q += U) {
+    T v[U][R], xv[U][R];
+    int c[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long i = base + lane + 32 * r;
+        const bool on = q + u < K && i < P;
+        c[u][r] = on ? ld_idx(ecol + (q + u) * P + i) : -1;
+        v[u][r] = on ? (T)ld_val(eval + (q + u) * P + i) : (T)0;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) xv[u][r] = c[u][r] >= 0 ? __ldg(x + c[u][r]) : (T)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q + u < K) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (c[u][r] >= 0) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = base + lane + 32 * r;
+    if (i < m) y[i] = ep(acc[r], y, i);
+  }
+}
+
 // One thread's R consecutive rows of a DIA product; `off` holds the nd
 // ascending diagonal offsets (shared or global memory), U diagonals per batch
 // (chosen on the host as for ELL).  Fill zeros are
@@ -253,6 +297,48 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
   write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
 
+
+// DIA with lane-striped rows: lane l of a warp takes rows base + l + 32 r
+// (r < R), so every value load and every x load of a diagonal is one
+// contiguous 32-element warp access.
+template <typename V, int R, int MODE, int U>
+__device__ __forceinline__ void dia_lane_group(const int32_t *off, int nd, const V *__restrict__ dval, long long P,
+                                               const typename Compute<V>::T *__restrict__ x,
+                                               const Epi<typename Compute<V>::T, MODE> &ep,
+                                               typename Compute<V>::T *__restrict__ y, long long m, long long n,
+                                               long long base, int lane) {
+  typedef typename Compute<V>::T T;
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+  for (int t = 0; t < nd; t += U) {
+    T v[U][R], xv[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool live = t + u < nd;
+      const long long o = live ? off[t + u] : 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long i = base + lane + 32 * r;
+        const long long j = i + o;
+        const bool in = live && i < m && j >= 0 && j < n;
+        v[u][r] = (live && i < P) ? (T)ld_val(dval + (long long)(t + u) * P + i) : (T)0;
+        xv[u][r] = in ? __ldg(x + j) : (T)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (t + u < nd) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = base + lane + 32 * r;
+    if (i < m) y[i] = ep(acc[r], y, i);
+  }
+}
 
 // One SELL-32 slice: lane l computes the row at sorted position 32*sl + l over
 // the slice's `w` slots, U slots loaded before their gathers.  w is uniform
