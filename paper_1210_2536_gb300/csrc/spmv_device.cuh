@@ -268,35 +268,35 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
   for (int r = 0; r < R; ++r) acc[r] = 0;
   for (int t = 0; t < nd; t += U) {
     T v[U][R], xv[U][R];
-    bool in[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool live = t + u < nd;
-      const long long o = live ? off[t + u] : 0;
+      const long long j0 = i0 + (live ? off[t + u] : 0);
       if (live) {
         load_vals<V, R>(dval + (long long)(t + u) * P + i0, v[u]);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[u][r] = 0;
       }
+      if (live && j0 >= 0 && j0 + R <= n) {  // the whole window inside x: no per-row checks
+        const T *xp = x + j0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const long long j = i0 + r + o;
-        in[u][r] = live && j >= 0 && j < n;
-        xv[u][r] = in[u][r] ? __ldg(x + j) : (T)0;
+        for (int r = 0; r < R; ++r) xv[u][r] = __ldg(xp + r);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) xv[u][r] = (live && j0 + r >= 0 && j0 + r < n) ? __ldg(x + j0 + r) : (T)0;
       }
     }
+    // out-of-range positions hold a stored +0 and read x as 0: no predicate
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (t + u < nd) {  // uniform across the warp: dead slots issue no FP work
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (in[u][r]) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
+        for (int r = 0; r < R; ++r) acc[r] = fused(acc[r], v[u][r], xv[u][r]);
       }
   }
   write_rows<T, R, MODE>(y, i0, m, acc, ep);
 }
-
 
 // DIA with lane-striped rows: lane l of a warp takes rows base + l + 32 r
 // (r < R), so every value load and every x load of a diagonal is one
