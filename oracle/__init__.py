@@ -12,6 +12,7 @@ Every function restates a definition of the paper:
   to_ell/to_dia/to_coo  the four basic storage formats (Sec. 2.1)
   to_hyb/sell_layout/to_sell/to_bcsr  further GPU formats left to future work
                   in Sec. 8 (HYB, SELL-C-sigma, BCSR; published definitions)
+  split_rows      rows split by length: long rows in chunks, short rows as COO
   mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
 Readings taken where the paper is silent are listed in ``oracle.c``.
 """
@@ -78,6 +79,7 @@ def lib():
         L.oracle_to_bcsr.restype = i64
         L.oracle_bcsr_choose.argtypes = [i64, i64, vp, vp, i64, vp]
         L.oracle_bcsr_choose.restype = i64
+        L.oracle_split.argtypes = [i64, vp, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_round_bf16.argtypes = [i64, vp, vp]
         L.oracle_bf16_to_double.argtypes = [i64, vp, vp]
         L.oracle_mlp_param_count.restype = i64
@@ -303,6 +305,24 @@ def bcsr_choose(m, n, rowptr, colidx, elem_size):
     nb = np.zeros(1, dtype=np.int64)
     b = int(lib().oracle_bcsr_choose(m, n, prp, pci, elem_size, nb.ctypes.data))
     return b, int(nb[0])
+
+
+def split_rows(m, rowptr, colidx, val, L=256, CK=4096):
+    """SPLIT layout: long rows (>= L entries) in chunks of <= CK entries, a COO
+    of the short rows' entries, the empty rows.  Returns a dict of arrays."""
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colidx, np.int32)
+    v = np.ascontiguousarray(val)
+    cnt = np.zeros(4, dtype=np.int64)
+    lib().oracle_split(m, prp, pci, v.ctypes.data, v.itemsize, L, CK, None, None, None, None, None, None, None, None,
+                       cnt.ctypes.data)
+    nl, nc, ns, ne = (int(c) for c in cnt)
+    out = {"lrows": np.empty(nl, np.int32), "crow": np.empty(nc, np.int32), "cstart": np.empty(nc, np.int32),
+           "cend": np.empty(nc, np.int32), "srow": np.empty(ns, np.int32), "scol": np.empty(ns, np.int32),
+           "sval": np.empty(ns, v.dtype), "empty": np.empty(ne, np.int32)}
+    lib().oracle_split(m, prp, pci, v.ctypes.data, v.itemsize, L, CK, *(out[k].ctypes.data for k in
+                       ("lrows", "crow", "cstart", "cend", "srow", "scol", "sval", "empty")), cnt.ctypes.data)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -502,6 +502,48 @@ int64_t oracle_bcsr_choose(int64_t m, int64_t n, const int32_t *rowptr, const in
   return best_b;
 }
 
+/* SPLIT: rows split by length.  Rows with at least L stored entries ("long")
+ * are listed in ascending order and cut into chunks of at most CK consecutive
+ * entries (a long row's chunks in order; chunk c covers entries
+ * [cstart[c], cend[c]) of row crow[c]); every other non-empty row ("short")
+ * goes, in CSR order, to a COO of its entries; empty rows are listed.  Each
+ * output array may be NULL to count only.  Writes the counts to cnt[4] =
+ * {long rows, chunks, short entries, empty rows}. */
+void oracle_split(int64_t m, const int32_t *rowptr, const int32_t *colidx, const void *val, int64_t elem_size,
+                  int64_t L, int64_t CK, int32_t *lrows, int32_t *crow, int32_t *cstart, int32_t *cend,
+                  int32_t *srow, int32_t *scol, void *sval, int32_t *empty, int64_t *cnt) {
+  const unsigned char *iv = (const unsigned char *)val;
+  int64_t nl = 0, nc = 0, ns = 0, ne = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t s0 = rowptr[i], e0 = rowptr[i + 1], rd = e0 - s0;
+    if (rd == 0) {
+      if (empty) empty[ne] = (int32_t)i;
+      ++ne;
+    } else if (rd >= L) {
+      if (lrows) lrows[nl] = (int32_t)i;
+      ++nl;
+      for (int64_t k = s0; k < e0; k += CK) {
+        if (crow) {
+          crow[nc] = (int32_t)i;
+          cstart[nc] = (int32_t)k;
+          cend[nc] = (int32_t)(k + CK < e0 ? k + CK : e0);
+        }
+        ++nc;
+      }
+    } else {
+      for (int64_t k = s0; k < e0; ++k) {
+        if (srow) {
+          srow[ns] = (int32_t)i;
+          scol[ns] = colidx[k];
+          memcpy((unsigned char *)sval + ns * elem_size, iv + k * elem_size, (size_t)elem_size);
+        }
+        ++ns;
+      }
+    }
+  }
+  cnt[0] = nl; cnt[1] = nc; cnt[2] = ns; cnt[3] = ne;
+}
+
 /* ------------------------------------------------------------------------ */
 /* BF16 storage: round-to-nearest-even of an FP64 value to the bfloat16 grid */
 /* (1 sign, 8 exponent, 7 fraction bits; IEEE 754 rounding), written from    */

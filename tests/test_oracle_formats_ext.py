@@ -1,7 +1,8 @@
 """Pins of the oracle's further GPU formats (left to future work in Sec. 8):
-HYB (Bell & Garland's ELL + COO split), SELL-C-sigma (Kreutzer et al.) and
-BCSR with b x b blocks.  Closed forms are derived by hand in the comments;
-the rest is brute force on small dense matrices."""
+HYB (Bell & Garland's ELL + COO split), SELL-C-sigma (Kreutzer et al.), BCSR
+with b x b blocks, and SPLIT (long rows in chunks, short rows as COO).  Closed
+forms are derived by hand in the comments; the rest is brute force on small
+dense matrices."""
 import numpy as np
 import pytest
 
@@ -197,3 +198,43 @@ def test_bcsr_choose_is_the_byte_minimum():
             best = min(cost.values())
             assert cost[b] == best and b == min(c for c in cost if cost[c] == best)
             assert nb == int(_bcsr_blocks_brute(mask, b).sum())
+
+
+# ---------------------------------------------------------------------------
+# SPLIT (long rows in chunks + a COO of the short rows)
+# ---------------------------------------------------------------------------
+
+def test_split_closed_form():
+    # lengths 0, 3, 10, 0, 1, 7 with L = 4, CK = 4: long rows 2 (10 entries ->
+    # chunks of 4, 4, 2) and 5 (7 -> 4, 3); short rows 1 and 4 (3 + 1 entries);
+    # empty rows 0 and 3
+    B = _from_lengths([0, 3, 10, 0, 1, 7])
+    s = oracle.split_rows(B.m, B.rowptr, B.colidx, B.val, L=4, CK=4)
+    assert list(s["lrows"]) == [2, 5] and list(s["empty"]) == [0, 3]
+    assert list(s["crow"]) == [2, 2, 2, 5, 5]
+    rp = B.rowptr
+    assert list(s["cstart"]) == [rp[2], rp[2] + 4, rp[2] + 8, rp[5], rp[5] + 4]
+    assert list(s["cend"]) == [rp[2] + 4, rp[2] + 8, rp[3], rp[5] + 4, rp[6]]
+    assert list(s["srow"]) == [1, 1, 1, 4] and list(s["scol"]) == [0, 1, 2, 0]
+
+
+@pytest.mark.parametrize("mk", MAKERS)
+@pytest.mark.parametrize("L", [1, 3, 16, 10 ** 6])
+def test_split_reconstructs_dense(mk, L):
+    A = mk()
+    s = oracle.split_rows(A.m, A.rowptr, A.colidx, A.val, L=L, CK=5)
+    rl = np.diff(A.rowptr)
+    assert list(s["lrows"]) == list(np.nonzero(rl >= L)[0]) and list(s["empty"]) == list(np.nonzero(rl == 0)[0])
+    d = np.zeros((A.m, A.n))
+    for r, a, b in zip(s["crow"], s["cstart"], s["cend"]):
+        assert 0 < b - a <= 5 and A.rowptr[r] <= a < b <= A.rowptr[r + 1]
+        d[r, A.colidx[a:b]] += A.val[a:b]
+    for r, c, v in zip(s["srow"], s["scol"], s["sval"]):
+        assert rl[r] < L
+        d[r, c] += v
+    assert np.array_equal(d, A.todense())
+    # chunks tile each long row exactly, in order
+    for r in s["lrows"]:
+        ch = [(a, b) for rr, a, b in zip(s["crow"], s["cstart"], s["cend"]) if rr == r]
+        assert ch[0][0] == A.rowptr[r] and ch[-1][1] == A.rowptr[r + 1]
+        assert all(ch[k][1] == ch[k + 1][0] for k in range(len(ch) - 1))
