@@ -59,13 +59,14 @@ typedef enum {
 
 typedef enum { SMAT_F64 = 0, SMAT_F32 = 1, SMAT_BF16 = 2 } smat_dtype_t;
 
-/* Storage formats: the four basic formats of Sec. 2.1, then three GPU formats
- * of the kind Sec. 8 leaves to future work (HYB: Bell & Garland's ELL + COO
+/* Storage formats: the four basic formats of Sec. 2.1, then GPU formats of
+ * the kind Sec. 8 leaves to future work (HYB: Bell & Garland's ELL + COO
  * split; SELL: Kreutzer et al.'s SELL-C-sigma with C = 32; BCSR: b x b blocks,
- * b in {2, 4, 8}). */
+ * b in {2, 4, 8}; SPLIT: rows of at least 1024 entries in chunks of at most
+ * 4096, each chunk summed by one CTA, the other rows as a COO). */
 typedef enum {
   SMAT_FMT_CSR = 0, SMAT_FMT_ELL = 1, SMAT_FMT_DIA = 2, SMAT_FMT_COO = 3,
-  SMAT_FMT_HYB = 4, SMAT_FMT_SELL = 5, SMAT_FMT_BCSR = 6
+  SMAT_FMT_HYB = 4, SMAT_FMT_SELL = 5, SMAT_FMT_BCSR = 6, SMAT_FMT_SPLIT = 7
 } smat_format_t;
 
 /* Kernel variants the selector chooses among (the paper's kernel library maps
@@ -92,7 +93,8 @@ typedef enum {
   SMAT_V_HYB = 9,        /* ELL part + COO tail                               */
   SMAT_V_SELL = 10,      /* SELL-32-sigma, a warp per slice                   */
   SMAT_V_BCSR = 11,      /* b x b blocks, b lanes per block row               */
-  SMAT_NUM_ALL_VARIANTS = 12
+  SMAT_V_SPLIT = 12,     /* long rows in CTA chunks + COO of the short rows   */
+  SMAT_NUM_ALL_VARIANTS = 13
 } smat_variant_t;
 
 /* Feature parameters (Sec. 4, Table "Feature parameters of a sparse matrix").
@@ -107,10 +109,11 @@ typedef enum {
  *       degrees k >= 1 with h[k] > 0 (P(k) ~ k^-R); r_valid = 0 and r = 0 when
  *       fewer than two degrees occur.
  * Ratios whose denominator is 0 are 0.
- * `admissible` bits 9-11 (HYB, SELL, BCSR) are set once the format's layout
- * has been measured (by smat_tune, smat_convert or a product through it):
- * each needs its stored slots (fill included) <= fill_ratio_max * NNZ and its
- * bytes <= bytes_cap * CSR bytes; HYB also an ELL width K >= 1. */
+ * `admissible` bits 9-12 (HYB, SELL, BCSR, SPLIT) are set once the format's
+ * layout has been measured (by smat_tune, smat_convert or a product through
+ * it): each needs its stored slots (fill included) <= fill_ratio_max * NNZ
+ * and its bytes <= bytes_cap * CSR bytes; HYB also an ELL width K >= 1, SPLIT
+ * at least one row of 1024 or more entries. */
 typedef struct {
   int64_t m, n, nnz;
   int64_t max_rd, min_rd, empty_rows;
@@ -148,7 +151,7 @@ typedef struct {
   int32_t keep_formats;    /* 1: keep every converted format after tuning      */
   int32_t sell_sigma;      /* SELL sort window in rows: a multiple of 32 in
                               [32, 8192] (default 256)                         */
-  int32_t trial_extended;  /* learned mode: also time HYB / SELL / BCSR when
+  int32_t trial_extended;  /* learned mode: also time HYB / SELL / BCSR / SPLIT when
                               they move at most 1.25x the matrix bytes of the
                               selector's pick (BCSR only for max_RD <= 64);
                               default 1                                       */
@@ -260,6 +263,9 @@ smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream);
  *        of position 32s + l at sum_{t<s} 32*width[t] + 32j + l
  *   BCSR: dims = {b, Nblocks}: browptr int32[ceil(M/b)+1], bcol int32[Nblocks],
  *        val[Nblocks*b*b] row-major per block
+ *   SPLIT: dims = {Nchunks, Nshort}: per chunk (row, first entry, end entry)
+ *        int32[Nchunks] each, chunks of one row consecutive and in order; the
+ *        short rows' COO row[Nshort], col[Nshort], val[Nshort] in CSR order
  * P is M rounded up to a multiple of 32; padding holds column -1 / value +0. */
 smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[2]);
 
@@ -268,7 +274,9 @@ smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[
  *   COO: idx <- row (val unused);
  *   HYB: idx <- ELL col, COO row, COO col; val <- ELL val, COO val;
  *   SELL: idx <- perm, width, col; val <- val;
- *   BCSR: idx <- browptr, bcol; val <- val.
+ *   BCSR: idx <- browptr, bcol; val <- val;
+ *   SPLIT: idx <- chunk rows, chunk starts, chunk ends, COO row, COO col;
+ *          val <- COO val.
  * Arrays are concatenated in the order listed.  Sizes as in smat_format_dims. */
 smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *idx, void *val);
 

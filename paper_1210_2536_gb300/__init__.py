@@ -23,15 +23,16 @@ LIB_PATH = os.path.join(_PKG, "libsmat.so")
 SMAT_OK, SMAT_ERR_INVALID_ARG, SMAT_ERR_INVALID_CSR, SMAT_ERR_ALLOC, SMAT_ERR_CUDA, \
     SMAT_ERR_UNSUPPORTED, SMAT_ERR_MODEL, SMAT_ERR_NOT_CONVERGED = range(8)
 SMAT_F64, SMAT_F32, SMAT_BF16 = range(3)
-SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO, SMAT_FMT_HYB, SMAT_FMT_SELL, SMAT_FMT_BCSR = range(7)
+(SMAT_FMT_CSR, SMAT_FMT_ELL, SMAT_FMT_DIA, SMAT_FMT_COO, SMAT_FMT_HYB, SMAT_FMT_SELL, SMAT_FMT_BCSR,
+ SMAT_FMT_SPLIT) = range(8)
 (SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32, SMAT_V_CSR_MERGE, SMAT_V_ELL,
  SMAT_V_DIA, SMAT_V_COO) = range(8)
 SMAT_NUM_VARIANTS = 8
 SMAT_V_CSR_SCALAR_EXACT = 8
-SMAT_V_HYB, SMAT_V_SELL, SMAT_V_BCSR = 9, 10, 11
-SMAT_NUM_ALL_VARIANTS = 12
+SMAT_V_HYB, SMAT_V_SELL, SMAT_V_BCSR, SMAT_V_SPLIT = 9, 10, 11, 12
+SMAT_NUM_ALL_VARIANTS = 13
 VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo",
-                 "csr_scalar_exact", "hyb", "sell", "bcsr"]
+                 "csr_scalar_exact", "hyb", "sell", "bcsr", "split"]
 SMAT_TUNE_LEARNED, SMAT_TUNE_EXHAUSTIVE, SMAT_TUNE_RULES, SMAT_TUNE_FIXED = range(4)
 SMAT_MLP_PARAMS = 5512
 DTYPES = {"f64": SMAT_F64, "f32": SMAT_F32, "bf16": SMAT_BF16}
@@ -527,8 +528,9 @@ class SpMatrix:
         return y
 
     def features(self) -> dict:
-        """Feature parameters, plus the sizes of the built HYB / SELL / BCSR
-        formats (hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b, bcsr_nb)."""
+        """Feature parameters, plus the sizes of the built HYB / SELL / BCSR /
+        SPLIT formats (hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b, bcsr_nb,
+        split_nc, split_ns)."""
         f = smat_get_features(self.h)
         out = {n: getattr(f, n) for n, _ in smat_features_t._fields_}
         out.update(self.layout())
@@ -537,7 +539,7 @@ class SpMatrix:
     def layout(self) -> dict:
         out = {}
         for fmt, keys in ((SMAT_FMT_HYB, ("hyb_K", "hyb_ncoo")), (SMAT_FMT_SELL, ("sell_ns", "sell_slots")),
-                          (SMAT_FMT_BCSR, ("bcsr_b", "bcsr_nb"))):
+                          (SMAT_FMT_BCSR, ("bcsr_b", "bcsr_nb")), (SMAT_FMT_SPLIT, ("split_nc", "split_ns"))):
             st, d0, d1 = smat_format_dims(self.h, fmt)
             if st == SMAT_OK:
                 out[keys[0]], out[keys[1]] = d0, d1
@@ -577,6 +579,8 @@ class SpMatrix:
         elif fmt == SMAT_FMT_BCSR:
             mb = (self.m + d0 - 1) // d0
             idx, val = np.empty(mb + 1 + d1, np.int32), np.empty(d1 * d0 * d0, vdt)
+        elif fmt == SMAT_FMT_SPLIT:
+            idx, val = np.empty(3 * d0 + 2 * d1, np.int32), np.empty(d1, vdt)
         else:
             idx, val = np.empty(d0, np.int32), None
         _check(smat_export_format(self.h, fmt, idx.ctypes.data, None if val is None else val.ctypes.data),
@@ -584,7 +588,7 @@ class SpMatrix:
         return idx, val, d0, d1
 
     def export_parts(self, fmt) -> dict:
-        """A built HYB / SELL / BCSR format split into its named arrays."""
+        """A built HYB / SELL / BCSR / SPLIT format split into its named arrays."""
         idx, val, d0, d1 = self.export(fmt)
         if fmt == SMAT_FMT_HYB:
             ne = d0 * ((self.m + 31) // 32 * 32)
@@ -595,6 +599,9 @@ class SpMatrix:
         if fmt == SMAT_FMT_BCSR:
             mb = (self.m + d0 - 1) // d0
             return {"b": d0, "browptr": idx[:mb + 1], "bcol": idx[mb + 1:], "val": val}
+        if fmt == SMAT_FMT_SPLIT:
+            return {"crow": idx[:d0], "cstart": idx[d0:2 * d0], "cend": idx[2 * d0:3 * d0],
+                    "srow": idx[3 * d0:3 * d0 + d1], "scol": idx[3 * d0 + d1:], "sval": val}
         raise ValueError(fmt)
 
 

@@ -75,7 +75,7 @@ def cfg1():
     scale = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(A.val), np.abs(x.cpu().numpy()))
     lat = {}
     err = {}
-    for v in list(range(8)) + [smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR]:
+    for v in list(range(8)) + [smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR, smat.SMAT_V_SPLIT]:
         if v < 8 and not (f["admissible"] >> v) & 1:
             continue
         y = torch.empty(A.m, dtype=torch.float64, device=dev)

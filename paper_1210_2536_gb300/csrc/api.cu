@@ -81,6 +81,7 @@ int variant_format(int v) {
   if (v == SMAT_V_HYB) return SMAT_FMT_HYB;
   if (v == SMAT_V_SELL) return SMAT_FMT_SELL;
   if (v == SMAT_V_BCSR) return SMAT_FMT_BCSR;
+  if (v == SMAT_V_SPLIT) return SMAT_FMT_SPLIT;
   return SMAT_FMT_CSR;
 }
 
@@ -96,21 +97,23 @@ double variant_bytes(const smat_s *h, int v) {
     case SMAT_V_ELL: return ell_bytes(h);
     case SMAT_V_DIA: return dia_bytes(h);
     case SMAT_V_COO: return (double)(h->esz + 8) * h->nnz;
-    case SMAT_V_HYB: case SMAT_V_SELL: case SMAT_V_BCSR: return h->ext_bytes[v - SMAT_V_HYB];
+    case SMAT_V_HYB: case SMAT_V_SELL: case SMAT_V_BCSR: case SMAT_V_SPLIT: return h->ext_bytes[v - SMAT_V_HYB];
     default: return csr_bytes(h);
   }
 }
 
-// HYB / SELL / BCSR: admissible once their layout is measured, under the
-// same two limits as ELL and DIA (stored slots <= fill_ratio_max x NNZ,
-// bytes <= bytes_cap x CSR bytes); HYB also needs an ELL part.
+// HYB / SELL / BCSR / SPLIT: admissible once their layout is measured, under
+// the same two limits as ELL and DIA (stored slots <= fill_ratio_max x NNZ,
+// bytes <= bytes_cap x CSR bytes); HYB also needs an ELL part, SPLIT a long
+// row (without one it is the COO plan).
 uint32_t ext_bits(const smat_s *h) {
   uint32_t mask = 0;
   const double cap = h->bytes_cap * std::max(csr_bytes(h), 1.0);
   const double lim = (double)h->fill_ratio_max * (double)h->nnz;
-  for (int e = 0; e < 3; ++e) {
+  for (int e = 0; e < 4; ++e) {
     if (!h->ext_known[e] || h->nnz == 0 || h->m == 0) continue;
     if (e == 0 && h->hyb_K < 1) continue;
+    if (e == SMAT_V_SPLIT - SMAT_V_HYB && h->split_nl < 1) continue;
     if (h->ext_slots[e] <= lim && h->ext_bytes[e] <= cap) mask |= 1u << (SMAT_V_HYB + e);
   }
   return mask;
@@ -268,6 +271,15 @@ void free_format(smat_s *h, int fmt) {
   } else if (fmt == SMAT_FMT_BCSR) {  // the 64-bit block row starts stay
     dev_free(h->bcsr_rowptr); dev_free(h->bcsr_col); dev_free(h->bcsr_val);
     h->bcsr_rowptr = h->bcsr_col = nullptr; h->bcsr_val = nullptr;
+  } else if (fmt == SMAT_FMT_SPLIT) {
+    for (int32_t **p : {&h->split_lchunk, &h->split_lrows, &h->split_crow, &h->split_cstart, &h->split_cend,
+                        &h->split_srow, &h->split_scol, &h->split_empty}) {
+      dev_free(*p);
+      *p = nullptr;
+    }
+    dev_free(h->split_sval); dev_free(h->split_part);
+    h->split_sval = h->split_part = nullptr;
+    h->split_built = false;
   }
 }
 
@@ -284,6 +296,7 @@ void free_ext_layouts(smat_s *h) {
   free_format(h, SMAT_FMT_BCSR);
   dev_free(h->bcsr_brp64);
   h->bcsr_brp64 = nullptr;
+  free_format(h, SMAT_FMT_SPLIT);
 }
 
 // Layout of a further format -- sizes without the values: HYB's width K and
@@ -310,6 +323,21 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
       h->hyb_ncoo = ncoo;
       h->ext_slots[e] = (double)K * h->m + (double)ncoo;
       h->ext_bytes[e] = (double)(esz + 4) * K * h->P + (double)(esz + 8) * ncoo;
+    } else if (v == SMAT_V_SPLIT) {
+      int64_t nl = 0, nc = 0, ns = 0;
+      for (int64_t k = 1; k < (int64_t)h->hist.size(); ++k) {
+        const int64_t c = h->hist[(size_t)k];
+        if (k >= SPLIT_L) {
+          nl += c;
+          nc += c * ((k + SPLIT_CK - 1) / SPLIT_CK);
+        } else {
+          ns += c * k;
+        }
+      }
+      h->split_nl = nl; h->split_nc = nc; h->split_ns = ns; h->split_ne = h->hist.empty() ? 0 : h->hist[0];
+      h->ext_slots[e] = (double)h->nnz;
+      h->ext_bytes[e] = (double)(esz + 4) * (h->nnz - ns) + 12.0 * nc + 4.0 * (2 * nl + 1) + (double)(esz + 8) * ns +
+                        4.0 * h->split_ne;
     } else if (v == SMAT_V_SELL) {
       free_sell_layout(h);  // drop what an earlier, failed attempt left
       const int64_t mp = (h->m + 31) / 32 * 32, ns = mp / 32;
@@ -474,8 +502,10 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     }
     return SMAT_OK;
   }
-  if (fmt == SMAT_FMT_HYB || fmt == SMAT_FMT_SELL || fmt == SMAT_FMT_BCSR) {
-    const int v = fmt == SMAT_FMT_HYB ? SMAT_V_HYB : (fmt == SMAT_FMT_SELL ? SMAT_V_SELL : SMAT_V_BCSR);
+  if (fmt == SMAT_FMT_HYB || fmt == SMAT_FMT_SELL || fmt == SMAT_FMT_BCSR || fmt == SMAT_FMT_SPLIT) {
+    const int v = fmt == SMAT_FMT_HYB ? SMAT_V_HYB
+                  : fmt == SMAT_FMT_SELL ? SMAT_V_SELL
+                  : fmt == SMAT_FMT_BCSR ? SMAT_V_BCSR : SMAT_V_SPLIT;
     TRYS(ext_layout(h, v, h->sell_sigma, s));
     if (!(h->f.admissible & (1u << v))) return SMAT_ERR_UNSUPPORTED;
     struct Undo {  // a failed build leaves no half-built format behind
@@ -504,6 +534,30 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
       TRY(dev_alloc(&p, (size_t)h->sell_slots * 4)); h->sell_col = (int32_t *)p;
       TRY(dev_alloc(&p, (size_t)h->sell_slots * h->esz)); h->sell_val = p;
       TRY(launch_to_sell(h, s));
+    } else if (fmt == SMAT_FMT_SPLIT) {
+      if (h->split_built) { undo.armed = false; return SMAT_OK; }
+      const size_t nl = (size_t)h->split_nl, nc = (size_t)h->split_nc, ns = (size_t)h->split_ns,
+                   ne = (size_t)h->split_ne;
+      TRY(dev_alloc(&p, (nl + 1) * 4)); h->split_lchunk = (int32_t *)p;
+      TRY(dev_alloc(&p, nl * 4)); h->split_lrows = (int32_t *)p;
+      TRY(dev_alloc(&p, nc * 4)); h->split_crow = (int32_t *)p;
+      TRY(dev_alloc(&p, nc * 4)); h->split_cstart = (int32_t *)p;
+      TRY(dev_alloc(&p, nc * 4)); h->split_cend = (int32_t *)p;
+      TRY(dev_alloc(&p, ns * 4)); h->split_srow = (int32_t *)p;
+      TRY(dev_alloc(&p, ns * 4)); h->split_scol = (int32_t *)p;
+      TRY(dev_alloc(&p, ns * h->esz)); h->split_sval = p;
+      TRY(dev_alloc(&p, ne * 4)); h->split_empty = (int32_t *)p;
+      TRY(dev_alloc(&p, nc * tsize(h))); h->split_part = p;
+      DevBuf cnt, pre;
+      const size_t M = (size_t)h->m;
+      TRY(cnt.alloc(4 * M * 8));
+      TRY(pre.alloc(4 * (M + 1) * 8));
+      long long *c = cnt.as<long long>(), *q = pre.as<long long>();
+      TRY(launch_split_counts(h, c, c + M, c + 2 * M, c + 3 * M, s));
+      for (int k = 0; k < 4; ++k) TRY(exclusive_scan(c + k * M, (long long)M, q + k * (M + 1), s));
+      TRY(launch_split_fill(h, q, q + (M + 1), q + 2 * (M + 1), q + 3 * (M + 1), s));
+      TRY(cudaStreamSynchronize(s));
+      h->split_built = true;
     } else {
       if (h->bcsr_val) { undo.armed = false; return SMAT_OK; }
       const int64_t bb = (int64_t)h->bcsr_b * h->bcsr_b;
@@ -539,6 +593,7 @@ bool variant_ready(const smat_s *h, int v) {
   if (fmt == SMAT_FMT_HYB && !h->hyb_built) return false;
   if (fmt == SMAT_FMT_SELL && !h->sell_val) return false;
   if (fmt == SMAT_FMT_BCSR && !h->bcsr_val) return false;
+  if (fmt == SMAT_FMT_SPLIT && !h->split_built) return false;
   if (carry_bytes_needed(h, v) > h->carry_bytes) return false;
   return true;
 }
@@ -606,7 +661,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     }
     if (!o.keep_formats) {
       // drop a trialled format right away unless it is the best so far
-      for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_BCSR; ++fmt)
+      for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_SPLIT; ++fmt)
         if (fmt != variant_format(*best)) free_format(h, fmt);
     }
   }
@@ -781,7 +836,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   for (auto &t : h->timings) t = -1.0f;
   const uint32_t allowed = (o.allowed ? o.allowed : ALL_VARIANTS) & ALL_VARIANTS;
   // layouts of the further formats the chosen mode may use
-  for (int e = SMAT_V_HYB; e <= SMAT_V_BCSR; ++e) {
+  for (int e = SMAT_V_HYB; e <= SMAT_V_SPLIT; ++e) {
     if (!((allowed >> e) & 1u)) continue;
     const bool want = o.mode == SMAT_TUNE_EXHAUSTIVE || (o.mode == SMAT_TUNE_FIXED && o.fixed_variant == e) ||
                       (o.mode == SMAT_TUNE_LEARNED && o.trial_extended &&
@@ -802,7 +857,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
                 SMAT_V_CSR_MERGE, SMAT_V_COO})
     if ((ok >> c) & 1u) cands.push_back(c);
   std::vector<int> ext;
-  for (int c = SMAT_V_HYB; c <= SMAT_V_BCSR; ++c)
+  for (int c = SMAT_V_HYB; c <= SMAT_V_SPLIT; ++c)
     if ((ok >> c) & 1u) ext.push_back(c);
   switch (o.mode) {
     case SMAT_TUNE_FIXED:
@@ -856,7 +911,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   }
   TRYS(prepare_variant(h, v, s));
   if (!o.keep_formats)
-    for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_BCSR; ++fmt)
+    for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_SPLIT; ++fmt)
       if (fmt != variant_format(v)) free_format(h, fmt);
   TRY(cudaStreamSynchronize(s));
   h->variant = v;
@@ -965,7 +1020,7 @@ smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_ALL_VARIANTS])
 
 smat_status_t smat_convert(smat_handle_t h, smat_format_t fmt, void *stream) {
   TRYS(check_handle(h));
-  if (fmt < SMAT_FMT_CSR || fmt > SMAT_FMT_BCSR) return SMAT_ERR_INVALID_ARG;
+  if (fmt < SMAT_FMT_CSR || fmt > SMAT_FMT_SPLIT) return SMAT_ERR_INVALID_ARG;
   TRYS(build_format(h, fmt, (cudaStream_t)stream));
   TRY(cudaStreamSynchronize((cudaStream_t)stream));
   return SMAT_OK;
@@ -982,6 +1037,7 @@ smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[
     case SMAT_FMT_HYB: if (!h->hyb_built) return SMAT_ERR_UNSUPPORTED; dims[0] = h->hyb_K; dims[1] = h->hyb_ncoo; break;
     case SMAT_FMT_SELL: if (!h->sell_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->sell_ns; dims[1] = h->sell_slots; break;
     case SMAT_FMT_BCSR: if (!h->bcsr_val) return SMAT_ERR_UNSUPPORTED; dims[0] = h->bcsr_b; dims[1] = h->bcsr_nb; break;
+    case SMAT_FMT_SPLIT: if (!h->split_built) return SMAT_ERR_UNSUPPORTED; dims[0] = h->split_nc; dims[1] = h->split_ns; break;
     default: return SMAT_ERR_INVALID_ARG;
   }
   return SMAT_OK;
@@ -1029,6 +1085,16 @@ smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *id
       TRY(cudaMemcpy(idx, h->bcsr_rowptr, (mb + 1) * 4, cudaMemcpyDefault));
       if (nb) TRY(cudaMemcpy(idx + mb + 1, h->bcsr_col, nb * 4, cudaMemcpyDefault));
       if (nb) TRY(cudaMemcpy(val, h->bcsr_val, nb * bb * h->esz, cudaMemcpyDefault));
+    } break;
+    case SMAT_FMT_SPLIT: {
+      if (!idx || (!val && h->split_ns > 0)) return SMAT_ERR_INVALID_ARG;
+      const size_t nc = (size_t)h->split_nc, ns = (size_t)h->split_ns;
+      if (nc) TRY(cudaMemcpy(idx, h->split_crow, nc * 4, cudaMemcpyDefault));
+      if (nc) TRY(cudaMemcpy(idx + nc, h->split_cstart, nc * 4, cudaMemcpyDefault));
+      if (nc) TRY(cudaMemcpy(idx + 2 * nc, h->split_cend, nc * 4, cudaMemcpyDefault));
+      if (ns) TRY(cudaMemcpy(idx + 3 * nc, h->split_srow, ns * 4, cudaMemcpyDefault));
+      if (ns) TRY(cudaMemcpy(idx + 3 * nc + ns, h->split_scol, ns * 4, cudaMemcpyDefault));
+      if (ns) TRY(cudaMemcpy(val, h->split_sval, ns * h->esz, cudaMemcpyDefault));
     } break;
     default:
       return SMAT_ERR_INVALID_ARG;

@@ -19,6 +19,10 @@
 //   BCSR  browptr[ceil(M/b) + 1]; bcol[k] ascending within a block row;
 //         bval[k*b*b + r*b + c] = a(I*b + r, bcol[k]*b + c), +0 where nothing
 //         is stored (also past the matrix edge).
+//   SPLIT rows of >= SPLIT_L (1024) entries ("long", listed ascending) cut into
+//         chunks of <= SPLIT_CK entries (row, first, end entry per chunk, a
+//         long row's chunks consecutive); the other non-empty rows' entries
+//         as a COO in CSR order; empty rows listed.
 #include <algorithm>
 #include <climits>
 
@@ -287,6 +291,56 @@ __global__ void to_bcsr_kernel(const int32_t *__restrict__ rowptr, const int32_t
         bval[kb * BS * BS + r * BS + (col[q] - J * BS)] = val[q];
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SPLIT: per-row counts, then each row's entries to their place
+// ---------------------------------------------------------------------------
+__global__ void split_counts_kernel(const int32_t *__restrict__ rowptr, long long m, long long *__restrict__ cl,
+                                    long long *__restrict__ cc, long long *__restrict__ cs,
+                                    long long *__restrict__ ce) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const long long rd = rowptr[i + 1] - rowptr[i];
+    const bool lng = rd >= SPLIT_L;
+    cl[i] = lng;
+    cc[i] = lng ? (rd + SPLIT_CK - 1) / SPLIT_CK : 0;
+    cs[i] = (!lng && rd > 0) ? rd : 0;
+    ce[i] = rd == 0;
+  }
+}
+
+template <typename B>
+__global__ void split_fill_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                  const B *__restrict__ val, long long m, const long long *__restrict__ pl,
+                                  const long long *__restrict__ pc, const long long *__restrict__ ps,
+                                  const long long *__restrict__ pe, int32_t *__restrict__ lrows,
+                                  int32_t *__restrict__ lchunk, int32_t *__restrict__ crow, int32_t *__restrict__ cstart,
+                                  int32_t *__restrict__ cend, int32_t *__restrict__ srow, int32_t *__restrict__ scol,
+                                  B *__restrict__ sval, int32_t *__restrict__ empty) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = rowptr[i], e0 = rowptr[i + 1], rd = e0 - s0;
+    if (rd == 0) {
+      empty[pe[i]] = (int32_t)i;
+    } else if (rd >= SPLIT_L) {
+      const long long l = pl[i];
+      lrows[l] = (int32_t)i;
+      lchunk[l] = (int32_t)pc[i];
+      long long c = pc[i];
+      for (long long k = s0; k < e0; k += SPLIT_CK, ++c) {
+        crow[c] = (int32_t)i;
+        cstart[c] = (int32_t)k;
+        cend[c] = (int32_t)(k + SPLIT_CK < e0 ? k + SPLIT_CK : e0);
+      }
+    } else {
+      long long o = ps[i];
+      for (long long k = s0; k < e0; ++k, ++o) {
+        srow[o] = (int32_t)i;
+        scol[o] = col[k];
+        sval[o] = val[k];
+      }
+    }
+    if (i == 0) lchunk[pl[m]] = (int32_t)pc[m];  // one past the last long row
   }
 }
 
@@ -572,6 +626,34 @@ cudaError_t launch_to_bcsr(const smat_s *h, const long long *brp, cudaStream_t s
     case 4: return to_bcsr_b<4>(h, brp, s);
     default: return to_bcsr_b<8>(h, brp, s);
   }
+}
+
+cudaError_t launch_split_counts(const smat_s *h, long long *cl, long long *cc, long long *cs, long long *ce,
+                                cudaStream_t s) {
+  if (h->m <= 0) return cudaSuccess;
+  split_counts_kernel<<<grid_for(h->m, 256, 152 * 16), 256, 0, s>>>(h->rowptr, h->m, cl, cc, cs, ce);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_fill(const smat_s *h, const long long *pl, const long long *pc, const long long *ps,
+                              const long long *pe, cudaStream_t s) {
+  if (h->m <= 0) return cudaSuccess;
+  const int g = grid_for(h->m, 256, 152 * 16);
+  switch (h->esz) {
+    case 8: split_fill_kernel<<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const Raw<8>::T *)h->val, h->m, pl, pc, ps, pe,
+                                                  h->split_lrows, h->split_lchunk, h->split_crow, h->split_cstart,
+                                                  h->split_cend, h->split_srow, h->split_scol,
+                                                  (Raw<8>::T *)h->split_sval, h->split_empty); break;
+    case 4: split_fill_kernel<<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const Raw<4>::T *)h->val, h->m, pl, pc, ps, pe,
+                                                  h->split_lrows, h->split_lchunk, h->split_crow, h->split_cstart,
+                                                  h->split_cend, h->split_srow, h->split_scol,
+                                                  (Raw<4>::T *)h->split_sval, h->split_empty); break;
+    default: split_fill_kernel<<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const Raw<2>::T *)h->val, h->m, pl, pc, ps, pe,
+                                                   h->split_lrows, h->split_lchunk, h->split_crow, h->split_cstart,
+                                                   h->split_cend, h->split_srow, h->split_scol,
+                                                   (Raw<2>::T *)h->split_sval, h->split_empty); break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_ext(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta, void *y,

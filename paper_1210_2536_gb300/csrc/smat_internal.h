@@ -99,10 +99,17 @@ struct smat_s {
   long long *bcsr_brp64 = nullptr;
   int32_t *bcsr_rowptr = nullptr, *bcsr_col = nullptr;
   void *bcsr_val = nullptr;
-  // measured layouts of HYB / SELL / BCSR (index v - SMAT_V_HYB): stored
-  // slots (fill included) and bytes, for their admissibility bits
-  bool ext_known[3] = {false, false, false};
-  double ext_slots[3] = {0, 0, 0}, ext_bytes[3] = {0, 0, 0};
+  // SPLIT: rows of >= SPLIT_L entries in chunks of <= SPLIT_CK, short rows as COO
+  int64_t split_nl = 0, split_nc = 0, split_ns = 0, split_ne = 0;
+  int32_t *split_lchunk = nullptr;  // first chunk of each long row, nl + 1 values
+  int32_t *split_lrows = nullptr, *split_crow = nullptr, *split_cstart = nullptr, *split_cend = nullptr;
+  int32_t *split_srow = nullptr, *split_scol = nullptr, *split_empty = nullptr;
+  void *split_sval = nullptr, *split_part = nullptr;
+  bool split_built = false;
+  // measured layouts of HYB / SELL / BCSR / SPLIT (index v - SMAT_V_HYB):
+  // stored slots (fill included) and bytes, for their admissibility bits
+  bool ext_known[4] = {false, false, false, false};
+  double ext_slots[4] = {0, 0, 0, 0}, ext_bytes[4] = {0, 0, 0, 0};
 
   // merge-path tile coordinates (int2 per tile boundary), computed once
   void *merge_coords = nullptr;
@@ -148,6 +155,16 @@ cudaError_t launch_sell_layout(const smat_s *h, int sigma, int32_t *perm, int32_
                                cudaStream_t s);
 cudaError_t launch_to_sell(const smat_s *h, cudaStream_t s);
 cudaError_t launch_bcsr_count(const smat_s *h, int b, long long *cnt, cudaStream_t s);
+#ifndef SMAT_SPLIT_L
+#define SMAT_SPLIT_L 1024
+#endif
+constexpr int64_t SPLIT_L = SMAT_SPLIT_L, SPLIT_CK = 4096;
+// SPLIT conversion: per-row counts (long flag, chunks, short entries, empty
+// flag) for the scans, then the fill from their exclusive scans.
+cudaError_t launch_split_counts(const smat_s *h, long long *cl, long long *cc, long long *cs, long long *ce,
+                                cudaStream_t s);
+cudaError_t launch_split_fill(const smat_s *h, const long long *pl, const long long *pc, const long long *ps,
+                              const long long *pe, cudaStream_t s);
 cudaError_t launch_to_bcsr(const smat_s *h, const long long *brp, cudaStream_t s);
 // SELL / BCSR products (HYB runs through the ELL and COO kernels of spmv.cu).
 cudaError_t launch_spmv_ext(const smat_s *h, int variant, const void *alpha, const void *x,

@@ -15,6 +15,8 @@
 // multiply and add, i.e. the same operations as the CSR definition.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "smat_internal.h"
 #include "spmv_device.cuh"
 
@@ -433,6 +435,75 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
                           blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// SPLIT, long rows (at least SPLIT_L = 1024 entries; measured on power-law
+// matrices against 128 and 256, where rows of a few hundred entries paid a
+// whole CTA's reduction for little work): one CTA of 256 threads per chunk of
+// at most 4096 entries of one row.  Thread t takes entries first + t + 256 j (j < 16), so every
+// column and value load is a contiguous warp access; one fused multiply-add
+// per entry; the 256 partial sums are added in a fixed order (warp butterfly,
+// then the 8 warp sums in turn) into part[chunk].  No row ends inside a
+// chunk, so there is no segmented scan: a tile of a long row costs one plain
+// block sum instead of the COO tile's carry resolution.
+// ---------------------------------------------------------------------------
+template <typename V, typename T>
+__global__ void __launch_bounds__(256) split_chunk_kernel(const int32_t *__restrict__ cstart,
+                                                          const int32_t *__restrict__ cend,
+                                                          const int32_t *__restrict__ col, const V *__restrict__ val,
+                                                          const T *__restrict__ x, T *__restrict__ part, long long nc) {
+  __shared__ T s_w[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (long long c = blockIdx.x; c < nc; c += gridDim.x) {
+    const int k0 = __ldg(cstart + c), k1 = __ldg(cend + c);
+    T acc = 0;
+    // steps j of 256 entries past the chunk's end are skipped by the whole
+    // CTA (a uniform test), so short chunks issue only the work they hold
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (k0 + 256 * 8 * b >= k1) break;
+      int cc[8];
+      T v[8], xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + (int)threadIdx.x + 256 * (8 * b + q);
+        const bool on = k < k1;
+        cc[q] = on ? ld_idx(col + k) : -1;
+        v[q] = on ? (T)ld_val(val + k) : (T)0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv[q] = cc[q] >= 0 ? __ldg(x + cc[q]) : (T)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (k0 + 256 * (8 * b + q) < k1) acc = fused(acc, v[q], xv[q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = add_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) s_w[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T t = s_w[0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) t = add_rn(t, s_w[k]);
+      part[c] = t;
+    }
+    __syncthreads();  // s_w is rewritten by the next chunk
+  }
+}
+
+// SPLIT, long rows: each row's chunk sums added in chunk order, then the
+// epilogue.
+template <typename T, int MODE>
+__global__ void split_rows_kernel(const int32_t *__restrict__ lrows, const int32_t *__restrict__ lchunk,
+                                  const T *__restrict__ part, long long nl, Epi<T, MODE> ep, T *__restrict__ y) {
+  for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (long long)gridDim.x * blockDim.x) {
+    const int c0 = lchunk[l], c1 = lchunk[l + 1];
+    T t = part[c0];
+    for (int c = c0 + 1; c < c1; ++c) t = add_rn(t, part[c]);
+    const long long r = lrows[l];
+    y[r] = ep(t, y, r);
+  }
+}
+
 // Fix-up: y[r] += alpha * (sum of the carries of row r), runs of equal rows
 // summed in tile order by the run's first entry.
 template <typename T, int MODE>
@@ -657,6 +728,28 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       return launch_coo<V, T, EPI_AXPBY>(h, h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y,
                                          h->hyb_ncoo, s);
     }
+    case SMAT_V_SPLIT: {
+      if (h->split_ne > 0) {
+        scale_rows_kernel<T, MODE><<<grid_for(h->split_ne, 256, 152 * 8), 256, 0, s>>>(h->split_empty, h->split_ne,
+                                                                                        ep, y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      if (h->split_nc > 0) {
+        const long long nc = h->split_nc;
+        split_chunk_kernel<V, T><<<(unsigned)std::min<long long>(nc, 1LL << 30), 256, 0, s>>>(
+            h->split_cstart, h->split_cend, h->colidx, val, x, (T *)h->split_part, nc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        split_rows_kernel<T, MODE><<<grid_for(h->split_nl, 256, 152 * 8), 256, 0, s>>>(
+            h->split_lrows, h->split_lchunk, (const T *)h->split_part, h->split_nl, ep, y);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      if (h->split_ns > 0)
+        return launch_coo<V, T, MODE>(h, h->split_srow, h->split_scol, (const V *)h->split_sval, x, ep, y,
+                                      h->split_ns, s);
+    } break;
     default:
       return cudaErrorInvalidValue;
   }
@@ -692,6 +785,7 @@ size_t carry_bytes_needed(const smat_s *h, int variant) {
   if (variant == SMAT_V_CSR_MERGE) tiles = (h->m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
   else if (variant == SMAT_V_COO) tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
   else if (variant == SMAT_V_HYB) tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  else if (variant == SMAT_V_SPLIT) tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
   else return 0;
   size_t tsz = h->dtype == SMAT_F64 ? 8 : 4;
   return (size_t)((tiles * 4 + 15) / 16) * 16 + (size_t)tiles * tsz;
@@ -710,6 +804,10 @@ int spmv_launch_count(const smat_s *h, int variant) {
   if (variant == SMAT_V_HYB) {
     long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
     return 1 + (h->hyb_ncoo > 0) + (tiles > 1);
+  }
+  if (variant == SMAT_V_SPLIT) {
+    long long tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    return (h->split_ne > 0) + 2 * (h->split_nc > 0) + (h->split_ns > 0) + (tiles > 1);
   }
   if (variant == SMAT_V_SELL) return h->sell_ns > 0;
   if (variant == SMAT_V_BCSR) return h->bcsr_mb > 0;

@@ -13,10 +13,13 @@ y written once (plus read when beta != 0):
   SELL                           (s_v + 4) slots + 4 Mp + 12 Nslices + 8
                                  (perm 4 B / position, width and pointer per slice)
   BCSR                           (s_v b^2 + 4) Nblocks + 4 (ceil(M/b) + 1)
+  SPLIT                          (s_v + 4) (NNZ - Nshort) + 12 Nchunks + (s_v + 8) Nshort
+                                 + 4 empty rows (+ 8 per long row, at most Nchunks: counted as Nchunks)
   every variant                  + s_x N + s_y M (1 + [beta != 0])
 
-The HYB / SELL / BCSR sizes come from the built format (SpMatrix.features()
-adds hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b and bcsr_nb once built).
+The HYB / SELL / BCSR / SPLIT sizes come from the built format
+(SpMatrix.features() adds hyb_K, hyb_ncoo, sell_ns, sell_slots, bcsr_b,
+bcsr_nb, split_nc and split_ns once built).
 
 GFLOP/s counts 2 NNZ flops per product (true nonzeros only).
 
@@ -29,7 +32,7 @@ from __future__ import annotations
 ELEM = {"f64": 8, "f32": 4, "bf16": 2}
 CSR_VARIANTS = (0, 1, 2, 3, 4, 8)
 V_ELL, V_DIA, V_COO = 5, 6, 7
-V_HYB, V_SELL, V_BCSR = 9, 10, 11
+V_HYB, V_SELL, V_BCSR, V_SPLIT = 9, 10, 11, 12
 
 
 def algorithmic_bytes(f: dict, variant: int, dtype: str, beta_nonzero: bool = False) -> float:
@@ -51,6 +54,9 @@ def algorithmic_bytes(f: dict, variant: int, dtype: str, beta_nonzero: bool = Fa
     elif variant == V_BCSR:
         b = f["bcsr_b"]
         mat = (sv * b * b + 4) * f["bcsr_nb"] + 4 * ((m + b - 1) // b + 1)
+    elif variant == V_SPLIT:
+        ns, nc = f["split_ns"], f["split_nc"]
+        mat = (sv + 4) * (nnz - ns) + 12 * nc + 8 * nc + (sv + 8) * ns + 4 * f["empty_rows"]
     else:
         raise ValueError(variant)
     return float(mat + sx * n + sx * m * (2 if beta_nonzero else 1))

@@ -71,7 +71,7 @@ def main():
     except Exception:
         pass
     names = smat.VARIANT_NAMES
-    vs = [v for v in range(8) if (f["admissible"] >> v) & 1] + [9, 10, 11] if a.variant == "all" \
+    vs = [v for v in range(8) if (f["admissible"] >> v) & 1] + [9, 10, 11, 12] if a.variant == "all" \
         else [names.index(a.variant)]
     out = {"matrix": A.name, "m": A.m, "nnz": A.nnz, "dtype": a.dtype, "variants": {}}
     for v in vs:

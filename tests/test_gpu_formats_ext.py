@@ -1,4 +1,4 @@
-"""GPU parity of the further formats (HYB, SELL-32-sigma, BCSR; future work in
+"""GPU parity of the further formats (HYB, SELL-32-sigma, BCSR, SPLIT; future work in
 Sec. 8): conversions bit for bit against the oracle's, products within the
 per-row bars, admissibility by the stated limits, and their place in the
 execute-and-measure search."""
@@ -15,7 +15,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 ESZ = {"f64": 8, "f32": 4, "bf16": 2}
-EXT = {smat.SMAT_V_HYB: smat.SMAT_FMT_HYB, smat.SMAT_V_SELL: smat.SMAT_FMT_SELL, smat.SMAT_V_BCSR: smat.SMAT_FMT_BCSR}
+EXT = {smat.SMAT_V_HYB: smat.SMAT_FMT_HYB, smat.SMAT_V_SELL: smat.SMAT_FMT_SELL, smat.SMAT_V_BCSR: smat.SMAT_FMT_BCSR,
+       smat.SMAT_V_SPLIT: smat.SMAT_FMT_SPLIT}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -77,6 +78,17 @@ def test_ext_conversions_bit_exact(case, dtype):
         brp, bcol, bval = oracle.to_bcsr(A.m, A.n, A.rowptr, A.colidx, vals, b)
         assert p["b"] == b and np.array_equal(p["browptr"], brp) and np.array_equal(p["bcol"], bcol)
         assert _same_bytes(p["val"], bval)
+    # SPLIT: rows of >= 1024 entries in chunks of <= 4096, the rest as COO
+    sp = oracle.split_rows(A.m, A.rowptr, A.colidx, vals, L=1024, CK=4096)
+    nl, nc, ns, ne = len(sp["lrows"]), len(sp["crow"]), len(sp["srow"]), len(sp["empty"])
+    byts = (esz + 4) * (A.nnz - ns) + 12 * nc + 4 * (2 * nl + 1) + (esz + 8) * ns + 4 * ne
+    want = _expected_admissible(A, dtype, A.nnz, byts, nl >= 1)
+    assert _convert(M, smat.SMAT_FMT_SPLIT) == want, name
+    if want:
+        p = M.export_parts(smat.SMAT_FMT_SPLIT)
+        for k in ("crow", "cstart", "cend", "srow", "scol"):
+            assert np.array_equal(p[k], sp[k]), (name, k)
+        assert _same_bytes(p["sval"], sp["sval"])
     adm = M.features()["admissible"]
     for v, fmt in EXT.items():
         assert bool((adm >> v) & 1) == (smat.smat_format_dims(M.h, fmt)[0] == smat.SMAT_OK), (name, v)
@@ -125,12 +137,15 @@ def test_ext_spmv(case, dtype, ab):
         ran += 1
     if A.nnz > 0 and name not in ("one_row", "one_col", "one_by_one", "long_row", "powerlaw_20000"):
         assert ran >= 2, name
+    if name in ("long_row", "powerlaw_20000"):   # rows of 1024 or more entries: SPLIT runs
+        assert (M.features()["admissible"] >> smat.SMAT_V_SPLIT) & 1, name
     M.close()
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_ext_misaligned_vectors_are_safe(dtype):
-    A = synth.blockdiag(999, 8, 2)
+@pytest.mark.parametrize("mk", [lambda: synth.blockdiag(999, 8, 2), lambda: synth.powerlaw(3000, 1.8, 2000, 6)])
+def test_ext_misaligned_vectors_are_safe(dtype, mk):
+    A = mk()
     M, vals64 = make(A, dtype)
     npdt = np.float64 if dtype == "f64" else np.float32
     x = synth.uniform(0, 1, A.n).astype(npdt)
@@ -141,7 +156,11 @@ def test_ext_misaligned_vectors_are_safe(dtype):
     xb[1:] = torch.from_numpy(x).to(DEV)
     for v in EXT:
         yb[1:] = torch.from_numpy(y0).to(DEV)
-        M.spmv(xb[1:], yb[1:], 1.5, -0.5, variant=v)
+        try:
+            M.spmv(xb[1:], yb[1:], 1.5, -0.5, variant=v)
+        except smat.SmatError as e:   # not admissible on this matrix
+            assert e.status == smat.SMAT_ERR_UNSUPPORTED
+            continue
         torch.cuda.synchronize()
         assert_close_rows(yb[1:].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
                           f"misaligned {dtype} {smat.VARIANT_NAMES[v]}")
