@@ -96,8 +96,8 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
   typedef typename Compute<V>::T T;
   constexpr int R = 16 / (int)sizeof(V);
   const Epi<T, MODE> ep{(T)M.alpha, (T)M.beta};
-  // tiles of ELL / DIA members start at multiples of BNT*R rows, so the
-  // lane-striped mappings (32*R rows per warp) stay inside their tile
+  // tiles of ELL members start at multiples of BNT*R rows, so the
+  // lane-striped mapping (32*R rows per warp) stays inside its tile
   if (KIND == KIND_ELL) {
     if (M.lane) {
       for (long long b = tl.row0 + (long long)(threadIdx.x >> 5) * 32 * R; b < tl.row1; b += (long long)BNT * R)
@@ -108,14 +108,14 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
         ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
     }
   } else if (KIND == KIND_DIA) {
-    if (sizeof(V) == 8) {  // FP64: lane-striped rows, as the single-matrix DIA kernel
-      for (long long b = tl.row0 + (long long)(threadIdx.x >> 5) * 32 * R; b < tl.row1; b += (long long)BNT * R)
-        dia_lane_group<V, R, MODE, 16 / R>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m,
-                                           M.n, b, threadIdx.x & 31);
-    } else {
-      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-        dia_group<V, R, MODE>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, i0);
-    }
+    // consecutive rows and checked x loads in every precision, FP64 with 4
+    // diagonals per batch: under this kernel's 64-register bound the
+    // lane-striped FP64 body spills (540 bytes, ptxas), the unchecked interior
+    // path 60-1000 bytes, 8-diagonal FP64 batches 140
+    constexpr int UD = sizeof(V) == 8 ? 4 : 16 / R;
+    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+      dia_group<V, R, MODE, UD, false>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n,
+                                       i0);
   } else if (KIND == KIND_SELL) {  // row0 / row1 are slice indices; a warp per slice
     for (long long sl = tl.row0 + threadIdx.x / 32; sl < tl.row1; sl += BNT / 32)
       sell_slice<V, MODE, 8>(M.sptr, M.swidth, M.sperm, M.scol, (const V *)M.sval, (const T *)M.x, ep, (T *)M.y, sl,

@@ -256,7 +256,7 @@ __device__ __forceinline__ void ell_lane_group(const int32_t *__restrict__ ecol,
 // (chosen on the host as for ELL).  Fill zeros are
 // multiplied like stored values; positions whose column falls outside the
 // matrix are dropped.
-template <typename V, int R, int MODE, int U = 16 / R>
+template <typename V, int R, int MODE, int U = 16 / R, bool FAST = true>
 __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *__restrict__ dval, long long P,
                                           const typename Compute<V>::T *__restrict__ x,
                                           const Epi<typename Compute<V>::T, MODE> &ep,
@@ -278,7 +278,7 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
 #pragma unroll
         for (int r = 0; r < R; ++r) v[u][r] = 0;
       }
-      if (live && j0 >= 0 && j0 + R <= n) {  // the whole window inside x: no per-row checks
+      if (FAST && live && j0 >= 0 && j0 + R <= n) {  // the whole window inside x: no per-row checks
         const T *xp = x + j0;
 #pragma unroll
         for (int r = 0; r < R; ++r) xv[u][r] = __ldg(xp + r);
