@@ -25,10 +25,17 @@
  *   - alpha and beta are HOST pointers to one scalar of the compute type.
  *     beta == 0 means y is only written (NaN in y is ignored, as in BLAS).
  *
- * Thread safety: calls on different handles are independent.  Calls on one
- * handle must not overlap: the merge-path and COO kernels keep their carries
- * in handle-owned scratch, so two products on one handle must be ordered
- * (same stream, or synchronised).
+ * Thread safety: calls on different handles are independent.  Products
+ * (smat_spmv, smat_spmv_variant) on one handle may run concurrently from
+ * different streams and host threads: the kernels that carry partial sums
+ * between CTAs (merge-path, COO, HYB, SPLIT) use the handle's own scratch on
+ * the first stream that runs products on it and scratch of their own on every
+ * further stream, allocated on that stream's first product (so a stream that
+ * is capturing a CUDA graph must have run a product on the handle before, or
+ * be its first stream; otherwise the product reports SMAT_ERR_CUDA).
+ * smat_tune, smat_convert, smat_destroy and the host-buffer products
+ * (smat_spmv_host*, which share the handle's staging buffers) must not overlap
+ * with other calls on the handle.
  */
 #ifndef SMAT_H
 #define SMAT_H
@@ -204,7 +211,9 @@ smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const
                         void *y, void *stream);
 
 /* Same product through a chosen variant (its format is built on first use;
- * SMAT_ERR_UNSUPPORTED if the variant is not admissible and cannot be built). */
+ * SMAT_ERR_UNSUPPORTED if the variant is not admissible and cannot be built).
+ * The first product through a variant builds its format and, like smat_tune,
+ * must not overlap other calls on the handle. */
 smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *alpha,
                                 const void *x, const void *beta, void *y, void *stream);
 

@@ -572,6 +572,53 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
   return SMAT_ERR_INVALID_ARG;
 }
 
+}  // namespace
+
+cudaError_t stream_scratch(const smat_s *h, cudaStream_t s, Scratch *out, bool claim) {
+  std::lock_guard<std::mutex> lock(h->scratch_mu);
+  if (!claim) {
+    *out = Scratch{h->carry, h->split_part};
+    return cudaSuccess;
+  }
+  if (!h->scratch_owned || h->scratch_owner == s) {
+    h->scratch_owned = true;
+    h->scratch_owner = s;
+    *out = Scratch{h->carry, h->split_part};
+    return cudaSuccess;
+  }
+  const size_t carry = (h->carry_bytes + 255) / 256 * 256;
+  const size_t need = carry + (size_t)h->split_nc * (h->dtype == SMAT_F64 ? 8 : 4);
+  smat_s::StreamScratch *hit = nullptr;
+  for (auto &e : h->more_scratch)
+    if (e.stream == s) hit = &e;
+  if (!hit || hit->bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return cudaErrorStreamCaptureUnsupported;
+    void *p = nullptr;
+    cudaError_t e = dev_alloc(&p, need > 0 ? need : 256);
+    if (e != cudaSuccess) return e;
+    if (hit) {
+      cudaStreamSynchronize(s);  // the old buffer's products on s are done
+      dev_free(hit->p);
+      hit->p = p;
+      hit->bytes = need;
+    } else {
+      h->more_scratch.push_back({s, p, need});
+      hit = &h->more_scratch.back();
+    }
+  }
+  *out = Scratch{hit->p, (char *)hit->p + carry};
+  return cudaSuccess;
+}
+
+void free_stream_scratch(smat_s *h) {
+  for (auto &e : h->more_scratch) dev_free(e.p);
+  h->more_scratch.clear();
+}
+
+namespace {
+
 smat_status_t ensure_scratch(smat_s *h, int variant) {
   size_t need = carry_bytes_needed(h, variant);
   if (need <= h->carry_bytes) return SMAT_OK;
@@ -643,10 +690,10 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     smat_status_t ps = prepare_variant(h, v, s);
     if (ps == SMAT_ERR_UNSUPPORTED || ps == SMAT_ERR_ALLOC) continue;  // skip, keep searching
     TRYS(ps);
-    for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s));
+    for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
     for (int r = 0; r < reps; ++r) {
       TRY(cudaEventRecord(ev[2 * r], s));
-      TRY(launch_spmv(h, v, a, x.p, b, y.p, s));
+      TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
       TRY(cudaEventRecord(ev[2 * r + 1], s));
     }
     TRY(cudaStreamSynchronize(s));
@@ -810,6 +857,7 @@ smat_status_t smat_destroy(smat_handle_t h) {
   free_format(h, SMAT_FMT_ELL); free_format(h, SMAT_FMT_DIA); free_format(h, SMAT_FMT_COO);
   free_ext_layouts(h);
   dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y); dev_free(h->merge_coords);
+  free_stream_scratch(h);
   delete h;
   return SMAT_OK;
 }

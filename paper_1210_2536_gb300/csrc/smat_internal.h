@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "smat.h"
@@ -116,6 +117,18 @@ struct smat_s {
   // scratch for merge-path and COO carries
   void *carry = nullptr;
   size_t carry_bytes = 0;
+  // The buffers above serve the first stream that runs products on the
+  // handle; every further stream gets scratch of its own on its first product
+  // there, so products on different streams never share carries.
+  struct StreamScratch {
+    cudaStream_t stream;
+    void *p;
+    size_t bytes;
+  };
+  mutable std::mutex scratch_mu;
+  mutable bool scratch_owned = false;
+  mutable cudaStream_t scratch_owner = nullptr;
+  mutable std::vector<StreamScratch> more_scratch;
 
   // host-buffer staging for smat_spmv_host
   void *stage_x = nullptr, *stage_y = nullptr;
@@ -175,6 +188,18 @@ cudaError_t launch_spmv_ext(const smat_s *h, int variant, const void *alpha, con
 long long merge_tiles(long long m, long long nnz);
 cudaError_t launch_merge_partition(const int32_t *rowptr, long long m, long long nnz, void *coords,
                                    cudaStream_t s);
+// Per-product scratch: carries (merge-path, COO, HYB and SPLIT tails) and
+// SPLIT's chunk sums.
+struct Scratch {
+  void *carry;
+  void *part;
+};
+// The scratch a product on stream s uses (see smat_s::more_scratch); a stream
+// that is capturing a graph and has none yet gets cudaErrorStreamCaptureUnsupported.
+// claim = false (the tuner's own products, which never overlap other calls)
+// uses the handle's buffers without making s their owner.
+cudaError_t stream_scratch(const smat_s *h, cudaStream_t s, Scratch *out, bool claim = true);
+void free_stream_scratch(smat_s *h);
 // Size in bytes of the carry scratch a variant needs (0 if none).
 size_t carry_bytes_needed(const smat_s *h, int variant);
 // Kernel launches one product through `variant` issues.
@@ -187,8 +212,9 @@ int batch_width_candidates(const smat_s *h, int variant, int out[2]);
 cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, const void *alpha, const void *x,
                               const void *beta, void *y, cudaStream_t s);
 // SpMV through one variant; alpha/beta are host scalars of the compute type.
+// claim: as in stream_scratch (false for the tuner's timing products).
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,
-                        const void *beta, void *y, cudaStream_t s);
+                        const void *beta, void *y, cudaStream_t s, bool claim = true);
 
 // MLP forward over standardised inputs (device), used by the selector.
 cudaError_t launch_mlp_forward(const float *params, const float *X, int B, float *logits,

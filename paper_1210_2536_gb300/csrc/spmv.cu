@@ -594,11 +594,11 @@ constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 // A COO product over (row, col, val) of length nnz, then the carry fix-up.
 template <typename V, typename T, int MODE>
-cudaError_t launch_coo(const smat_s *h, const int32_t *row, const int32_t *col, const V *val, const T *x,
+cudaError_t launch_coo(const Scratch &sc, const int32_t *row, const int32_t *col, const V *val, const T *x,
                        const Epi<T, MODE> &ep, T *y, long long nnz, cudaStream_t s) {
   const long long tiles = (nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-  int32_t *crow = (int32_t *)h->carry;
-  T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+  int32_t *crow = (int32_t *)sc.carry;
+  T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
   coo_kernel<V, T, COO_NT, COO_CH, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(row, col, val, x, ep, y, nnz, crow, cval);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -664,7 +664,7 @@ void launch_ell_dia(const smat_s *h, const typename Compute<V>::T *x, const Epi<
 }
 
 template <typename V, int MODE>
-cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha, const void *x_p,
+cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename Compute<V>::T alpha, const void *x_p,
                       typename Compute<V>::T beta, void *y_p, cudaStream_t s, int u_req, int lane_req) {
   typedef typename Compute<V>::T T;
   const Epi<T, MODE> ep{alpha, beta};
@@ -692,8 +692,8 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       break;
     case SMAT_V_CSR_MERGE: {
       long long tiles = (m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
-      int32_t *crow = (int32_t *)h->carry;
-      T *cval = (T *)((char *)h->carry + ((tiles * 4 + 15) / 16) * 16);
+      int32_t *crow = (int32_t *)sc.carry;
+      T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
       csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
           h->rowptr, h->colidx, val, x, ep, y, m, h->nnz, (const int2 *)h->merge_coords, crow, cval);
       cudaError_t e = cudaGetLastError();
@@ -715,7 +715,7 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
         if (e != cudaSuccess) return e;
       }
       if (h->nnz == 0) break;
-      return launch_coo<V, T, MODE>(h, h->coo_row, h->colidx, val, x, ep, y, h->nnz, s);
+      return launch_coo<V, T, MODE>(sc, h->coo_row, h->colidx, val, x, ep, y, h->nnz, s);
     }
     case SMAT_V_HYB: {
       // the ELL part writes every row (y = alpha*part + beta*y), then the COO
@@ -725,7 +725,7 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess || h->hyb_ncoo == 0) return e;
       const Epi<T, EPI_AXPBY> add{alpha, (T)1};
-      return launch_coo<V, T, EPI_AXPBY>(h, h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y,
+      return launch_coo<V, T, EPI_AXPBY>(sc, h->hyb_crow, h->hyb_ccol, (const V *)h->hyb_cval, x, add, y,
                                          h->hyb_ncoo, s);
     }
     case SMAT_V_SPLIT: {
@@ -738,16 +738,16 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
       if (h->split_nc > 0) {
         const long long nc = h->split_nc;
         split_chunk_kernel<V, T><<<(unsigned)std::min<long long>(nc, 1LL << 30), 256, 0, s>>>(
-            h->split_cstart, h->split_cend, h->colidx, val, x, (T *)h->split_part, nc);
+            h->split_cstart, h->split_cend, h->colidx, val, x, (T *)sc.part, nc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         split_rows_kernel<T, MODE><<<grid_for(h->split_nl, 256, 152 * 8), 256, 0, s>>>(
-            h->split_lrows, h->split_lchunk, (const T *)h->split_part, h->split_nl, ep, y);
+            h->split_lrows, h->split_lchunk, (const T *)sc.part, h->split_nl, ep, y);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
       if (h->split_ns > 0)
-        return launch_coo<V, T, MODE>(h, h->split_srow, h->split_scol, (const V *)h->split_sval, x, ep, y,
+        return launch_coo<V, T, MODE>(sc, h->split_srow, h->split_scol, (const V *)h->split_sval, x, ep, y,
                                       h->split_ns, s);
     } break;
     default:
@@ -757,15 +757,15 @@ cudaError_t spmv_mode(const smat_s *h, int variant, typename Compute<V>::T alpha
 }
 
 template <typename V>
-cudaError_t spmv_typed(const smat_s *h, int variant, const void *alpha_p, const void *x_p, const void *beta_p,
-                       void *y_p, cudaStream_t s, int u_req, int lane_req) {
+cudaError_t spmv_typed(const smat_s *h, const Scratch &sc, int variant, const void *alpha_p, const void *x_p,
+                       const void *beta_p, void *y_p, cudaStream_t s, int u_req, int lane_req) {
   typedef typename Compute<V>::T T;
   const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
   if (h->m == 0) return cudaSuccess;
   switch (epi_mode((double)alpha, (double)beta)) {
-    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
-    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
-    default: return spmv_mode<V, EPI_AXPBY>(h, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
+    case EPI_COPY: return spmv_mode<V, EPI_COPY>(h, sc, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
+    case EPI_SCALE: return spmv_mode<V, EPI_SCALE>(h, sc, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
+    default: return spmv_mode<V, EPI_AXPBY>(h, sc, variant, alpha, x_p, beta, y_p, s, u_req, lane_req);
   }
 }
 
@@ -815,7 +815,7 @@ int spmv_launch_count(const smat_s *h, int variant) {
 }
 
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
-                        void *y, cudaStream_t s) {
+                        void *y, cudaStream_t s, bool claim) {
   // ELL, DIA and HYB read x and write y, and BCSR reads x, with vector
   // accesses of up to 16 bytes; vectors that are not 16-byte aligned take the
   // CSR-scalar kernel instead.
@@ -823,10 +823,15 @@ cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const v
       (((uintptr_t)x | (uintptr_t)y) & 15u) != 0)
     variant = SMAT_V_CSR_SCALAR;
   if (variant == SMAT_V_SELL || variant == SMAT_V_BCSR) return launch_spmv_ext(h, variant, alpha, x, beta, y, s);
+  Scratch sc{nullptr, nullptr};
+  if (carry_bytes_needed(h, variant) > 0 || variant == SMAT_V_SPLIT) {
+    cudaError_t e = stream_scratch(h, s, &sc, claim);
+    if (e != cudaSuccess) return e;
+  }
   switch (h->dtype) {
-    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, 0, -1);
-    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, 0, -1);
-    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, 0, -1);
+    case SMAT_F64: return spmv_typed<double>(h, sc, variant, alpha, x, beta, y, s, 0, -1);
+    case SMAT_F32: return spmv_typed<float>(h, sc, variant, alpha, x, beta, y, s, 0, -1);
+    default: return spmv_typed<__nv_bfloat16>(h, sc, variant, alpha, x, beta, y, s, 0, -1);
   }
 }
 
@@ -840,10 +845,11 @@ int batch_width_candidates(const smat_s *h, int variant, int out[2]) {
 
 cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, const void *alpha, const void *x,
                               const void *beta, void *y, cudaStream_t s) {
+  const Scratch none{nullptr, nullptr};  // ELL / DIA use no scratch
   switch (h->dtype) {
-    case SMAT_F64: return spmv_typed<double>(h, variant, alpha, x, beta, y, s, u, lane);
-    case SMAT_F32: return spmv_typed<float>(h, variant, alpha, x, beta, y, s, u, lane);
-    default: return spmv_typed<__nv_bfloat16>(h, variant, alpha, x, beta, y, s, u, lane);
+    case SMAT_F64: return spmv_typed<double>(h, none, variant, alpha, x, beta, y, s, u, lane);
+    case SMAT_F32: return spmv_typed<float>(h, none, variant, alpha, x, beta, y, s, u, lane);
+    default: return spmv_typed<__nv_bfloat16>(h, none, variant, alpha, x, beta, y, s, u, lane);
   }
 }
 

@@ -118,3 +118,29 @@ def test_full_size_bench_workload_parity(dtype):
             assert f[k] == fo[k], (A.name, k)
         M.close()
     smat.smat_set_model(None, None, None)
+
+
+def test_concurrent_products_on_one_handle():
+    # products on one handle from two streams at once: the plans that carry
+    # partial sums between CTAs (merge-path, COO, HYB, SPLIT) give each stream
+    # scratch of its own, so every product is the oracle's
+    A = synth.powerlaw(150000, 1.8, 5000, 3)
+    M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
+                      torch.from_numpy(A.val).to(DEV), "f64")
+    xs = [synth.uniform(70 + k, 1, A.n) for k in range(2)]
+    refs = [reference(A, A.val, x, 1.0, 0.0, None) for x in xs]
+    xd = [torch.from_numpy(x).to(DEV) for x in xs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for v in (smat.SMAT_V_COO, smat.SMAT_V_CSR_MERGE, smat.SMAT_V_HYB, smat.SMAT_V_SPLIT):
+        M.spmv(xd[0], variant=v)          # builds the format
+        torch.cuda.synchronize()
+        ys = [[torch.empty(A.m, dtype=torch.float64, device=DEV) for _ in range(6)] for _ in range(2)]
+        for r in range(6):
+            for k in range(2):
+                M.spmv(xd[k], ys[k][r], variant=v, stream=streams[k])
+        torch.cuda.synchronize()
+        for k in range(2):
+            ref, scale = refs[k]
+            for r in range(6):
+                assert_close_rows(ys[k][r].cpu().numpy(), ref, scale, TOL["f64"], f"{smat.VARIANT_NAMES[v]} s{k} r{r}")
+    M.close()
