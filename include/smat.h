@@ -23,7 +23,8 @@
  *     SMAT_BF16 store values in FP32 / bfloat16 and compute with FP32
  *     accumulation, FP32 x and y, FP32 alpha and beta.
  *   - alpha and beta are HOST pointers to one scalar of the compute type.
- *     beta == 0 means y is only written (NaN in y is ignored, as in BLAS).
+ *     beta == 0 means y is only written (NaN in y is ignored, as in BLAS);
+ *     alpha == 0 gives y = beta*y (0 when beta == 0) without reading A or x.
  *
  * Thread safety: calls on different handles are independent.  Products
  * (smat_spmv, smat_spmv_variant) on one handle may run concurrently from

@@ -814,8 +814,27 @@ int spmv_launch_count(const smat_s *h, int variant) {
   return 1;
 }
 
+// alpha == 0: y = beta*y (0 when beta == 0) without reading A or x, so that
+// non-finite values in x cannot reach y (the BLAS convention).
+template <typename T>
+__global__ void beta_only_kernel(T *__restrict__ y, long long m, T beta) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mul_rn(beta, y[i]);
+}
+
+template <typename T>
+cudaError_t beta_only(const smat_s *h, const void *beta_p, void *y, cudaStream_t s) {
+  const T beta = *(const T *)beta_p;
+  if (h->m == 0) return cudaSuccess;
+  if (beta == (T)0) return cudaMemsetAsync(y, 0, (size_t)h->m * sizeof(T), s);
+  beta_only_kernel<T><<<grid_for(h->m, 256, 152 * 8), 256, 0, s>>>((T *)y, h->m, beta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x, const void *beta,
                         void *y, cudaStream_t s, bool claim) {
+  if (h->dtype == SMAT_F64 ? *(const double *)alpha == 0.0 : *(const float *)alpha == 0.0f)
+    return h->dtype == SMAT_F64 ? beta_only<double>(h, beta, y, s) : beta_only<float>(h, beta, y, s);
   // ELL, DIA and HYB read x and write y, and BCSR reads x, with vector
   // accesses of up to 16 bytes; vectors that are not 16-byte aligned take the
   // CSR-scalar kernel instead.

@@ -253,3 +253,28 @@ def test_coo_full_and_partial_tiles(dtype):
         assert np.array_equal(outs[0], outs[1]), A.name
         assert A.nnz % 2048 != 0   # a partial last tile is part of the case
         M.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_alpha_zero_reads_neither_matrix_nor_x(dtype):
+    # alpha = 0: y = beta*y (0 when beta = 0) in every variant, even with NaN
+    # and Inf in x (the BLAS convention: A and x are not referenced)
+    A = synth.powerlaw(20000, 1.8, 3000, 4)
+    M, _ = make(A, dtype)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    x = synth.uniform(0, 1, A.n).astype(npdt)
+    x[::7] = np.nan
+    x[3::11] = np.inf
+    y0 = synth.uniform(1, 1, A.m).astype(npdt)
+    xd = torch.from_numpy(x).to(DEV)
+    for v in list(range(smat.SMAT_NUM_VARIANTS)) + [smat.SMAT_V_HYB, smat.SMAT_V_SPLIT]:
+        for beta in (0.0, -0.75):
+            y = torch.from_numpy(y0.copy()).to(DEV)
+            try:
+                M.spmv(xd, y, 0.0, beta, variant=v)
+            except smat.SmatError:
+                continue
+            torch.cuda.synchronize()
+            want = (np.float64(beta) * y0.astype(np.float64)).astype(npdt) if beta else np.zeros_like(y0)
+            assert np.array_equal(y.cpu().numpy(), want), (smat.VARIANT_NAMES[v], beta)
+    M.close()
