@@ -139,6 +139,26 @@ def dram_traffic_record(kernel_key):
     return None
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(mats, xs, dtypes, seconds):
     """The oracle (threaded, nonzero-balanced rows, FP64 accumulation) timed
     on this host's cores over passes of the same products."""
@@ -167,6 +187,7 @@ def cpu_baseline(mats, xs, dtypes, seconds):
     st = time.perf_counter() - t1
     sflops = flops
     return {"value": round(flops * passes / dt / 1e9, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{passes} full passes over the {len(prods)} products (all rows), FP64 accumulation, "
                       f"{threads} threads, {dt:.1f} s",
             "serial_1core": {"value": round(sflops / st / 1e9, 3), "unit": UNIT,
@@ -223,7 +244,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "scale": args.scale},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
