@@ -4,6 +4,7 @@ see roofline.py).  Used for kernel studies and profiler captures:
 
   python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --dtype f64 --variant all
   python -m paper_1210_2536_gb300.spmv_case --matrix powerlaw:2000000 --variant coo --reps 3
+  python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --variant dia --cold
 
 Matrices: stencil2d5:<m>, stencil3d7:<m>, stencil3d27:<m>, uniform:<n>[:lambda],
 powerlaw:<n>[:alpha], blockdiag:<n>[:b].
@@ -48,6 +49,9 @@ def main():
     ap.add_argument("--variant", default="all")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--cold", action="store_true",
+                    help="write a buffer of twice the L2 size between timed repetitions (x and the matrix "
+                         "start from HBM)")
     a = ap.parse_args()
     A = make_matrix(a.matrix)
     from . import synth
@@ -73,7 +77,12 @@ def main():
     names = smat.VARIANT_NAMES
     vs = [v for v in range(8) if (f["admissible"] >> v) & 1] + [9, 10, 11, 12] if a.variant == "all" \
         else [names.index(a.variant)]
-    out = {"matrix": A.name, "m": A.m, "nnz": A.nnz, "dtype": a.dtype, "variants": {}}
+    out = {"matrix": A.name, "m": A.m, "nnz": A.nnz, "dtype": a.dtype, "cache": "cold" if a.cold else "warm-x",
+           "variants": {}}
+    flush = None
+    if a.cold:
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        flush = torch.empty(2 * l2 // 4, dtype=torch.int32, device=dev)
     for v in vs:
         try:
             M.spmv(x, y, variant=v)   # builds the format; further formats may not be admissible
@@ -84,6 +93,8 @@ def main():
             M.spmv(x, y, variant=v)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
         for s, e in ev:
+            if flush is not None:
+                flush.fill_(1)
             s.record()
             M.spmv(x, y, variant=v)
             e.record()
