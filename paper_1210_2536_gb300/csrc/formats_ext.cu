@@ -1,8 +1,10 @@
 // Further GPU storage formats: HYB (Bell & Garland, 2009), SELL-C-sigma
-// (Kreutzer, Hager, Wellein, Fehske & Bishop, 2014) and BCSR with b x b
-// blocks (register blocking, Im & Yelick).  arXiv 1210.2536 works with DIA,
-// ELL, CSR and COO (Sec. 2.1) and leaves more formats to future work
-// (Sec. 8); these three join the same execute-and-measure search (Sec. 6).
+// (Kreutzer, Hager, Wellein, Fehske & Bishop, 2014), BCSR with b x b blocks
+// (register blocking, Im & Yelick) and SPLIT (long rows in chunks, the rest as
+// COO).  arXiv 1210.2536 works with DIA, ELL, CSR and COO (Sec. 2.1) and leaves
+// more formats to future work (Sec. 8); these join the same execute-and-measure
+// search (Sec. 6).  This file holds their conversions and the SELL and BCSR
+// kernels; HYB and SPLIT run through kernels of spmv.cu.
 //
 // Layouts (the oracle builds the same arrays element for element):
 //   HYB   ELL part ecol/eval[s*P + i] for s < K (slots past a row's length:

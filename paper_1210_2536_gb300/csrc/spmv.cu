@@ -1,18 +1,22 @@
 // SpMV kernels y = alpha*A*x + beta*y for the four basic formats
 // (arXiv 1210.2536, Sec. 2.1; the paper's kernel library maps each format to
-// its best implementation, Sec. 3).  GPU implementations of CSR follow Bell &
-// Garland (2008, cited by the paper: scalar and vector kernels) and Merrill &
-// Garland (2016: merge-path); COO uses a tiled segmented reduction.
+// its best implementation, Sec. 3), and the launches of the further formats
+// that reuse them (HYB: ELL + COO tail; SPLIT: long rows in CTA chunks + COO).
+// GPU implementations of CSR follow Bell & Garland (2008, cited by the paper:
+// scalar and vector kernels) and Merrill & Garland (2016: merge-path); COO uses
+// a tiled segmented reduction.
 //
-// All kernels are bound by HBM bandwidth: they stream the format's index and
-// value arrays once with coalesced (ELL, DIA: 16-byte vector) loads, gather x
-// through L1/L2, and write y once.  The alpha/beta epilogue is fused:
+// The kernels stream the format's index and value arrays once with coalesced
+// (ELL, DIA: 16-byte vector or lane-striped) loads, gather x through L1/L2 and
+// write y once.  They are bound by HBM, by the random x gathers, or (FP64) by
+// the FP64 pipe, which GB300 runs at about 2 operations per clock per SM: every
+// kernel spends one fused multiply-add per stored product, and only
+// SMAT_V_CSR_SCALAR_EXACT rounds products and sums separately, in ascending
+// column order, as the CSR definition does.  The alpha/beta epilogue is fused:
 //   y_i = alpha*acc            if beta == 0 (y is not read)
-//   y_i = alpha*acc + beta*y_i otherwise, each product rounded separately.
-// Storage V in {double, float, bf16}; compute T = double for V = double,
-// float otherwise.  For V = double the CSR-scalar, ELL and DIA kernels add
-// products one at a time in ascending column order with separately rounded
-// multiply and add, i.e. the same operations as the CSR definition.
+//   y_i = alpha*acc + beta*y_i otherwise
+// and alpha == 0 skips A and x altogether.  Storage V in {double, float,
+// bf16}; compute T = double for V = double, float otherwise.
 #include <cuda_bf16.h>
 
 #include <algorithm>
