@@ -391,6 +391,10 @@ def run_ours(args):
     dom_key = f"{dom['variant']}:{dom['dtype']}:{dom['matrix']}"
     rb = roof_bound(dp["f"], dp["plan"]["variant"], dp["dt"], dom["_d"] / 1e3, peak)
     traffic = dram_traffic_record(dom_key)
+    # random-column products are bound by x gathers before HBM: the measured
+    # gather rate of this GPU over the dominant product's own x and count
+    gather_peak = smat.smat_measure_gather_rate(dp["A"].n, dp["A"].nnz, dp["dt"], 20)
+    gather_frac = dp["A"].nnz / (dom["_d"] / 1e3) / gather_peak
     for r in per:
         r.pop("_d")
         r.pop("alg_bytes")
@@ -445,7 +449,8 @@ def run_ours(args):
                                        "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"),
                          "unit": rb["unit"], "frac": round(rb["frac"], 4), "traffic": traffic,
                          "alg_bytes_per_launch": rb["alg_bytes"], "hbm_frac": round(rb["hbm_frac"], 4),
-                         "fp64_frac": round(rb["fp64_frac"], 4) if "fp64_frac" in rb else None},
+                         "fp64_frac": round(rb["fp64_frac"], 4) if "fp64_frac" in rb else None,
+                         "gather_peak_gps": round(gather_peak / 1e9, 1), "gather_frac": round(gather_frac, 4)},
             "step_hbm_frac": round(sum(algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"]) for p in prods)
                                    / (ms / K / 1e3) / 1e9 / peak, 4),
             "gpu_launches": launches_per_step * K,

@@ -290,6 +290,19 @@ smat_status_t smat_format_dims(smat_handle_t h, smat_format_t fmt, int64_t dims[
  * Arrays are concatenated in the order listed.  Sizes as in smat_format_dims. */
 smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *idx, void *val);
 
+/* Measured ceiling for gather-bound products (no counterpart in the paper,
+ * which measures on CPUs): a kernel streams nidx int32 indices, uniform in
+ * [0, n), and gathers x[index] from an x of n elements of dtype's compute type
+ * (FP64, or FP32 for FP32 / BF16 storage), 8 per thread and nothing else.
+ * Runs 3 untimed and `reps` timed passes on the legacy default stream and
+ * writes the median rate in gathers per second.  SpMV on random columns
+ * (x resident in L2) cannot gather faster; the benchmark reports products'
+ * fraction of this rate beside their HBM fraction.  Allocates and frees its
+ * own device buffers (nidx*4 + n*8 + nidx bytes at most).  Errors:
+ * INVALID_ARG (n < 1, n > 2^31 - 1, nidx < 8, reps < 1), ALLOC, CUDA. */
+smat_status_t smat_measure_gather_rate(int64_t n, int64_t nidx, smat_dtype_t dtype, int32_t reps,
+                                       double *gathers_per_s);
+
 /* ------------------------------------------------------------------------ */
 /* Learned selector (replaces the ruleset classifier of Sec. 5)             */
 /* MLP 12 -> 64 -> ReLU -> 64 -> ReLU -> 8 over standardised features.       */

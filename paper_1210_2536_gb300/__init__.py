@@ -98,6 +98,7 @@ _SIGS = {
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
     "smat_get_plan": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "smat_get_timings": (ctypes.c_int, [_VP, _VP]),
+    "smat_measure_gather_rate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int32, _VP]),
     "smat_convert": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_format_dims": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_export_format": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
@@ -233,6 +234,13 @@ def smat_get_timings(h) -> np.ndarray:
 
 def smat_convert(h, fmt, stream=0):
     return lib().smat_convert(h, fmt, stream)
+
+
+def smat_measure_gather_rate(n: int, nidx: int, dtype: str = "f64", reps: int = 20) -> float:
+    """Random gathers per second this GPU serves from an x of n elements (see smat.h)."""
+    r = ctypes.c_double(0.0)
+    _check(lib().smat_measure_gather_rate(n, nidx, DTYPES[dtype], reps, ctypes.byref(r)), "smat_measure_gather_rate")
+    return float(r.value)
 
 
 def smat_format_dims(h, fmt):

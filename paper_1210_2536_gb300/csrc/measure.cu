@@ -1,0 +1,87 @@
+// A measured ceiling for gather-bound products.  SpMV with random column
+// indices (the uniform and power-law structures) is bound by the rate at
+// which the GPU serves independent random loads of x from L2, not by HBM
+// bandwidth.  This kernel streams an index array (int32, 16-byte loads) and
+// gathers x at those indices, 8 per thread, with nothing else to do: its rate
+// is the ceiling a product's gathers can reach on this GPU.  The paper has no
+// counterpart (it measures on CPUs); this is measurement support only.
+#include <algorithm>
+#include <vector>
+
+#include "smat_internal.h"
+
+namespace smat {
+namespace {
+
+// Indices uniform in [0, n): a 64-bit multiplicative hash of (seed, i).
+__global__ void gather_index_kernel(int32_t *__restrict__ idx, long long nidx, long long n, unsigned long long seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nidx; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i + seed * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    idx[i] = (int32_t)(z % (unsigned long long)n);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gather_rate_kernel(const int32_t *__restrict__ idx, const T *__restrict__ x,
+                                                          T *__restrict__ out, long long nthreads) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  const int4 a = __ldcs(reinterpret_cast<const int4 *>(idx) + 2 * t);
+  const int4 b = __ldcs(reinterpret_cast<const int4 *>(idx) + 2 * t + 1);
+  out[t] = __ldg(x + a.x) + __ldg(x + a.y) + __ldg(x + a.z) + __ldg(x + a.w) + __ldg(x + b.x) + __ldg(x + b.y) +
+           __ldg(x + b.z) + __ldg(x + b.w);
+}
+
+template <typename T>
+cudaError_t run_gather(long long n, long long nidx, int reps, double *rate) {
+  void *pi = nullptr, *px = nullptr, *po = nullptr;
+  const long long nt = nidx / 8;
+  cudaError_t e = dev_alloc(&pi, (size_t)nidx * 4);
+  if (e == cudaSuccess) e = dev_alloc(&px, (size_t)n * sizeof(T));
+  if (e == cudaSuccess) e = dev_alloc(&po, (size_t)nt * sizeof(T));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<float> ms;
+  if (e == cudaSuccess) {
+    gather_index_kernel<<<1216, 256>>>((int32_t *)pi, nidx, n, 12345ull);
+    e = cudaMemset(px, 0, (size_t)n * sizeof(T));
+  }
+  const unsigned grid = (unsigned)((nt + 255) / 256);
+  for (int r = -3; r < reps && e == cudaSuccess; ++r) {  // three untimed passes first
+    cudaEventRecord(e0);
+    gather_rate_kernel<T><<<grid, 256>>>((const int32_t *)pi, (const T *)px, (T *)po, nt);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && r >= 0) ms.push_back(t);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dev_free(pi); dev_free(px); dev_free(po);
+  if (e != cudaSuccess) return e;
+  std::sort(ms.begin(), ms.end());
+  *rate = (double)(nt * 8) / (ms[ms.size() / 2] * 1e-3);
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace smat
+
+extern "C" smat_status_t smat_measure_gather_rate(int64_t n, int64_t nidx, smat_dtype_t dtype, int32_t reps,
+                                                  double *gathers_per_s) {
+  if (!gathers_per_s || n < 1 || n > INT32_MAX || nidx < 8 || reps < 1) return SMAT_ERR_INVALID_ARG;
+  if (dtype != SMAT_F64 && dtype != SMAT_F32 && dtype != SMAT_BF16) return SMAT_ERR_INVALID_ARG;
+  nidx = nidx / 8 * 8;
+  const cudaError_t e = dtype == SMAT_F64 ? smat::run_gather<double>(n, nidx, reps, gathers_per_s)
+                                          : smat::run_gather<float>(n, nidx, reps, gathers_per_s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SMAT_ERR_ALLOC;
+  }
+  return e == cudaSuccess ? SMAT_OK : SMAT_ERR_CUDA;
+}

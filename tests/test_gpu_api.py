@@ -160,3 +160,13 @@ def test_exhaustive_pick_is_stable_when_retimed():
         best = min(v for v in t if v > 0)
         assert t[first] <= 1.15 * best, (A.name, smat.VARIANT_NAMES[first], t[first], best)
         M.close()
+
+
+def test_gather_rate_measurement():
+    # the gather ceiling: positive, and no faster for FP64 than for FP32 x
+    r64 = smat.smat_measure_gather_rate(2_000_000, 4_000_000, "f64", 5)
+    r32 = smat.smat_measure_gather_rate(2_000_000, 4_000_000, "f32", 5)
+    assert 1e9 < r64 < 1e13 and 1e9 < r32 < 1e13
+    assert r64 <= 1.5 * r32
+    with pytest.raises(smat.SmatError):
+        smat.smat_measure_gather_rate(0, 100, "f64", 5)
