@@ -280,8 +280,23 @@ __device__ __forceinline__ void dia_group(const int32_t *off, int nd, const V *_
       }
       if (FAST && live && j0 >= 0 && j0 + R <= n) {  // the whole window inside x: no per-row checks
         const T *xp = x + j0;
+        if constexpr (sizeof(T) == 4 && R % 4 == 0) {
+          // i0 is a multiple of R, so the window is 16-byte aligned exactly when
+          // the diagonal's offset is a multiple of 4 (uniform over the warp)
+          if ((j0 & 3) == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) xv[u][r] = __ldg(xp + r);
+            for (int q = 0; q < R / 4; ++q) {
+              const float4 f = __ldg(reinterpret_cast<const float4 *>(xp) + q);
+              xv[u][4 * q] = f.x; xv[u][4 * q + 1] = f.y; xv[u][4 * q + 2] = f.z; xv[u][4 * q + 3] = f.w;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) xv[u][r] = __ldg(xp + r);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) xv[u][r] = __ldg(xp + r);
+        }
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) xv[u][r] = (live && j0 + r >= 0 && j0 + r < n) ? __ldg(x + j0 + r) : (T)0;
