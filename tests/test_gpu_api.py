@@ -147,7 +147,7 @@ def test_concurrent_products_on_one_handle():
 
 
 def test_exhaustive_pick_is_stable_when_retimed():
-    # the exhaustive search is its own judge: a second, independent search
+    # the exhaustive search checks itself: a second, independent search
     # finds the first search's pick within 15 % of its own fastest variant (timing noise of
     # ~20 us launches included)
     for A in (synth.stencil3d7(96), synth.powerlaw(300000, 1.8, 5000, 2), synth.uniform_random(300000, 16.0, 3)):
