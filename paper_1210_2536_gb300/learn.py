@@ -4,7 +4,7 @@ timings, train the MLP on the GPU with libsmat's own kernels, and evaluate it
 on held-out matrices against the exhaustive search (regret) and against the
 paper's rules.
 
-  python -m paper_1210_2536_gb300.learn label --out ds.jsonl [--count 2000]
+  python -m paper_1210_2536_gb300.learn label --out ds.jsonl [--count 2400]
   python -m paper_1210_2536_gb300.learn train --data ds.jsonl --model m.bin --report r.json
 
 Dataset line (JSON): id, kind, params, m, n, nnz, features (12 selector
@@ -51,7 +51,7 @@ def _generate_pinned(kind, params, seed, torch):
     return m, n, nnz, rp, col, val
 
 
-def label(out_path, count=2000, start=0, reps=7, budget_ms=20000.0, log_every=50):
+def label(out_path, count=synth.DATASET_SIZE, start=0, reps=7, budget_ms=20000.0, log_every=50):
     import torch
 
     import paper_1210_2536_gb300 as smat
@@ -252,7 +252,7 @@ def main():
     sub = ap.add_subparsers(dest="cmd", required=True)
     a = sub.add_parser("label")
     a.add_argument("--out", required=True)
-    a.add_argument("--count", type=int, default=2000)
+    a.add_argument("--count", type=int, default=synth.DATASET_SIZE)
     a.add_argument("--start", type=int, default=0)
     a.add_argument("--reps", type=int, default=7)
     t = sub.add_parser("train")
@@ -279,6 +279,15 @@ def main():
            "train_seconds": train_s, "loss_first": hist[0], "loss_last": hist[-1],
            "train": evaluate(predict(params, mean, std, tr), tr),
            "heldout": evaluate(predict(params, mean, std, he), he)}
+    # the six primary structure classes alone, and each class on its own
+    prim = [r for r in he if r["id"] < synth.DATASET_PRIMARY]
+    rep["heldout_primary"] = evaluate(predict(params, mean, std, prim), prim)
+    rep["heldout_by_kind"] = {}
+    for kind in sorted({r["kind"] for r in he}):
+        sub = [r for r in he if r["kind"] == kind]
+        ev = evaluate(predict(params, mean, std, sub), sub)
+        rep["heldout_by_kind"][kind] = {"n": ev["n"], "mlp": ev["mlp"], "mlp_with_fallback": ev["mlp_with_fallback"],
+                                        "rules": ev["rules"]}
     json.dump(rep, open(args.report, "w"), indent=1)
     h = rep["heldout"]
     print(json.dumps({k: h[k] for k in ("mlp", "mlp_with_fallback", "rules", "always_csr_scalar", "fallback_rate")},

@@ -22,8 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
 _LIB = os.path.join(_HERE, "libsmatsynth.so")
 
-STENCIL2D5, STENCIL3D7, STENCIL3D27, UNIFORM, POWERLAW, BLOCKDIAG = range(6)
-KIND_NAMES = ["stencil2d5", "stencil3d7", "stencil3d27", "uniform", "powerlaw", "blockdiag"]
+STENCIL2D5, STENCIL3D7, STENCIL3D27, UNIFORM, POWERLAW, BLOCKDIAG, BOX3D = range(7)
+KIND_NAMES = ["stencil2d5", "stencil3d7", "stencil3d27", "uniform", "powerlaw", "blockdiag", "box3d"]
 
 
 def build(force: bool = False) -> str:
@@ -163,6 +163,13 @@ def blockdiag(n: int, b: int = 8, seed: int = 0) -> CSR:
     return generate(BLOCKDIAG, [n, b], seed, name=f"blockdiag_{n}_b{b}")
 
 
+def box3d(m: int, r: int = 2) -> CSR:
+    """The (2r+1)^3-point box stencil on an m^3 grid (r = 1: the 27-point
+    stencil), rows truncated at the grid's boundary: the shape of the Galerkin
+    operators on coarse multigrid levels, whose stencils widen level by level."""
+    return generate(BOX3D, [m, r], 0, name=f"box3d_{m}^3_r{r}")
+
+
 # ---------------------------------------------------------------------------
 # Workload recipes (sizes of the paper-shaped synthetic workloads)
 # ---------------------------------------------------------------------------
@@ -190,14 +197,30 @@ def _meta_uniforms(matrix_id: int, count: int) -> np.ndarray:
     return uniform(0x5EED0000 + matrix_id, 7, count, 0.0, 1.0)
 
 
+# The labelled set: matrices 0 .. DATASET_PRIMARY-1 over the six structure
+# classes above, then DATASET_SIZE - DATASET_PRIMARY box stencils, which cover
+# the banded operators with hundreds to thousands of entries per row on small
+# grids that coarse multigrid levels produce (none of the six classes has
+# that shape, and a selector trained without it mispicks there).
+DATASET_PRIMARY = 2000
+DATASET_SIZE = 2400
+
+
 def dataset_spec(matrix_id: int, n_lo: float = 1e3, n_hi: float = 4e6, nnz_lo: float = 1e4,
                  nnz_hi: float = 5e7):
     """Generator kind and parameters of matrix ``matrix_id`` of the labelled
-    training/held-out set: the kind is uniform over the six structures
-    (block diagonal with b in {2,4,8,16}), n log-uniform on [n_lo, n_hi] and the
-    target nnz log-uniform on [nnz_lo, nnz_hi], clipped to what the kind can
-    realise at that n.  Returns (kind, params, seed)."""
+    training/held-out set.  Below DATASET_PRIMARY the kind is uniform over the
+    six structures (block diagonal with b in {2,4,8,16}), n log-uniform on
+    [n_lo, n_hi] and the target nnz log-uniform on [nnz_lo, nnz_hi], clipped to
+    what the kind can realise at that n.  From DATASET_PRIMARY on: box stencils
+    of radius r uniform in 2..6 on m^3 grids, n = m^3 log-uniform on
+    [512, min(n_hi, nnz_hi / (2r+1)^3)].  Returns (kind, params, seed)."""
     u = _meta_uniforms(matrix_id, 4)
+    if matrix_id >= DATASET_PRIMARY:
+        r = 2 + min(4, int(u[0] * 5))
+        hi = min(n_hi, nnz_hi / float((2 * r + 1) ** 3))
+        n = math.exp(math.log(512.0) + u[1] * (math.log(hi) - math.log(512.0)))
+        return BOX3D, [max(8, int(round(n ** (1.0 / 3.0)))), r], matrix_id
     kind = min(5, int(u[0] * 6))
     n = int(round(math.exp(math.log(n_lo) + u[1] * (math.log(n_hi) - math.log(n_lo)))))
     target = math.exp(math.log(nnz_lo) + u[2] * (math.log(nnz_hi) - math.log(nnz_lo)))

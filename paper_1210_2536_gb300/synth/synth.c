@@ -88,11 +88,15 @@ static int64_t uint_below(uint32_t a, uint32_t b, int64_t n) {
 /*   SYN_UNIFORM      p0 = n, p1 = lambda     Poisson(lambda) row lengths    */
 /*   SYN_POWERLAW     p0 = n, p1 = alpha, p2 = kmax   Zipf(alpha) on [1,kmax] */
 /*   SYN_BLOCKDIAG    p0 = n, p1 = b          dense b x b diagonal blocks    */
+/*   SYN_BOX3D        p0 = m, p1 = r          (2r+1)^3-point box stencil on  */
+/*                    an m^3 grid, values (2r+1)^3-1 / -1 (r = 1 is the      */
+/*                    27-point stencil); the wide operators of coarse        */
+/*                    multigrid levels                                       */
 /* Random kinds draw columns uniformly without replacement and N(0,1) values. */
 /* Stencils use natural (x fastest) ordering and Dirichlet boundaries.       */
 /* ------------------------------------------------------------------------ */
 enum { SYN_STENCIL2D5 = 0, SYN_STENCIL3D7 = 1, SYN_STENCIL3D27 = 2,
-       SYN_UNIFORM = 3, SYN_POWERLAW = 4, SYN_BLOCKDIAG = 5 };
+       SYN_UNIFORM = 3, SYN_POWERLAW = 4, SYN_BLOCKDIAG = 5, SYN_BOX3D = 6 };
 
 typedef struct {
   int kind;
@@ -114,7 +118,8 @@ int64_t synth_dims(int kind, const double *p, int64_t *n_rows, int64_t *n_cols) 
   switch (kind) {
     case SYN_STENCIL2D5: r = (int64_t)p[0] * (int64_t)p[1]; break;
     case SYN_STENCIL3D7:
-    case SYN_STENCIL3D27: { int64_t m = (int64_t)p[0]; r = m * m * m; } break;
+    case SYN_STENCIL3D27:
+    case SYN_BOX3D: { int64_t m = (int64_t)p[0]; r = m * m * m; } break;
     case SYN_UNIFORM:
     case SYN_POWERLAW:
     case SYN_BLOCKDIAG: r = (int64_t)p[0]; break;
@@ -153,6 +158,12 @@ static void gauss_pair(uint32_t w[4], double *z0, double *z1) {
   *z1 = r * sin(t);
 }
 
+/* Grid points within r of coordinate c on a line of m points. */
+static int64_t box_span(int64_t c, int64_t m, int64_t r) {
+  int64_t lo = c - r < 0 ? 0 : c - r, hi = c + r > m - 1 ? m - 1 : c + r;
+  return hi - lo + 1;
+}
+
 static int64_t stencil_len(int kind, const double *p, int64_t i) {
   if (kind == SYN_STENCIL2D5) {
     int64_t mx = (int64_t)p[0], my = (int64_t)p[1];
@@ -161,6 +172,11 @@ static int64_t stencil_len(int kind, const double *p, int64_t i) {
   }
   int64_t m = (int64_t)p[0];
   int64_t ix = i % m, iy = (i / m) % m, iz = i / (m * m);
+  if (kind == SYN_BOX3D) {
+    int64_t r = (int64_t)p[1];
+    int64_t nx = box_span(ix, m, r), ny = box_span(iy, m, r), nz = box_span(iz, m, r);
+    return nx * ny * nz;
+  }
   if (kind == SYN_STENCIL3D7)
     return 1 + (ix > 0) + (ix < m - 1) + (iy > 0) + (iy < m - 1) + (iz > 0) + (iz < m - 1);
   int64_t nx = 1 + (ix > 0) + (ix < m - 1), ny = 1 + (iy > 0) + (iy < m - 1),
@@ -192,14 +208,18 @@ static void stencil_fill(int kind, const double *p, int64_t i, int32_t *col, dou
     if (iz < m - 1) { col[k] = (int32_t)(i + m2); val[k++] = -1.0; }
     return;
   }
-  for (int dz = -1; dz <= 1; ++dz) {
+  /* 27-point (r = 1) and box stencils: every grid point within r in each
+     coordinate, in ascending column order */
+  const int64_t r = kind == SYN_BOX3D ? (int64_t)p[1] : 1;
+  const double centre = (double)((2 * r + 1) * (2 * r + 1) * (2 * r + 1) - 1);
+  for (int64_t dz = -r; dz <= r; ++dz) {
     if (iz + dz < 0 || iz + dz >= m) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
+    for (int64_t dy = -r; dy <= r; ++dy) {
       if (iy + dy < 0 || iy + dy >= m) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
+      for (int64_t dx = -r; dx <= r; ++dx) {
         if (ix + dx < 0 || ix + dx >= m) continue;
         col[k] = (int32_t)(i + dz * m2 + dy * m + dx);
-        val[k++] = (dx == 0 && dy == 0 && dz == 0) ? 26.0 : -1.0;
+        val[k++] = (dx == 0 && dy == 0 && dz == 0) ? centre : -1.0;
       }
     }
   }
@@ -261,7 +281,8 @@ static void *rowlen_worker(void *arg) {
     switch (J->kind) {
       case SYN_STENCIL2D5:
       case SYN_STENCIL3D7:
-      case SYN_STENCIL3D27: len = stencil_len(J->kind, J->p, i); break;
+      case SYN_STENCIL3D27:
+      case SYN_BOX3D: len = stencil_len(J->kind, J->p, i); break;
       case SYN_UNIFORM: {
         uint32_t w[4];
         draw(J->seed, (uint64_t)i, P_ROWLEN, 0, w);
@@ -301,7 +322,8 @@ static void *fill_worker(void *arg) {
     switch (J->kind) {
       case SYN_STENCIL2D5:
       case SYN_STENCIL3D7:
-      case SYN_STENCIL3D27: stencil_fill(J->kind, J->p, i, col, val); continue;
+      case SYN_STENCIL3D27:
+      case SYN_BOX3D: stencil_fill(J->kind, J->p, i, col, val); continue;
       case SYN_UNIFORM:
       case SYN_POWERLAW: uniform_columns(J->seed, i, J->n_cols, len, col); break;
       case SYN_BLOCKDIAG: {

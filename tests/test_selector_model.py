@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import paper_1210_2536_gb300 as smat
-from paper_1210_2536_gb300 import learn
+from paper_1210_2536_gb300 import learn, synth
 
 
 def _heldout():
@@ -19,8 +19,13 @@ def _heldout():
 
 def test_dataset_and_split():
     train, held = _heldout()
-    assert len(train) + len(held) == 2000 and len(held) == 398
-    assert {r["kind"] for r in held} == {r["kind"] for r in train}
+    assert len(train) + len(held) == synth.DATASET_SIZE == 2400 and len(held) == 398 + 80
+    assert {r["kind"] for r in held} == {r["kind"] for r in train} == set(synth.KIND_NAMES)
+    # every record is the matrix its id names (the generators' contract)
+    for r in train + held:
+        kind, params, _ = synth.dataset_spec(r["id"])
+        assert r["kind"] == synth.KIND_NAMES[kind]
+        assert np.allclose(r["params"], [float(v) for v in params], rtol=1e-12)
 
 
 def _oracle_forward(params, Xs):

@@ -31,6 +31,7 @@ def _check_canonical(A):
     lambda: synth.stencil2d5(7, 5), lambda: synth.stencil3d7(5), lambda: synth.stencil3d27(4),
     lambda: synth.uniform_random(300, 6.0, 3), lambda: synth.powerlaw(400, 1.8, 100, 4),
     lambda: synth.blockdiag(37, 8, 5), lambda: synth.uniform_random(50, 40.0, 1),
+    lambda: synth.box3d(6, 2), lambda: synth.box3d(5, 4),
 ])
 def test_canonical_csr(maker):
     _check_canonical(maker())
@@ -75,3 +76,48 @@ def test_distributions_close_to_their_means():
 def test_dataset_specs_cover_all_kinds():
     kinds = {synth.dataset_spec(i)[0] for i in range(200)}
     assert kinds == set(range(6))
+    assert synth.dataset_spec(synth.DATASET_PRIMARY)[0] == synth.BOX3D
+
+
+def test_box_stencil_closed_forms():
+    # radius 1 is the 27-point stencil, bit for bit
+    a, b = synth.box3d(7, 1), synth.stencil3d27(7)
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.colidx, b.colidx)
+    assert np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64))
+    for m, r in [(9, 2), (6, 3), (4, 5)]:
+        A = synth.box3d(m, r)
+        # points within r of c on a line of m points, cubed over the three axes
+        line = sum(min(c + r, m - 1) - max(c - r, 0) + 1 for c in range(m))
+        assert (A.m, A.nnz) == (m ** 3, line ** 3)
+        d = A.todense()
+        assert np.array_equal(d, d.T)
+        w = (2 * r + 1) ** 3
+        assert np.all(np.diag(d) == w - 1.0)
+        # every off-diagonal entry is -1, and the pattern is |di|,|dj|,|dk| <= r
+        g = np.indices((m, m, m)).reshape(3, -1)[::-1].T       # (x, y, z) of each row, x fastest
+        near = np.all(np.abs(g[:, None, :] - g[None, :, :]) <= r, axis=2)
+        assert np.array_equal(d != 0, near)
+        off = d[near & ~np.eye(m ** 3, dtype=bool)]
+        assert np.all(off == -1.0)
+        # rows with the whole box inside the grid sum to zero
+        full = np.diff(A.rowptr) == w
+        assert np.all(d[full].sum(axis=1) == 0.0)
+
+
+def test_galerkin_levels_have_box_stencil_patterns():
+    # the widened labelled set stands in for coarse multigrid operators: their
+    # sparsity patterns are box stencils whose radius grows level by level
+    H = synth.galerkin_hierarchy(32, 4)
+    for A, (m, r) in zip(H, [(32, 1), (16, 2), (8, 3), (4, 3)]):
+        B = synth.box3d(m, r)
+        assert np.array_equal(A.rowptr, B.rowptr) and np.array_equal(A.colidx, B.colidx)
+
+
+def test_widened_dataset_specs():
+    from collections import Counter
+    specs = [synth.dataset_spec(i) for i in range(synth.DATASET_PRIMARY, synth.DATASET_SIZE)]
+    assert {k for k, _, _ in specs} == {synth.BOX3D}
+    radii = Counter(int(p[1]) for _, p, _ in specs)
+    assert set(radii) == {2, 3, 4, 5, 6} and min(radii.values()) >= 50
+    for _, (m, r), seed in specs:
+        assert m >= 8 and m ** 3 * (2 * r + 1) ** 3 <= 5e7 * 1.05   # nnz bound (before boundary truncation)
