@@ -343,15 +343,25 @@ smat_status_t smat_mlp_adam(float *p, const float *g, float *m, float *v, int64_
 /* different matrices used in turn, so one format does not fit them all     */
 /* (Sec. 1).                                                                 */
 /* ------------------------------------------------------------------------ */
+typedef enum {
+  SMAT_BATCH_AUTO = 0,        /* time the graph plans and the per-matrix launches */
+  SMAT_BATCH_GRAPH = 1,       /* the persistent launch, captured in a graph       */
+  SMAT_BATCH_PER_MATRIX = 2   /* each member's own plan, launched in turn         */
+} smat_batch_mode_t;
+
 typedef struct {
   int32_t tile_scale;   /* tile size multiplier; 0 = autotune over {1,2,4,8}     */
   int32_t ctas_per_sm;  /* resident CTAs per SM; 0 = autotune over {2,4,8}       */
-  int32_t trial_reps;   /* timed graph launches per autotuning candidate       */
+  int32_t trial_reps;   /* timed launches per autotuning candidate             */
+  int32_t mode;         /* smat_batch_mode_t; default SMAT_BATCH_AUTO          */
 } smat_batch_opts_t;
 
 typedef struct {
   int32_t count, tiles, grid, tile_scale, ctas_per_sm;
-  double tuned_ms;      /* median time of one batched product while tuning     */
+  double tuned_ms;      /* median time of one product of the chosen plan       */
+  int32_t per_matrix;   /* 1: the members' own launches won the tuning         */
+  double graph_ms;      /* median time of the best graph plan (-1: not timed)  */
+  double per_matrix_ms; /* median time of the per-matrix launches (-1: not timed) */
 } smat_batch_info_t;
 
 void smat_batch_opts_default(smat_batch_opts_t *opts);
@@ -364,11 +374,16 @@ smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int3
 
 /* Build the work table (row tiles of every product, largest first), capture
  * the persistent launch in a CUDA graph and autotune tile size and CTAs per
- * SM by timing the graph.  Returns after `stream` has finished.  Must run
- * again if a member handle is re-tuned. */
+ * SM by timing the graph.  In SMAT_BATCH_AUTO mode the members' own launches,
+ * one after another, are timed too and kept when faster, so a batch is never
+ * slower than the loop it replaces (a few large members in formats whose
+ * single-matrix kernels outrun the persistent kernel's bodies).  Returns
+ * after `stream` has finished.  Must run again if a member handle is
+ * re-tuned. */
 smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, void *stream);
 
-/* y_i = alpha_i A_i x_i + beta_i y_i for every member i in one graph launch on
+/* y_i = alpha_i A_i x_i + beta_i y_i for every member i in one graph launch
+ * (or, when the tuning chose them, the members' own launches in turn) on
  * `stream`.  alphas / betas: HOST arrays of `count` scalars of the compute
  * type; xs / ys: HOST arrays of `count` DEVICE pointers, 16-byte aligned for
  * ELL and DIA members (SMAT_ERR_INVALID_ARG otherwise).  Descriptors are

@@ -34,6 +34,7 @@ SMAT_NUM_ALL_VARIANTS = 13
 VARIANT_NAMES = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo",
                  "csr_scalar_exact", "hyb", "sell", "bcsr", "split"]
 SMAT_TUNE_LEARNED, SMAT_TUNE_EXHAUSTIVE, SMAT_TUNE_RULES, SMAT_TUNE_FIXED = range(4)
+SMAT_BATCH_AUTO, SMAT_BATCH_GRAPH, SMAT_BATCH_PER_MATRIX = range(3)
 SMAT_MLP_PARAMS = 5512
 DTYPES = {"f64": SMAT_F64, "f32": SMAT_F32, "bf16": SMAT_BF16}
 
@@ -73,12 +74,14 @@ class smat_cg_info_t(ctypes.Structure):
 
 
 class smat_batch_opts_t(ctypes.Structure):
-    _fields_ = [("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("trial_reps", ctypes.c_int32)]
+    _fields_ = [("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("trial_reps", ctypes.c_int32),
+                ("mode", ctypes.c_int32)]
 
 
 class smat_batch_info_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("tiles", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
+                ("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tuned_ms", ctypes.c_double),
+                ("per_matrix", ctypes.c_int32), ("graph_ms", ctypes.c_double), ("per_matrix_ms", ctypes.c_double)]
 
 
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64

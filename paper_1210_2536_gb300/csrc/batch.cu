@@ -108,14 +108,23 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
         ell_group<V, R, MODE>(M.ecol, (const V *)M.eval, M.P, M.K, (const T *)M.x, ep, (T *)M.y, M.m, i0);
     }
   } else if (KIND == KIND_DIA) {
-    // consecutive rows and checked x loads in every precision, FP64 with 4
-    // diagonals per batch: under this kernel's 64-register bound the
-    // lane-striped FP64 body spills (540 bytes, ptxas), the unchecked interior
-    // path 60-1000 bytes, 8-diagonal FP64 batches 140
-    constexpr int UD = sizeof(V) == 8 ? 4 : 16 / R;
-    for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
-      dia_group<V, R, MODE, UD, false>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n,
-                                       i0);
+    // The single-matrix kernel's bodies: FP64 lane-striped rows with 4
+    // diagonals per batch (tiles start at multiples of BNT*R rows, so a
+    // warp's 32*R rows stay inside its tile); FP32 and BF16 consecutive rows
+    // with the unchecked interior path.  They need this kind's bound of 3 CTAs
+    // per SM (80 registers; ptxas: an 8-byte spill for FP64, none otherwise).
+    // The checked consecutive-row body that fits 64 registers took 0.431 ms
+    // on the Galerkin hierarchy of the 27-point operator on 128^3 (DIA on its
+    // two finest levels) against 0.244.
+    if (sizeof(V) == 8) {
+      for (long long b = tl.row0 + (long long)(threadIdx.x >> 5) * 32 * R; b < tl.row1; b += (long long)BNT * R)
+        dia_lane_group<V, R, MODE, 4>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m, M.n, b,
+                                      threadIdx.x & 31);
+    } else {
+      for (long long i0 = tl.row0 + (long long)threadIdx.x * R; i0 < tl.row1; i0 += (long long)BNT * R)
+        dia_group<V, R, MODE, 16 / R, true>(M.doff, M.nd, (const V *)M.dval, M.P, (const T *)M.x, ep, (T *)M.y, M.m,
+                                            M.n, i0);
+    }
   } else if (KIND == KIND_SELL) {  // row0 / row1 are slice indices; a warp per slice
     for (long long sl = tl.row0 + threadIdx.x / 32; sl < tl.row1; sl += BNT / 32)
       sell_slice<V, MODE, 8>(M.sptr, M.swidth, M.sperm, M.scol, (const V *)M.sval, (const T *)M.x, ep, (T *)M.y, sl,
@@ -134,7 +143,7 @@ __device__ __forceinline__ void batch_tile(const BatchMat &M, const BatchTile &t
 // counter, largest first, until none are left.  One kernel per kind keeps
 // each kernel's register budget to its own format's needs.
 template <typename V, int KIND>
-__global__ void __launch_bounds__(BNT, KIND == KIND_ELL ? 2 : 4) batch_kernel(const BatchMat *__restrict__ mats,
+__global__ void __launch_bounds__(BNT, KIND == KIND_ELL ? 2 : (KIND == KIND_DIA ? 3 : 4)) batch_kernel(const BatchMat *__restrict__ mats,
                                                     const BatchTile *__restrict__ tiles, int ntiles,
                                                     unsigned int *counter) {
   __shared__ int s_t;
@@ -187,7 +196,8 @@ struct smat_batch_s {
   unsigned int *d_counter = nullptr;  // one tile counter per format kind
   int ntiles = 0, grid = 0, tile_scale = 0, ctas_per_sm = 0;
   int kind_tiles[smat::NKIND] = {}, kind_first[smat::NKIND] = {}, kind_grid[smat::NKIND] = {};
-  double tuned_ms = -1.0;
+  double tuned_ms = -1.0, graph_ms = -1.0, loop_ms = -1.0;
+  bool loop = false;  // the members' own launches in turn won the tuning
   cudaStream_t cap = nullptr, fork[smat::NKIND - 1] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[smat::NKIND - 1] = {};
   cudaGraph_t graph = nullptr;
@@ -433,6 +443,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
   }
   BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
   BTRY(cudaStreamSynchronize(s));
+  if (o.mode < SMAT_BATCH_AUTO || o.mode > SMAT_BATCH_PER_MATRIX) return SMAT_ERR_INVALID_ARG;
   // autotune: tile scale x resident CTAs per SM, timed as the captured graph
   std::vector<int> scales, ctas;
   if (o.tile_scale > 0) scales.push_back(o.tile_scale); else scales = {1, 2, 4, 8};
@@ -444,6 +455,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
   double best = 1e30;
   int best_s = scales[0], best_c = ctas[0];
   const int reps = std::max(1, o.trial_reps);
+  if (o.mode == SMAT_BATCH_PER_MATRIX) scales.clear();
   for (int sc : scales) {
     for (int cp : ctas) {
       {
@@ -464,9 +476,47 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
       if (med < best) { best = med; best_s = sc; best_c = cp; }
     }
   }
-  smat_status_t st = build_plan(b, best_s, best_c);
-  if (st != SMAT_OK) return st;
-  b->tuned_ms = best;
+  b->graph_ms = scales.empty() ? -1.0 : best;
+  // the members' own plans launched in turn, timed the same way
+  b->loop = false;
+  b->loop_ms = -1.0;
+  if (o.mode != SMAT_BATCH_GRAPH) {
+    const double one = 1.0, zero = 0.0;
+    const float onef = 1.0f, zerof = 0.0f;
+    const void *al = b->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
+    const void *be = b->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
+    auto run_loop = [&]() -> cudaError_t {
+      for (int i = 0; i < n; ++i) {
+        const BatchMat &M = b->mats[(size_t)i];
+        if (M.m == 0) continue;
+        const smat_s *h = b->hs[(size_t)i];
+        cudaError_t e = launch_spmv(h, h->variant, al, M.x, be, M.y, s);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    };
+    for (int w = 0; w < 2; ++w) BTRY(run_loop());
+    std::vector<float> ms((size_t)reps);
+    for (int r = 0; r < reps; ++r) {
+      BTRY(cudaEventRecord(e0, s));
+      BTRY(run_loop());
+      BTRY(cudaEventRecord(e1, s));
+      BTRY(cudaEventSynchronize(e1));
+      BTRY(cudaEventElapsedTime(&ms[(size_t)r], e0, e1));
+    }
+    std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
+    b->loop_ms = ms[(size_t)reps / 2];
+    b->loop = o.mode == SMAT_BATCH_PER_MATRIX || b->loop_ms < best;
+  }
+  if (b->loop) {
+    free_graph(b);
+    b->tuned_ms = b->loop_ms;
+    b->ready = true;
+  } else {
+    smat_status_t st = build_plan(b, best_s, best_c);
+    if (st != SMAT_OK) return st;
+    b->tuned_ms = best;
+  }
   // forget the timing buffers: the next smat_batch_spmv installs the caller's vectors
   for (auto &M : b->mats) { M.x = nullptr; M.y = nullptr; }
   BTRY(cudaStreamSynchronize(s));
@@ -494,6 +544,16 @@ smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *co
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->loop) {  // the members' own plans, in turn
+    const size_t ts = b->dtype == SMAT_F64 ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < n; ++i) {
+      const smat_s *h = b->hs[(size_t)i];
+      if (h->m == 0) continue;
+      BTRY(launch_spmv(h, h->variant, (const char *)alphas + ts * (size_t)i, xs[i], (const char *)betas + ts * (size_t)i,
+                       ys[i], s));
+    }
+    return SMAT_OK;
+  }
   if (changed)
     BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
   BTRY(cudaGraphLaunch(b->exec, s));
@@ -508,6 +568,9 @@ smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info) {
   info->tile_scale = b->tile_scale;
   info->ctas_per_sm = b->ctas_per_sm;
   info->tuned_ms = b->tuned_ms;
+  info->per_matrix = b->loop ? 1 : 0;
+  info->graph_ms = b->graph_ms;
+  info->per_matrix_ms = b->loop_ms;
   return SMAT_OK;
 }
 
@@ -517,6 +580,7 @@ void smat_batch_opts_default(smat_batch_opts_t *o) {
   o->tile_scale = 0;
   o->ctas_per_sm = 0;
   o->trial_reps = 10;
+  o->mode = SMAT_BATCH_AUTO;
 }
 
 }  // extern "C"

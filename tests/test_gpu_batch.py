@@ -31,13 +31,23 @@ def _handles(mats, dtype):
     return hs
 
 
+@pytest.mark.parametrize("mode", [smat.SMAT_BATCH_GRAPH, smat.SMAT_BATCH_PER_MATRIX, smat.SMAT_BATCH_AUTO])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_batch_matches_oracle_and_single_products(dtype):
+def test_batch_matches_oracle_and_single_products(dtype, mode):
     mats = _members()
     hs = _handles(mats, dtype)
-    B = smat.Batch(hs).tune(trial_reps=3)
+    B = smat.Batch(hs).tune(trial_reps=3, mode=mode)
     info = B.info()
-    assert info["count"] == len(mats) and info["tiles"] > 0 and info["grid"] > 0 and info["tuned_ms"] > 0
+    assert info["count"] == len(mats) and info["tuned_ms"] > 0
+    if mode == smat.SMAT_BATCH_GRAPH:
+        assert info["per_matrix"] == 0 and info["tiles"] > 0 and info["grid"] > 0 and info["per_matrix_ms"] == -1.0
+        assert info["tuned_ms"] == info["graph_ms"]
+    elif mode == smat.SMAT_BATCH_PER_MATRIX:
+        assert info["per_matrix"] == 1 and info["graph_ms"] == -1.0 and info["tuned_ms"] == info["per_matrix_ms"]
+    else:  # both timed, the faster kept
+        assert info["graph_ms"] > 0 and info["per_matrix_ms"] > 0
+        assert info["tuned_ms"] == min(info["graph_ms"], info["per_matrix_ms"])
+        assert info["per_matrix"] == (1 if info["per_matrix_ms"] < info["graph_ms"] else 0)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     npdt = np.float64 if dtype == "f64" else np.float32
     for call, seed in enumerate((0, 3)):
@@ -86,7 +96,7 @@ def test_batch_galerkin_hierarchy(dtype):
     pytest.importorskip("scipy")
     mats = synth.galerkin_hierarchy(24, 5)
     hs = _handles(mats, dtype)
-    B = smat.Batch(hs).tune(trial_reps=3)
+    B = smat.Batch(hs).tune(trial_reps=3, mode=smat.SMAT_BATCH_GRAPH)
     npdt = np.float64 if dtype == "f64" else np.float32
     xs = [torch.from_numpy(synth.uniform(40 + i, 1, A.n).astype(npdt)).to(DEV) for i, A in enumerate(mats)]
     y0 = [synth.uniform(50 + i, 2, A.m).astype(npdt) for i, A in enumerate(mats)]
@@ -100,6 +110,40 @@ def test_batch_galerkin_hierarchy(dtype):
         single = hs[i].spmv(xs[i]).cpu().numpy().astype(np.float64)
         ref1, scale1 = reference(A, v64, xs[i].cpu().numpy(), 1.0, 0.0, None)
         assert_close_rows(single, ref1, scale1, TOL[dtype], f"level {i} ({A.name}) own plan {hs[i].plan()['name']}")
+    B.close()
+    for M in hs:
+        M.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_batch_dia_members(dtype):
+    # DIA members run the single-matrix kernel's bodies inside the persistent
+    # kernel (FP64 lane-striped rows, FP32/BF16 the unchecked interior path
+    # with 16-byte x loads); small tiles give every matrix several tiles and
+    # ragged ends, and the sizes leave partial warps at the tails
+    mats = [synth.stencil3d7(21), synth.stencil3d27(13), synth.box3d(9, 2), synth.box3d(5, 3),
+            synth.stencil2d5(37, 29), synth.stencil3d7(3)]
+    hs = []
+    for A in mats:
+        vals, _ = stored_values(A, dtype)
+        M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, np.ascontiguousarray(vals), dtype)
+        M.tune("fixed", variant=smat.SMAT_V_DIA)
+        assert M.plan()["variant"] == smat.SMAT_V_DIA
+        hs.append(M)
+    B = smat.Batch(hs).tune(trial_reps=2, tile_scale=1, ctas_per_sm=2, mode=smat.SMAT_BATCH_GRAPH)
+    assert B.info()["per_matrix"] == 0
+    tdt = np.float64 if dtype == "f64" else np.float32
+    for call, beta in enumerate((0.0, 1.5)):
+        xs = [torch.from_numpy(synth.uniform(70 + i, 1, A.n).astype(tdt)).to(DEV) for i, A in enumerate(mats)]
+        y0 = [synth.uniform(80 + i, 2, A.m).astype(tdt) for i, A in enumerate(mats)]
+        ys = [torch.from_numpy(v.copy()).to(DEV) for v in y0]
+        B.spmv(xs, ys, [0.75] * len(mats), [beta] * len(mats))
+        torch.cuda.synchronize()
+        for i, A in enumerate(mats):
+            _, v64 = stored_values(A, dtype)
+            ref, scale = reference(A, v64, xs[i].cpu().numpy(), 0.75, beta, y0[i] if beta else None)
+            assert_close_rows(ys[i].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
+                              f"call {call} {A.name} ({dtype})")
     B.close()
     for M in hs:
         M.close()
