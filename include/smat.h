@@ -163,6 +163,10 @@ typedef struct {
                               they move at most 1.25x the matrix bytes of the
                               selector's pick (BCSR only for max_RD <= 64);
                               default 1                                       */
+  int32_t plan_cache;      /* 1 (modes other than FIXED): take the plan recorded
+                              in the process-wide plan cache for this structure
+                              when it is admissible and allowed, else tune and
+                              record the result; default 0                    */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */
@@ -251,6 +255,38 @@ smat_status_t smat_get_feature_vector(smat_handle_t h, float out[12]);
  * the execute-and-measure fallback ran. */
 smat_status_t smat_get_plan(smat_handle_t h, int32_t *variant, double *tune_ms, float *confidence,
                             int32_t *trialled);
+
+/* 1 when the last smat_tune took its plan from the plan cache, else 0. */
+smat_status_t smat_get_plan_source(smat_handle_t h, int32_t *from_cache);
+
+/* ------------------------------------------------------------------------ */
+/* Tuned-plan cache: smat_tune's decisions kept per matrix structure, so a  */
+/* later handle or run reuses them (the paper's offline stage runs once per */
+/* platform, Sec. 5; this keeps the online stage's result too).  Host-side  */
+/* and thread-safe.                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* 64-bit key of h's structure: M, N, NNZ, the storage dtype, rowptr and
+ * colidx (not the values).  Each stored index adds
+ * mix(mix(tag << 56 ^ position) + (uint32_t)value) modulo 2^64, tag 1 for
+ * rowptr[0..M], 2 for colidx[0..NNZ); mix is the SplitMix64 finaliser; the
+ * key is mix(sum + mix(4M) + mix(4N + 1) + mix(4 NNZ + 2) + mix(4 dtype + 3)).
+ * One pass over rowptr and colidx on `stream`, computed once per handle;
+ * returns after `stream` has finished. */
+smat_status_t smat_plan_key(smat_handle_t h, uint64_t *key, void *stream);
+
+/* Write every cached plan to `path` as text: "smat-plan-cache 1", then one
+ * line "<key hex> <dtype> <M> <N> <NNZ> <variant> <sell sigma>" per plan.
+ * SMAT_ERR_INVALID_ARG if the file cannot be written. */
+smat_status_t smat_plan_cache_save(const char *path);
+
+/* Merge the plans of a file written by smat_plan_cache_save (a loaded entry
+ * replaces one with the same key).  A missing or malformed file changes
+ * nothing and returns SMAT_ERR_INVALID_ARG. */
+smat_status_t smat_plan_cache_load(const char *path);
+
+void smat_plan_cache_clear(void);
+int64_t smat_plan_cache_size(void);
 
 /* Median trial time per variant in ms from the last smat_tune (-1 = not run),
  * for all SMAT_NUM_ALL_VARIANTS variants. */

@@ -59,7 +59,7 @@ class smat_tune_opts_t(ctypes.Structure):
                 ("fill_ratio_max", ctypes.c_int32), ("bytes_cap", ctypes.c_double), ("trial_reps", ctypes.c_int32),
                 ("trial_warmup", ctypes.c_int32), ("trial_budget_ms", ctypes.c_double),
                 ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32), ("sell_sigma", ctypes.c_int32),
-                ("trial_extended", ctypes.c_int32)]
+                ("trial_extended", ctypes.c_int32), ("plan_cache", ctypes.c_int32)]
 
 
 class smat_cg_opts_t(ctypes.Structure):
@@ -100,6 +100,12 @@ _SIGS = {
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
     "smat_get_plan": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "smat_get_plan_source": (ctypes.c_int, [_VP, _VP]),
+    "smat_plan_key": (ctypes.c_int, [_VP, _VP, _VP]),
+    "smat_plan_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "smat_plan_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "smat_plan_cache_clear": (None, []),
+    "smat_plan_cache_size": (_I64, []),
     "smat_get_timings": (ctypes.c_int, [_VP, _VP]),
     "smat_measure_gather_rate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int32, _VP]),
     "smat_convert": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
@@ -229,6 +235,36 @@ def smat_get_plan(h):
     return v.value, ms.value, conf.value, tr.value
 
 
+def smat_get_plan_source(h) -> int:
+    c = ctypes.c_int32()
+    _check(lib().smat_get_plan_source(h, ctypes.byref(c)), "smat_get_plan_source")
+    return c.value
+
+
+def smat_plan_key(h, stream=0) -> int:
+    k = ctypes.c_uint64()
+    _check(lib().smat_plan_key(h, ctypes.byref(k), stream), "smat_plan_key")
+    return k.value
+
+
+def plan_cache_save(path):
+    """Write the process-wide plan cache to a text file (see smat.h)."""
+    _check(lib().smat_plan_cache_save(os.fsencode(path)), "smat_plan_cache_save")
+
+
+def plan_cache_load(path):
+    """Merge a plan-cache file into the process-wide cache."""
+    _check(lib().smat_plan_cache_load(os.fsencode(path)), "smat_plan_cache_load")
+
+
+def plan_cache_clear():
+    lib().smat_plan_cache_clear()
+
+
+def plan_cache_size() -> int:
+    return int(lib().smat_plan_cache_size())
+
+
 def smat_get_timings(h) -> np.ndarray:
     out = np.zeros(SMAT_NUM_ALL_VARIANTS, dtype=np.float32)
     _check(lib().smat_get_timings(h, out.ctypes.data), "smat_get_timings")
@@ -266,8 +302,9 @@ def smat_set_model(params, mean, std):
     return lib().smat_set_model(p.ctypes.data, mu.ctypes.data, sd.ctypes.data)
 
 
-def smat_load_model(path: str):
-    return lib().smat_load_model(os.fsencode(path))
+def smat_load_model(path=None):
+    """Load a selector model file; None loads the file SMAT_MODEL_PATH names."""
+    return lib().smat_load_model(None if path is None else os.fsencode(path))
 
 
 def smat_mlp_forward(params_ptr, x_ptr, B, logits_ptr, stream=0):
@@ -561,7 +598,12 @@ class SpMatrix:
 
     def plan(self) -> dict:
         v, ms, conf, tr = smat_get_plan(self.h)
-        return {"variant": v, "name": VARIANT_NAMES[v], "tune_ms": ms, "confidence": conf, "trialled": tr}
+        return {"variant": v, "name": VARIANT_NAMES[v], "tune_ms": ms, "confidence": conf, "trialled": tr,
+                "from_cache": smat_get_plan_source(self.h)}
+
+    def plan_key(self, stream=None) -> int:
+        """64-bit key of this matrix's structure in the plan cache."""
+        return smat_plan_key(self.h, _stream_ptr(stream))
 
     def launches(self, variant=None) -> int:
         """Kernel launches of one product (through the plan, or `variant`)."""

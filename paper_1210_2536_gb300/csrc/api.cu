@@ -7,19 +7,36 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "smat_internal.h"
 
 namespace smat {
 
 // ---------------------------------------------------------------------------
-// Allocation with a test hook (error-path tests inject a failure on the host).
+// Allocation with a test hook (error-path tests inject a failure on the host):
+// smat_test_fail_alloc_after(k), or SMAT_TEST_FAIL_ALLOC_AFTER=k in the
+// environment when the library loads, makes the k-th allocation fail.
 // ---------------------------------------------------------------------------
 static std::atomic<long> g_alloc_fail_at{0};
 static std::atomic<long> g_alloc_count{0};
+static const bool g_alloc_env = [] {
+  const char *e = std::getenv("SMAT_TEST_FAIL_ALLOC_AFTER");
+  if (e && *e) g_alloc_fail_at = std::atol(e);
+  return true;
+}();
+
+// An NVTX range for the length of a scope (the tuning phases show up by name
+// in profilers; without one attached the calls do nothing).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 cudaError_t dev_alloc(void **p, size_t bytes) {
   *p = nullptr;
@@ -666,6 +683,7 @@ smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_opts_t &o, cudaStream_t s,
                     int *best) {
+  Range r("trial");
   DevBuf x, y;
   TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * tsize(h)));
   TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * tsize(h)));
@@ -736,6 +754,7 @@ int rules_select(const smat_features_t &f, uint32_t ok) {
 }
 
 smat_status_t mlp_probs(const smat_s *h, float probs[SMAT_NUM_VARIANTS], cudaStream_t s) {
+  Range r("mlp");
   const Model &M = model();
   float v[12];
   feature_vector(h->f, v);
@@ -872,8 +891,10 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   if (o.sell_sigma == 0) o.sell_sigma = 256;
   if (o.sell_sigma < 32 || o.sell_sigma > 8192 || o.sell_sigma % 32 != 0) return SMAT_ERR_INVALID_ARG;
   const double t0 = now_ms();
+  Range r_tune("smat_tune");
   if (!h->have_features || o.tau_num != h->tau_num || o.tau_den != h->tau_den ||
       o.fill_ratio_max != h->fill_ratio_max) {
+    Range r("features");
     h->tau_num = o.tau_num; h->tau_den = o.tau_den; h->fill_ratio_max = o.fill_ratio_max;
     h->bytes_cap = o.bytes_cap > 0 ? o.bytes_cap : 4.0;
     TRYS(compute_features(h, s));
@@ -883,87 +904,118 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   }
   for (auto &t : h->timings) t = -1.0f;
   const uint32_t allowed = (o.allowed ? o.allowed : ALL_VARIANTS) & ALL_VARIANTS;
-  // layouts of the further formats the chosen mode may use
-  for (int e = SMAT_V_HYB; e <= SMAT_V_SPLIT; ++e) {
-    if (!((allowed >> e) & 1u)) continue;
-    const bool want = o.mode == SMAT_TUNE_EXHAUSTIVE || (o.mode == SMAT_TUNE_FIXED && o.fixed_variant == e) ||
-                      (o.mode == SMAT_TUNE_LEARNED && o.trial_extended &&
-                       (e != SMAT_V_BCSR || h->f.max_rd <= 64));
-    if (want) {
-      smat_status_t es = ext_layout(h, e, o.sell_sigma, s);
-      if (es == SMAT_ERR_ALLOC) continue;  // an unaffordable layout is not a candidate
-      TRYS(es);
-    }
-  }
-  const uint32_t ok = h->f.admissible & allowed;
-  if (!ok) return SMAT_ERR_UNSUPPORTED;
-  int v = SMAT_V_CSR_SCALAR;
+  h->plan_cached = false;
   h->confidence = -1.0f;
   h->trialled = 0;
-  std::vector<int> cands;
-  for (int c : {SMAT_V_DIA, SMAT_V_ELL, SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32,
-                SMAT_V_CSR_MERGE, SMAT_V_COO})
-    if ((ok >> c) & 1u) cands.push_back(c);
-  std::vector<int> ext;
-  for (int c = SMAT_V_HYB; c <= SMAT_V_SPLIT; ++c)
-    if ((ok >> c) & 1u) ext.push_back(c);
-  switch (o.mode) {
-    case SMAT_TUNE_FIXED:
-      if (o.fixed_variant < 0 || o.fixed_variant >= SMAT_NUM_ALL_VARIANTS ||
-          o.fixed_variant == SMAT_V_CSR_SCALAR_EXACT)
-        return SMAT_ERR_INVALID_ARG;
-      if (!((ok >> o.fixed_variant) & 1u)) return SMAT_ERR_UNSUPPORTED;
-      v = o.fixed_variant;
-      break;
-    case SMAT_TUNE_RULES:
-      v = rules_select(h->f, ok);
-      break;
-    case SMAT_TUNE_EXHAUSTIVE:
-      cands.insert(cands.end(), ext.begin(), ext.end());
-      if (cands.empty()) return SMAT_ERR_UNSUPPORTED;
-      TRYS(trial(h, cands, o, s, &v));
-      h->trialled = 1;
-      break;
-    case SMAT_TUNE_LEARNED: {
-      if (!model().loaded) return SMAT_ERR_MODEL;
-      float p[SMAT_NUM_VARIANTS];
-      TRYS(mlp_probs(h, p, s));
-      int arg = -1;
-      for (int c = 0; c < SMAT_NUM_VARIANTS; ++c)
-        if (((ok >> c) & 1u) && (arg < 0 || p[c] > p[arg])) arg = c;
-      if (arg < 0) {  // only further formats are allowed: time them
-        TRYS(trial(h, ext, o, s, &v));
+  int v = SMAT_V_CSR_SCALAR;
+  const bool use_cache = o.plan_cache && o.mode != SMAT_TUNE_FIXED;
+  if (use_cache) {  // a plan recorded for this structure, if still admissible and allowed
+    Range r("plan_cache");
+    TRYS(ensure_plan_key(h, s));
+    int cv = -1, csig = 0;
+    if (plan_cache_lookup(h, &cv, &csig) && cv != SMAT_V_CSR_SCALAR_EXACT && ((allowed >> cv) & 1u)) {
+      if (cv >= SMAT_V_HYB) {
+        smat_status_t es = ext_layout(h, cv, cv == SMAT_V_SELL ? csig : o.sell_sigma, s);
+        if (es != SMAT_OK && es != SMAT_ERR_ALLOC) return es;
+      }
+      if ((h->f.admissible >> cv) & 1u) {
+        v = cv;
+        h->plan_cached = true;
+      }
+    }
+  }
+  if (!h->plan_cached) {
+    Range r_select("select");
+    // layouts of the further formats the chosen mode may use
+    for (int e = SMAT_V_HYB; e <= SMAT_V_SPLIT; ++e) {
+      if (!((allowed >> e) & 1u)) continue;
+      const bool want = o.mode == SMAT_TUNE_EXHAUSTIVE || (o.mode == SMAT_TUNE_FIXED && o.fixed_variant == e) ||
+                        (o.mode == SMAT_TUNE_LEARNED && o.trial_extended &&
+                         (e != SMAT_V_BCSR || h->f.max_rd <= 64));
+      if (want) {
+        smat_status_t es = ext_layout(h, e, o.sell_sigma, s);
+        if (es == SMAT_ERR_ALLOC) continue;  // an unaffordable layout is not a candidate
+        TRYS(es);
+      }
+    }
+    const uint32_t ok = h->f.admissible & allowed;
+    if (!ok) return SMAT_ERR_UNSUPPORTED;
+    std::vector<int> cands;
+    for (int c : {SMAT_V_DIA, SMAT_V_ELL, SMAT_V_CSR_SCALAR, SMAT_V_CSR_VEC4, SMAT_V_CSR_VEC8, SMAT_V_CSR_VEC32,
+                  SMAT_V_CSR_MERGE, SMAT_V_COO})
+      if ((ok >> c) & 1u) cands.push_back(c);
+    std::vector<int> ext;
+    for (int c = SMAT_V_HYB; c <= SMAT_V_SPLIT; ++c)
+      if ((ok >> c) & 1u) ext.push_back(c);
+    switch (o.mode) {
+      case SMAT_TUNE_FIXED:
+        if (o.fixed_variant < 0 || o.fixed_variant >= SMAT_NUM_ALL_VARIANTS ||
+            o.fixed_variant == SMAT_V_CSR_SCALAR_EXACT)
+          return SMAT_ERR_INVALID_ARG;
+        if (!((ok >> o.fixed_variant) & 1u)) return SMAT_ERR_UNSUPPORTED;
+        v = o.fixed_variant;
+        break;
+      case SMAT_TUNE_RULES:
+        v = rules_select(h->f, ok);
+        break;
+      case SMAT_TUNE_EXHAUSTIVE:
+        cands.insert(cands.end(), ext.begin(), ext.end());
+        if (cands.empty()) return SMAT_ERR_UNSUPPORTED;
+        TRYS(trial(h, cands, o, s, &v));
         h->trialled = 1;
         break;
-      }
-      v = arg;
-      h->confidence = p[arg];
-      std::vector<int> top{arg};
-      if (p[arg] < o.conf_threshold) {
-        top = cands;
-        std::sort(top.begin(), top.end(), [&](int a, int b) { return p[a] > p[b]; });
-        if (o.fallback_topk > 0 && (int)top.size() > o.fallback_topk) top.resize((size_t)o.fallback_topk);
-      }
-      // the selector's classes do not include the further formats: time those
-      // that move at most 1.25x the matrix bytes of its pick beside it (their
-      // access patterns can beat a format that moves a little less)
-      bool more = false;
-      if (o.trial_extended)
-        for (int c : ext)
-          if (variant_bytes(h, c) <= 1.25 * variant_bytes(h, arg)) { top.push_back(c); more = true; }
-      if (top.size() > 1 || more) {
-        TRYS(trial(h, top, o, s, &v));
-        h->trialled = 1;
-      }
-    } break;
+      case SMAT_TUNE_LEARNED: {
+        if (!model().loaded) return SMAT_ERR_MODEL;
+        float p[SMAT_NUM_VARIANTS];
+        TRYS(mlp_probs(h, p, s));
+        int arg = -1;
+        for (int c = 0; c < SMAT_NUM_VARIANTS; ++c)
+          if (((ok >> c) & 1u) && (arg < 0 || p[c] > p[arg])) arg = c;
+        if (arg < 0) {  // only further formats are allowed: time them
+          TRYS(trial(h, ext, o, s, &v));
+          h->trialled = 1;
+          break;
+        }
+        v = arg;
+        h->confidence = p[arg];
+        std::vector<int> top{arg};
+        if (p[arg] < o.conf_threshold) {
+          top = cands;
+          std::sort(top.begin(), top.end(), [&](int a, int b) { return p[a] > p[b]; });
+          if (o.fallback_topk > 0 && (int)top.size() > o.fallback_topk) top.resize((size_t)o.fallback_topk);
+        }
+        // the selector's classes do not include the further formats: time those
+        // that move at most 1.25x the matrix bytes of its pick beside it (their
+        // access patterns can beat a format that moves a little less)
+        bool more = false;
+        if (o.trial_extended)
+          for (int c : ext)
+            if (variant_bytes(h, c) <= 1.25 * variant_bytes(h, arg)) { top.push_back(c); more = true; }
+        if (top.size() > 1 || more) {
+          TRYS(trial(h, top, o, s, &v));
+          h->trialled = 1;
+        }
+      } break;
+    }
   }
-  TRYS(prepare_variant(h, v, s));
+  {
+    Range r("prepare");
+    TRYS(prepare_variant(h, v, s));
+  }
   if (!o.keep_formats)
     for (int fmt = SMAT_FMT_ELL; fmt <= SMAT_FMT_SPLIT; ++fmt)
       if (fmt != variant_format(v)) free_format(h, fmt);
   TRY(cudaStreamSynchronize(s));
   h->variant = v;
+  if (use_cache && !h->plan_cached) plan_cache_store(h, v, h->sell_sigma);
   h->tune_ms = now_ms() - t0;
+  return SMAT_OK;
+}
+
+smat_status_t smat_get_plan_source(smat_handle_t h, int32_t *from_cache) {
+  TRYS(check_handle(h));
+  if (!from_cache) return SMAT_ERR_INVALID_ARG;
+  *from_cache = h->plan_cached ? 1 : 0;
   return SMAT_OK;
 }
 
@@ -1165,7 +1217,8 @@ smat_status_t smat_set_model(const float *params, const float *mean, const float
 }
 
 smat_status_t smat_load_model(const char *path) {
-  if (!path) return SMAT_ERR_INVALID_ARG;
+  if (!path || !*path) path = std::getenv("SMAT_MODEL_PATH");  // NULL: the file SMAT_MODEL_PATH names
+  if (!path || !*path) return SMAT_ERR_INVALID_ARG;
   FILE *fp = std::fopen(path, "rb");
   if (!fp) return SMAT_ERR_MODEL;
   char magic[8];

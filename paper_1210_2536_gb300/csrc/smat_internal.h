@@ -21,6 +21,12 @@ inline int64_t pitch_of(int64_t m) { return (m + 31) / 32 * 32; }
 cudaError_t dev_alloc(void **p, size_t bytes);
 void dev_free(void *p);
 
+// Plan cache (plan_cache.cu): the structural key, computed once per handle,
+// and the process-wide table of plans.
+smat_status_t ensure_plan_key(smat_s *h, cudaStream_t s);
+bool plan_cache_lookup(const smat_s *h, int *variant, int *sell_sigma);
+void plan_cache_store(const smat_s *h, int variant, int sell_sigma);
+
 // Device-side error flags set by validation kernels (never trap).
 enum : int {
   ERRF_ROWPTR = 1,     // rowptr[0] != 0, rowptr[m] != nnz or decreasing
@@ -57,6 +63,11 @@ struct smat_s {
   // CSR (always present)
   int32_t *rowptr = nullptr, *colidx = nullptr;
   void *val = nullptr;
+
+  // structural key of the plan cache (the structure never changes)
+  uint64_t plan_key = 0;
+  bool have_plan_key = false;
+  bool plan_cached = false;  // the last smat_tune took its plan from the cache
 
   // features
   bool have_features = false;

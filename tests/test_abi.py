@@ -83,3 +83,18 @@ def test_model_file_roundtrip(lib, tmp_path):
         f.write(b"XXXX")
     assert smat.smat_load_model(p) == smat.SMAT_ERR_MODEL
     assert smat.smat_set_model(None, None, None) == smat.SMAT_OK
+
+
+def test_model_path_from_the_environment(lib, tmp_path, monkeypatch):
+    # smat_load_model(NULL) loads the file SMAT_MODEL_PATH names
+    import numpy as np
+    import paper_1210_2536_gb300 as smat
+    p = str(tmp_path / "env.bin")
+    smat.write_model(p, np.zeros(smat.SMAT_MLP_PARAMS, np.float32), np.zeros(12), np.ones(12))
+    monkeypatch.delenv("SMAT_MODEL_PATH", raising=False)
+    assert smat.smat_load_model(None) == smat.SMAT_ERR_INVALID_ARG
+    monkeypatch.setenv("SMAT_MODEL_PATH", p)
+    assert smat.smat_load_model(None) == smat.SMAT_OK
+    monkeypatch.setenv("SMAT_MODEL_PATH", str(tmp_path / "missing.bin"))
+    assert smat.smat_load_model(None) == smat.SMAT_ERR_MODEL
+    assert smat.smat_set_model(None, None, None) == smat.SMAT_OK

@@ -24,11 +24,17 @@ def test_segments_choose_per_part_and_match_oracle(dtype):
     vals, v64 = stored_values(A, dtype)
     M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
                       torch.from_numpy(np.ascontiguousarray(vals)).to(DEV), dtype)
+    # the paper's rules decide from the features alone, so the per-part
+    # choice is deterministic: DIA for the banded rows, another format for
+    # the power-law rows (timed picks on parts this small are within noise)
+    R = smat.Segments(M, 4, "rules")
+    vr = R.info()["variants"]
+    assert vr[0] == "dia" and vr[-1] != "dia", vr
+    R.close()
     S = smat.Segments(M, 4, "exhaustive", trial_reps=3)
     info = S.info()
     rs = info["row_starts"]
     assert rs[0] == 0 and rs[-1] == A.m and all(r % 8 == 0 for r in rs[:-1]) and len(rs) >= 3
-    assert len(set(info["variants"])) >= 2, info          # the two parts pick different formats
     npdt = np.float64 if dtype == "f64" else np.float32
     x = synth.uniform(0, 1, A.n).astype(npdt)
     y0 = synth.uniform(1, 1, A.m).astype(npdt)
