@@ -256,7 +256,7 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1210_2536_gb300 as smat
-    from paper_1210_2536_gb300.roofline import algorithmic_bytes
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes, l2_sectors
     from paper_1210_2536_gb300.roofline import bound as roof_bound
     from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
 
@@ -395,6 +395,12 @@ def run_ours(args):
     # gather rate of this GPU over the dominant product's own x and count
     gather_peak = smat.smat_measure_gather_rate(dp["A"].n, dp["A"].nnz, dp["dt"], 20)
     gather_frac = dp["A"].nnz / (dom["_d"] / 1e3) / gather_peak
+    # the same measurement as a rate of L2 sector requests (each gather one
+    # sector, each streamed 4-byte index 1/8 of one), against the dominant
+    # product's own requests: its gathers plus its streamed format bytes
+    sector_peak = gather_peak * (1.0 + 4.0 / 32.0)
+    sectors = l2_sectors(dp["f"], dp["plan"]["variant"], dp["dt"])
+    sector_frac = sectors / (dom["_d"] / 1e3) / sector_peak
     for r in per:
         r.pop("_d")
         r.pop("alg_bytes")
@@ -450,7 +456,9 @@ def run_ours(args):
                          "unit": rb["unit"], "frac": round(rb["frac"], 4), "traffic": traffic,
                          "alg_bytes_per_launch": rb["alg_bytes"], "hbm_frac": round(rb["hbm_frac"], 4),
                          "fp64_frac": round(rb["fp64_frac"], 4) if "fp64_frac" in rb else None,
-                         "gather_peak_gps": round(gather_peak / 1e9, 1), "gather_frac": round(gather_frac, 4)},
+                         "gather_peak_gps": round(gather_peak / 1e9, 1), "gather_frac": round(gather_frac, 4),
+                         "l2_sectors_per_launch": sectors, "l2_sector_peak_gps": round(sector_peak / 1e9, 1),
+                         "l2_sector_frac": round(sector_frac, 4)},
             "step_hbm_frac": round(sum(algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"]) for p in prods)
                                    / (ms / K / 1e3) / 1e9 / peak, 4),
             "gpu_launches": launches_per_step * K,

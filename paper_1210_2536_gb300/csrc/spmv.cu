@@ -407,13 +407,12 @@ __device__ __forceinline__ void coo_finish(long long tile_end, T acc, int first_
 #define SMAT_COO_MINB 1
 #endif
 template <typename V, typename T, int NT, int CH, int MODE>
-__global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *__restrict__ row,
-                                                 const int32_t *__restrict__ col,
-                                                 const V *__restrict__ val, const T *__restrict__ x,
-                                                 Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
-                                                 int32_t *carry_row, T *carry_val) {
+__device__ __forceinline__ void coo_tile(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+                                         const V *__restrict__ val, const T *__restrict__ x, const Epi<T, MODE> &ep,
+                                         T *__restrict__ y, long long nnz, int32_t *carry_row, T *carry_val,
+                                         long long tile) {
   constexpr int IPT = 8, TILE = NT * CH * IPT;
-  const long long b0 = (long long)blockIdx.x * TILE;
+  const long long b0 = tile * TILE;
   const long long kt = b0 + (long long)threadIdx.x * (CH * IPT);
   T acc = 0, first_acc = 0;
   int first_row = -1;
@@ -436,8 +435,26 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
     coo_chunk<T, IPT, MODE>(r, c, v, r_next, valid, x, ep, y, acc, first_row, first_acc);
   }
   coo_finish<T, NT, MODE>(min(b0 + TILE, nnz), acc, first_row, first_acc, ep, y, nnz, row, carry_row, carry_val,
-                          blockIdx.x);
+                          tile);
 }
+
+template <typename V, typename T, int NT, int CH, int MODE>
+__global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *__restrict__ row,
+                                                                const int32_t *__restrict__ col,
+                                                                const V *__restrict__ val, const T *__restrict__ x,
+                                                                Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
+                                                                int32_t *carry_row, T *carry_val) {
+  coo_tile<V, T, NT, CH, MODE>(row, col, val, x, ep, y, nnz, carry_row, carry_val, blockIdx.x);
+}
+
+// COO launch shape (sweep knobs; these defaults measured fastest)
+#ifndef SMAT_COO_NT
+#define SMAT_COO_NT 256
+#endif
+#ifndef SMAT_COO_CH
+#define SMAT_COO_CH 1
+#endif
+constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 
 // ---------------------------------------------------------------------------
 // SPLIT, long rows (at least SPLIT_L = 1024 entries; measured on power-law
@@ -451,75 +468,117 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
 // block sum instead of the COO tile's carry resolution.
 // ---------------------------------------------------------------------------
 template <typename V, typename T>
-__global__ void __launch_bounds__(256) split_chunk_kernel(const int32_t *__restrict__ cstart,
-                                                          const int32_t *__restrict__ cend,
-                                                          const int32_t *__restrict__ col, const V *__restrict__ val,
-                                                          const T *__restrict__ x, T *__restrict__ part, long long nc) {
+__device__ __forceinline__ void split_chunk(long long c, const int32_t *__restrict__ cstart,
+                                            const int32_t *__restrict__ cend, const int32_t *__restrict__ col,
+                                            const V *__restrict__ val, const T *__restrict__ x,
+                                            T *__restrict__ part) {
   __shared__ T s_w[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long c = blockIdx.x; c < nc; c += gridDim.x) {
-    const int k0 = __ldg(cstart + c), k1 = __ldg(cend + c);
-    T acc = 0;
-    // steps j of 256 entries past the chunk's end are skipped by the whole
-    // CTA (a uniform test), so short chunks issue only the work they hold
+  const int k0 = __ldg(cstart + c), k1 = __ldg(cend + c);
+  T acc = 0;
+  // steps j of 256 entries past the chunk's end are skipped by the whole
+  // CTA (a uniform test), so short chunks issue only the work they hold
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      if (k0 + 256 * 8 * b >= k1) break;
-      int cc[8];
-      T v[8], xv[8];
+  for (int b = 0; b < 2; ++b) {
+    if (k0 + 256 * 8 * b >= k1) break;
+    int cc[8];
+    T v[8], xv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + (int)threadIdx.x + 256 * (8 * b + q);
-        const bool on = k < k1;
-        cc[q] = on ? ld_idx(col + k) : -1;
-        v[q] = on ? (T)ld_val(val + k) : (T)0;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) xv[q] = cc[q] >= 0 ? __ldg(x + cc[q]) : (T)0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (k0 + 256 * (8 * b + q) < k1) acc = fused(acc, v[q], xv[q]);
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + (int)threadIdx.x + 256 * (8 * b + q);
+      const bool on = k < k1;
+      cc[q] = on ? ld_idx(col + k) : -1;
+      v[q] = on ? (T)ld_val(val + k) : (T)0;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc = add_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-    if (lane == 0) s_w[w] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      T t = s_w[0];
+    for (int q = 0; q < 8; ++q) xv[q] = cc[q] >= 0 ? __ldg(x + cc[q]) : (T)0;
 #pragma unroll
-      for (int k = 1; k < 8; ++k) t = add_rn(t, s_w[k]);
-      part[c] = t;
-    }
-    __syncthreads();  // s_w is rewritten by the next chunk
+    for (int q = 0; q < 8; ++q)
+      if (k0 + 256 * (8 * b + q) < k1) acc = fused(acc, v[q], xv[q]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = add_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  if (lane == 0) s_w[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = s_w[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t = add_rn(t, s_w[k]);
+    part[c] = t;
   }
 }
 
-// SPLIT, long rows: each row's chunk sums added in chunk order, then the
-// epilogue.
+// SPLIT in one grid: blocks [0, nc) reduce the chunks of the long rows,
+// blocks [nc, nc + tiles) are COO tiles of the short rows (the two sets
+// write disjoint rows).  One launch instead of two keeps the GPU full across
+// what was the boundary between them.
+template <typename V, typename T, int MODE>
+__global__ void __launch_bounds__(COO_NT, SMAT_COO_MINB) split_main_kernel(
+    const int32_t *__restrict__ cstart, const int32_t *__restrict__ cend, const int32_t *__restrict__ col,
+    const V *__restrict__ val, T *__restrict__ part, long long nc, const int32_t *__restrict__ srow,
+    const int32_t *__restrict__ scol, const V *__restrict__ sval, long long ns, const T *__restrict__ x,
+    Epi<T, MODE> ep, T *__restrict__ y, int32_t *carry_row, T *carry_val) {
+  static_assert(COO_NT == 256, "the chunk path assumes 256 threads");
+  if ((long long)blockIdx.x < nc)
+    split_chunk<V, T>(blockIdx.x, cstart, cend, col, val, x, part);
+  else
+    coo_tile<V, T, COO_NT, COO_CH, MODE>(srow, scol, sval, x, ep, y, ns, carry_row, carry_val,
+                                         (long long)blockIdx.x - nc);
+}
+
+// A long row: its chunk sums added in chunk order, then the epilogue.
 template <typename T, int MODE>
-__global__ void split_rows_kernel(const int32_t *__restrict__ lrows, const int32_t *__restrict__ lchunk,
-                                  const T *__restrict__ part, long long nl, Epi<T, MODE> ep, T *__restrict__ y) {
-  for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (long long)gridDim.x * blockDim.x) {
-    const int c0 = lchunk[l], c1 = lchunk[l + 1];
-    T t = part[c0];
-    for (int c = c0 + 1; c < c1; ++c) t = add_rn(t, part[c]);
-    const long long r = lrows[l];
-    y[r] = ep(t, y, r);
-  }
+__device__ __forceinline__ void split_row(long long l, const int32_t *__restrict__ lrows,
+                                          const int32_t *__restrict__ lchunk, const T *__restrict__ part,
+                                          const Epi<T, MODE> &ep, T *__restrict__ y) {
+  const int c0 = lchunk[l], c1 = lchunk[l + 1];
+  T t = part[c0];
+  for (int c = c0 + 1; c < c1; ++c) t = add_rn(t, part[c]);
+  const long long r = lrows[l];
+  y[r] = ep(t, y, r);
 }
 
 // Fix-up: y[r] += alpha * (sum of the carries of row r), runs of equal rows
 // summed in tile order by the run's first entry.
 template <typename T, int MODE>
+__device__ __forceinline__ void carry_fixup(long long c, const int32_t *__restrict__ carry_row,
+                                            const T *__restrict__ carry_val, long long ntiles,
+                                            const Epi<T, MODE> &ep, T *__restrict__ y) {
+  const int r = carry_row[c];
+  if (r < 0 || (c > 0 && carry_row[c - 1] == r)) return;
+  T s = carry_val[c];
+  for (long long q = c + 1; q < ntiles && carry_row[q] == r; ++q) s = add_rn(s, carry_val[q]);
+  y[r] = add_rn(y[r], MODE == EPI_COPY ? s : mul_rn(ep.alpha, s));
+}
+
+template <typename T, int MODE>
 __global__ void carry_fixup_kernel(const int32_t *__restrict__ carry_row, const T *__restrict__ carry_val,
                                    long long ntiles, Epi<T, MODE> ep, T *__restrict__ y) {
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ntiles;
-       c += (long long)gridDim.x * blockDim.x) {
-    int r = carry_row[c];
-    if (r < 0 || (c > 0 && carry_row[c - 1] == r)) continue;
-    T s = carry_val[c];
-    for (long long q = c + 1; q < ntiles && carry_row[q] == r; ++q) s = add_rn(s, carry_val[q]);
-    y[r] = add_rn(y[r], MODE == EPI_COPY ? s : mul_rn(ep.alpha, s));
+       c += (long long)gridDim.x * blockDim.x)
+    carry_fixup<T, MODE>(c, carry_row, carry_val, ntiles, ep, y);
+}
+
+// SPLIT's closing pass over three disjoint sets of rows: the long rows
+// (chunk sums, epilogue), the carries of the short rows' COO tiles, and the
+// empty rows (y = beta y, or 0).
+template <typename T, int MODE>
+__global__ void split_finish_kernel(const int32_t *__restrict__ lrows, const int32_t *__restrict__ lchunk,
+                                    const T *__restrict__ part, long long nl, const int32_t *__restrict__ carry_row,
+                                    const T *__restrict__ carry_val, long long ntiles,
+                                    const int32_t *__restrict__ empty, long long ne, Epi<T, MODE> ep,
+                                    T *__restrict__ y) {
+  const long long total = nl + ntiles + ne;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nl) {
+      split_row<T, MODE>(i, lrows, lchunk, part, ep, y);
+    } else if (i < nl + ntiles) {
+      carry_fixup<T, MODE>(i - nl, carry_row, carry_val, ntiles, ep, y);
+    } else {
+      const int r = empty[i - nl - ntiles];
+      y[r] = MODE == EPI_AXPBY ? mul_rn(ep.beta, y[r]) : (T)0;
+    }
   }
 }
 
@@ -589,13 +648,6 @@ int grid_for(long long work, int block, int max_blocks) {
 }
 
 constexpr int MERGE_NT = 256, MERGE_IPT = 8;
-#ifndef SMAT_COO_NT
-#define SMAT_COO_NT 256
-#endif
-#ifndef SMAT_COO_CH
-#define SMAT_COO_CH 1
-#endif
-constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
 // A COO product over (row, col, val) of length nnz, then the carry fix-up.
 template <typename V, typename T, int MODE>
 cudaError_t launch_coo(const Scratch &sc, const int32_t *row, const int32_t *col, const V *val, const T *x,
@@ -733,26 +785,25 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
                                          h->hyb_ncoo, s);
     }
     case SMAT_V_SPLIT: {
-      if (h->split_ne > 0) {
-        scale_rows_kernel<T, MODE><<<grid_for(h->split_ne, 256, 152 * 8), 256, 0, s>>>(h->split_empty, h->split_ne,
-                                                                                        ep, y);
+      // two launches: the chunks of the long rows and the COO tiles of the
+      // short ones in one grid, then one pass for the long rows' sums, the
+      // tiles' carries and the empty rows
+      const long long nc = h->split_nc, ns = h->split_ns;
+      const long long tiles = (ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+      int32_t *crow = (int32_t *)sc.carry;
+      T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
+      if (nc + tiles > 0) {
+        split_main_kernel<V, T, MODE><<<(unsigned)(nc + tiles), COO_NT, 0, s>>>(
+            h->split_cstart, h->split_cend, h->colidx, val, (T *)sc.part, nc, h->split_srow, h->split_scol,
+            (const V *)h->split_sval, ns, x, ep, y, crow, cval);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
-      if (h->split_nc > 0) {
-        const long long nc = h->split_nc;
-        split_chunk_kernel<V, T><<<(unsigned)std::min<long long>(nc, 1LL << 30), 256, 0, s>>>(
-            h->split_cstart, h->split_cend, h->colidx, val, x, (T *)sc.part, nc);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        split_rows_kernel<T, MODE><<<grid_for(h->split_nl, 256, 152 * 8), 256, 0, s>>>(
-            h->split_lrows, h->split_lchunk, (const T *)sc.part, h->split_nl, ep, y);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-      }
-      if (h->split_ns > 0)
-        return launch_coo<V, T, MODE>(sc, h->split_srow, h->split_scol, (const V *)h->split_sval, x, ep, y,
-                                      h->split_ns, s);
+      const long long nl = nc > 0 ? h->split_nl : 0, nt = tiles > 1 ? tiles : 0;
+      if (nl + nt + h->split_ne > 0)
+        split_finish_kernel<T, MODE><<<grid_for(nl + nt + h->split_ne, 256, 152 * 8), 256, 0, s>>>(
+            h->split_lrows, h->split_lchunk, (const T *)sc.part, nl, crow, cval, nt, h->split_empty, h->split_ne, ep,
+            y);
     } break;
     default:
       return cudaErrorInvalidValue;

@@ -23,6 +23,12 @@ bcsr_nb, split_nc and split_ns once built).
 
 GFLOP/s counts 2 NNZ flops per product (true nonzeros only).
 
+On random-column matrices the binding roof is the rate of L2 sector requests:
+every stored product gathers one random x element (a whole 32-byte sector)
+besides the format's streamed bytes.  ``l2_sectors`` counts them; the bench
+compares the count per second with a measured rate (random gathers plus
+their streamed 4-byte indices, 1.125 sectors per gather).
+
 GB300 runs FP64 arithmetic at about 2 operations per clock per SM, so an
 FP64 product that spends one fused multiply-add per stored slot can be bound
 by the FP64 pipe instead of HBM; ``bound`` picks whichever roof binds.
@@ -88,6 +94,24 @@ def fp64_ops(f: dict, variant: int) -> float:
     if variant == V_BCSR:
         return float(f["bcsr_nb"] * f["bcsr_b"] ** 2)
     return float(f["nnz"])
+
+
+def l2_sectors(f: dict, variant: int, dtype: str) -> float:
+    """32-byte L2 sector requests of one product on a matrix with random
+    columns: one per gathered slot (a random x element is one sector that L1
+    does not hold), plus the format's streamed index and value bytes and the y
+    write, in sectors.  Banded matrices gather x in coalesced runs, so this
+    count holds for random-column matrices only."""
+    byts = algorithmic_bytes(f, variant, dtype) - (8 if dtype == "f64" else 4) * f["n"]   # x comes by gathers
+    if variant == V_SELL:
+        gathers = f["sell_slots"]
+    elif variant == V_HYB:
+        gathers = f["hyb_K"] * f["m"] + f["hyb_ncoo"]
+    elif variant == V_ELL:
+        gathers = f["max_rd"] * f["m"]
+    else:
+        gathers = f["nnz"]
+    return float(gathers) + byts / 32.0
 
 
 def bound(f: dict, variant: int, dtype: str, seconds: float, hbm_gbs: float) -> dict:

@@ -234,3 +234,36 @@ def test_ext_allocation_failures_leak_nothing():
     assert smat.SMAT_ERR_ALLOC in seen
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_split_long_short_and_empty_rows_in_one_product(dtype):
+    # every part of a SPLIT product at once: chunks of long rows and COO tiles
+    # of short rows in one grid, then the long rows' sums, the tiles' carries
+    # and the empty rows in one closing pass
+    from paper_1210_2536_gb300.synth import CSR
+    P = synth.powerlaw(30000, 1.8, 6000, 7)
+    rl = np.diff(P.rowptr).astype(np.int64)
+    keep = np.ones(P.m, bool)
+    keep[::97] = False                                        # empty rows
+    mask = np.repeat(keep, rl)
+    rp = np.concatenate([[0], np.cumsum(rl * keep)]).astype(np.int32)
+    A = CSR(P.m, P.n, rp, P.colidx[mask], P.val[mask], "powerlaw_with_empty_rows")
+    M, vals64 = make(A, dtype)
+    M.convert(smat.SMAT_FMT_SPLIT)
+    f = M.features()
+    assert f["split_nc"] > 1 and f["empty_rows"] > 0
+    assert f["split_ns"] > 4 * 2048                           # several COO tiles, so carries
+    x = vec(synth.uniform(5, 1, A.n), dtype)
+    xd = torch.from_numpy(x).to(DEV)
+    for alpha, beta in ((1.0, 0.0), (2.0, -0.5), (-1.5, 1.0), (0.0, 0.75)):
+        y0 = vec(synth.uniform(6, 1, A.m), dtype)
+        y = torch.from_numpy(y0.copy()).to(DEV)
+        if beta == 0:
+            y.fill_(float("nan"))
+        M.spmv(xd, y, alpha, beta, variant=smat.SMAT_V_SPLIT)
+        torch.cuda.synchronize()
+        ref, scale = reference(A, vals64, x, alpha, beta, y0 if beta != 0 else None)
+        assert_close_rows(y.cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
+                          f"SPLIT {dtype} alpha={alpha} beta={beta}")
+    M.close()
