@@ -416,14 +416,20 @@ def run_ours(args):
     # each product's copy in, kernel and copy out go to a stream of its own, so
     # no product's copy in waits behind another's copy out and the transfers
     # of one product overlap the kernels of the others; the step ends when
-    # every stream is done (y is then on the host)
+    # every stream is done (y is then on the host).  Products are issued
+    # shortest kernel first (their measured time alone): the short products'
+    # copies out then run under the long kernels instead of queueing behind
+    # them (measured on the structures suite: 374 GFLOP/s against 329 in the
+    # suite's order and 318 longest first)
+    order = sorted(range(len(prods)), key=lambda j: prods[j]["pick_ms"])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
 
     def e2e_step():
-        for j, (p, (xh, yh)) in enumerate(zip(prods, pinned)):
-            p["M"].spmv_host_async(xh, yh, stream=streams[j])
+        for j in order:
+            xh, yh = pinned[j]
+            prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
         for st in streams:
             st.synchronize()
 
@@ -465,7 +471,7 @@ def run_ours(args):
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": E,
-                    "how": "smat_spmv_host_async per product from pinned host x/y, a stream per product, all synced per step"},
+                    "how": "smat_spmv_host_async per product from pinned host x/y, a stream per product, shortest kernel first, all synced per step"},
             "cpu_baseline": cpu,
             "per_matrix": per,
         }

@@ -860,9 +860,10 @@ int spmv_launch_count(const smat_s *h, int variant) {
     long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
     return 1 + (h->hyb_ncoo > 0) + (tiles > 1);
   }
-  if (variant == SMAT_V_SPLIT) {
-    long long tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-    return (h->split_ne > 0) + 2 * (h->split_nc > 0) + (h->split_ns > 0) + (tiles > 1);
+  if (variant == SMAT_V_SPLIT) {  // the main grid, then the closing pass when it has rows to do
+    const long long tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    const long long nl = h->split_nc > 0 ? h->split_nl : 0, nt = tiles > 1 ? tiles : 0;
+    return (h->split_nc + tiles > 0) + (nl + nt + h->split_ne > 0);
   }
   if (variant == SMAT_V_SELL) return h->sell_ns > 0;
   if (variant == SMAT_V_BCSR) return h->bcsr_mb > 0;

@@ -267,3 +267,14 @@ def test_split_long_short_and_empty_rows_in_one_product(dtype):
         assert_close_rows(y.cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
                           f"SPLIT {dtype} alpha={alpha} beta={beta}")
     M.close()
+
+
+def test_split_launch_count():
+    # SPLIT is two launches: the grid of chunks and COO tiles, then the
+    # closing pass (long rows' sums, carries, empty rows) when it has work
+    from test_gpu_parity import _long_row
+    for A, want in ((synth.powerlaw(30000, 1.8, 6000, 7), 2), (_long_row(), 2)):
+        M, _ = make(A, "f64")
+        M.convert(smat.SMAT_FMT_SPLIT)
+        assert M.launches(smat.SMAT_V_SPLIT) == want, A.name
+        M.close()
