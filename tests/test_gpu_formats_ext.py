@@ -275,6 +275,6 @@ def test_split_launch_count():
     from test_gpu_parity import _long_row
     for A, want in ((synth.powerlaw(30000, 1.8, 6000, 7), 2), (_long_row(), 2)):
         M, _ = make(A, "f64")
-        M.convert(smat.SMAT_FMT_SPLIT)
-        assert M.launches(smat.SMAT_V_SPLIT) == want, A.name
+        M.tune("fixed", variant=smat.SMAT_V_SPLIT)
+        assert M.launches() == want, A.name
         M.close()
