@@ -424,6 +424,26 @@ __device__ __forceinline__ void coo_tile(const int32_t *__restrict__ row, const 
   for (int ch = 0; ch < CH; ++ch) {
     const long long k0 = kt + ch * IPT;
     const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
+    if (CH == 1 && sizeof(V) == 8) {
+      // FP64: the row after this thread's entries is the next lane's first
+      // row (a lane past the end holds -1), so only lane 31 loads it: one L2
+      // sector request fewer per thread on a kernel bound by their rate
+      // (power-law SPLIT 176 -> 166.5 us).  The column and value loads go
+      // first so the gathers do not wait for the shuffle.  In FP32 the
+      // shuffle costs 8 registers (48 -> 56) and was 2-7 % slower.  Every
+      // lane reaches the shuffle before any leaves.
+      const bool full = valid == IPT;
+      int r[IPT], c[IPT];
+      T v[IPT];
+      load_i32_run<IPT>(col + k0, full, valid, c, 0);
+      load_val_run<V, IPT>(val + k0, full, valid, v);
+      load_i32_run<IPT>(row + k0, full, valid, r, -1);
+      int r_next = __shfl_down_sync(FULL, r[0], 1);
+      if ((threadIdx.x & 31) == 31) r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
+      if (valid == 0) break;
+      coo_chunk<T, IPT, MODE>(r, c, v, r_next, valid, x, ep, y, acc, first_row, first_acc);
+      continue;
+    }
     if (valid == 0) break;
     const bool full = valid == IPT;
     int r[IPT], c[IPT];
