@@ -1,15 +1,18 @@
 // SpMV kernels y = alpha*A*x + beta*y for the four basic formats
 // (arXiv 1210.2536, Sec. 2.1; the paper's kernel library maps each format to
 // its best implementation, Sec. 3), and the launches of the further formats
-// that reuse them (HYB: ELL + COO tail; SPLIT: long rows in CTA chunks + COO).
+// that reuse them (HYB: ELL + COO tail; SPLIT: long rows in CTA chunks and
+// COO tiles of the short rows in one grid, then one closing pass).
 // GPU implementations of CSR follow Bell & Garland (2008, cited by the paper:
 // scalar and vector kernels) and Merrill & Garland (2016: merge-path); COO uses
 // a tiled segmented reduction.
 //
 // The kernels stream the format's index and value arrays once with coalesced
 // (ELL, DIA: 16-byte vector or lane-striped) loads, gather x through L1/L2 and
-// write y once.  They are bound by HBM, by the random x gathers, or (FP64) by
-// the FP64 pipe, which GB300 runs at about 2 operations per clock per SM: every
+// write y once.  They are bound by HBM, by the random x gathers (more exactly
+// by the rate of 32-byte L2 sector requests that the gathers and the streamed
+// arrays make together), or (FP64) by the FP64 pipe, which GB300 runs at
+// about 2 operations per clock per SM: every
 // kernel spends one fused multiply-add per stored product, and only
 // SMAT_V_CSR_SCALAR_EXACT rounds products and sums separately, in ascending
 // column order, as the CSR definition does.  The alpha/beta epilogue is fused:
