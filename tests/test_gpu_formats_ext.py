@@ -278,3 +278,32 @@ def test_split_launch_count():
         M.tune("fixed", variant=smat.SMAT_V_SPLIT)
         assert M.launches() == want, A.name
         M.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_every_variant_gives_the_same_bits_twice(dtype):
+    # every kernel combines its partial sums in a fixed order (no atomics on
+    # values), so a product repeated on the same inputs gives identical bits:
+    # the carries of COO / merge-path / HYB / SPLIT tiles and SPLIT's chunk
+    # sums included
+    A = synth.powerlaw(40000, 1.8, 5000, 11)
+    M, _ = make(A, dtype)
+    x = torch.from_numpy(vec(synth.uniform(2, 1, A.n), dtype)).to(DEV)
+    y0 = vec(synth.uniform(3, 1, A.m), dtype)
+    ran = 0
+    for v in range(smat.SMAT_NUM_ALL_VARIANTS):
+        outs = []
+        for _ in range(2):
+            y = torch.from_numpy(y0.copy()).to(DEV)
+            try:
+                M.spmv(x, y, 1.5, 0.25, variant=v)
+            except smat.SmatError as e:
+                assert e.status == smat.SMAT_ERR_UNSUPPORTED
+                break
+            torch.cuda.synchronize()
+            outs.append(y.cpu().numpy())
+        if len(outs) == 2:
+            assert np.array_equal(outs[0].view(np.uint8), outs[1].view(np.uint8)), smat.VARIANT_NAMES[v]
+            ran += 1
+    assert ran >= 8
+    M.close()
