@@ -548,6 +548,15 @@ smat_status_t smat_spmv_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, con
  * every entry point returns SMAT_ERR_ALLOC and frees what it had allocated. */
 void smat_test_fail_alloc_after(int32_t k);
 
+/* ------------------------------------------------------------------------ */
+/* Device memory                                                             */
+/* ------------------------------------------------------------------------ */
+/* The library takes device memory from a stream-ordered pool of its own that
+ * keeps up to 1 GiB of freed blocks for later allocations (a cudaMalloc and
+ * cudaFree pair costs 60-120 us on GB300; tuning makes dozens).  This call
+ * waits for the device and returns every cached block to the system. */
+smat_status_t smat_release_cached_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -38,17 +39,106 @@ struct Range {
   ~Range() { nvtxRangePop(); }
 };
 
+static bool inject_alloc_failure() {
+  const long k = ++g_alloc_count;
+  const long f = g_alloc_fail_at.load();
+  return f > 0 && k == f;
+}
+
+// Device memory comes from a library-owned stream-ordered pool of the current
+// device, which keeps up to 1 GiB of freed blocks for the next allocation: a
+// cudaMalloc + cudaFree pair costs 60-120 us on GB300, a pooled one about
+// 2 us, and one tuning makes dozens (features, layouts, conversions, trials).
+// Without a pool (creation failed) allocation falls back to cudaMalloc.
+struct DevPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t s = nullptr;  // orders the pool's long-lived allocations and frees
+  bool tried = false;
+};
+
+std::mutex &pool_mu() {
+  static std::mutex mu;
+  return mu;
+}
+
+DevPool *pools() {
+  static DevPool p[64];
+  return p;
+}
+
+DevPool &dev_pool() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(pool_mu());
+  DevPool &d = pools()[dev & 63];
+  if (!d.tried) {
+    d.tried = true;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    uint64_t keep = 1ull << 30;
+    if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&d.s, cudaStreamNonBlocking) != cudaSuccess) {
+      if (d.pool) cudaMemPoolDestroy(d.pool);
+      d.pool = nullptr;
+      cudaGetLastError();
+    }
+  }
+  return d;
+}
+
+// Long-lived buffers (formats, handle copies): ready for every stream when
+// this returns.
 cudaError_t dev_alloc(void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return cudaSuccess;
-  long k = ++g_alloc_count;
-  long f = g_alloc_fail_at.load();
-  if (f > 0 && k == f) return cudaErrorMemoryAllocation;
-  return cudaMalloc(p, bytes);
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
+  DevPool &d = dev_pool();
+  if (!d.pool) return cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, d.pool, d.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d.s);
+  if (e != cudaSuccess && *p) {
+    cudaFreeAsync(*p, d.s);
+    *p = nullptr;
+  }
+  return e;
 }
 
+// As cudaFree: the device is synchronised first, so no kernel in any stream
+// still uses the block when the pool may hand it out again.
 void dev_free(void *p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  DevPool &d = dev_pool();
+  if (!d.pool) {
+    cudaFree(p);
+    return;
+  }
+  cudaDeviceSynchronize();
+  cudaFreeAsync(p, d.s);
+}
+
+// Temporaries used on one stream only: allocated and freed in that stream's
+// order, with no synchronisation at all.
+cudaError_t tmp_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
+  DevPool &d = dev_pool();
+  if (!d.pool) return cudaMalloc(p, bytes);
+  return cudaMallocFromPoolAsync(p, bytes, d.pool, s);
+}
+
+void tmp_free(void *p, cudaStream_t s) {
+  if (!p) return;
+  DevPool &d = dev_pool();
+  if (!d.pool) {
+    cudaFree(p);
+    return;
+  }
+  cudaFreeAsync(p, s);
 }
 
 Model &model() {
@@ -58,10 +148,15 @@ Model &model() {
 
 namespace {
 
+// A temporary device buffer used on one stream, freed in that stream's order.
 struct DevBuf {
   void *p = nullptr;
-  ~DevBuf() { dev_free(p); }
-  cudaError_t alloc(size_t bytes) { return dev_alloc(&p, bytes); }
+  cudaStream_t s;
+  explicit DevBuf(cudaStream_t st) : s(st) {}
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { tmp_free(p, s); }
+  cudaError_t alloc(size_t bytes) { return tmp_alloc(&p, bytes, s); }
   template <typename T> T *as() const { return (T *)p; }
 };
 
@@ -185,7 +280,7 @@ smat_status_t compute_features(smat_s *h, cudaStream_t s) {
   f.nnz = h->nnz;
   RowStats st{0ull, 0, h->m > 0 ? INT_MAX : 0, 0, 0};
   if (h->m > 0) {
-    DevBuf d_st;
+    DevBuf d_st(s);
     TRY(d_st.alloc(sizeof(RowStats)));
     TRY(cudaMemcpyAsync(d_st.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
     TRY(launch_row_stats(h->rowptr, h->m, d_st.as<RowStats>(), s));
@@ -202,7 +297,7 @@ smat_status_t compute_features(smat_s *h, cudaStream_t s) {
   h->dia_offsets_complete = false;
   const int64_t nd_all = h->m + h->n - 1;
   if (h->m > 0 && h->n > 0) {
-    DevBuf d_hist, d_cnt, d_counts, d_off;
+    DevBuf d_hist(s), d_cnt(s), d_counts(s), d_off(s);
     TRY(d_hist.alloc((size_t)hist_len * sizeof(int)));
     TRY(d_cnt.alloc((size_t)nd_all * sizeof(int)));
     TRY(cudaMemsetAsync(d_hist.p, 0, (size_t)hist_len * sizeof(int), s));
@@ -359,7 +454,7 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
       free_sell_layout(h);  // drop what an earlier, failed attempt left
       const int64_t mp = (h->m + 31) / 32 * 32, ns = mp / 32;
       void *perm = nullptr, *width = nullptr, *ptr = nullptr;
-      DevBuf cnt;
+      DevBuf cnt(s);
       TRY(dev_alloc(&perm, (size_t)mp * 4));
       h->sell_perm = (int32_t *)perm;
       TRY(dev_alloc(&width, (size_t)ns * 4));
@@ -383,7 +478,7 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
       double best_bytes = 0.0;
       for (int b = 2; b <= 8; b *= 2) {
         const int64_t mb = (h->m + b - 1) / b;
-        DevBuf cnt;
+        DevBuf cnt(s);
         void *brp = nullptr;
         TRY(cnt.alloc((size_t)mb * 8));
         TRY(dev_alloc(&brp, (size_t)(mb + 1) * 8));
@@ -424,7 +519,7 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
     slot = cand[0];
     return SMAT_OK;
   }
-  DevBuf x, y;
+  DevBuf x(s), y(s);
   const size_t xs = (size_t)std::max<int64_t>(h->n, 1) * tsize(h), ys = (size_t)std::max<int64_t>(h->m, 1) * tsize(h);
   TRY(x.alloc(xs));
   TRY(y.alloc(ys));
@@ -508,7 +603,7 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     }
     if (h->f.empty_rows > 0) {
       void *l = nullptr;
-      DevBuf cnt;
+      DevBuf cnt(s);
       TRY(dev_alloc(&l, (size_t)h->f.empty_rows * 4));
       h->coo_empty = (int32_t *)l;
       h->coo_nempty = h->f.empty_rows;
@@ -538,7 +633,7 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
       TRY(dev_alloc(&p, (size_t)nc * 4)); h->hyb_crow = (int32_t *)p;
       TRY(dev_alloc(&p, (size_t)nc * 4)); h->hyb_ccol = (int32_t *)p;
       TRY(dev_alloc(&p, (size_t)nc * h->esz)); h->hyb_cval = p;
-      DevBuf cnt, off;
+      DevBuf cnt(s), off(s);
       TRY(cnt.alloc((size_t)h->m * 8));
       TRY(off.alloc((size_t)(h->m + 1) * 8));
       TRY(launch_hyb_tail_counts(h, K, cnt.as<long long>(), s));
@@ -565,7 +660,7 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
       TRY(dev_alloc(&p, ns * h->esz)); h->split_sval = p;
       TRY(dev_alloc(&p, ne * 4)); h->split_empty = (int32_t *)p;
       TRY(dev_alloc(&p, nc * tsize(h))); h->split_part = p;
-      DevBuf cnt, pre;
+      DevBuf cnt(s), pre(s);
       const size_t M = (size_t)h->m;
       TRY(cnt.alloc(4 * M * 8));
       TRY(pre.alloc(4 * (M + 1) * 8));
@@ -684,7 +779,7 @@ smat_status_t prepare_variant(smat_s *h, int v, cudaStream_t s) {
 smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_opts_t &o, cudaStream_t s,
                     int *best) {
   Range r("trial");
-  DevBuf x, y;
+  DevBuf x(s), y(s);
   TRY(x.alloc((size_t)std::max<int64_t>(h->n, 1) * tsize(h)));
   TRY(y.alloc((size_t)std::max<int64_t>(h->m, 1) * tsize(h)));
   TRY(cudaMemsetAsync(x.p, 0, (size_t)std::max<int64_t>(h->n, 1) * tsize(h), s));
@@ -759,7 +854,7 @@ smat_status_t mlp_probs(const smat_s *h, float probs[SMAT_NUM_VARIANTS], cudaStr
   float v[12];
   feature_vector(h->f, v);
   for (int i = 0; i < 12; ++i) v[i] = (v[i] - M.mean[i]) / (M.stdv[i] > 0 ? M.stdv[i] : 1.0f);
-  DevBuf d;
+  DevBuf d(s);
   const size_t np = SMAT_MLP_PARAMS;
   TRY(d.alloc((np + 12 + 8) * sizeof(float)));
   float *dp = d.as<float>(), *dx = dp + np, *dz = dx + 12;
@@ -820,6 +915,22 @@ const char *smat_status_string(smat_status_t s) {
     case SMAT_ERR_NOT_CONVERGED: return "not converged";
   }
   return "unknown status";
+}
+
+smat_status_t smat_release_cached_memory(void) {
+  std::lock_guard<std::mutex> lk(pool_mu());
+  bool ok = true;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int dev = 0; dev < 64; ++dev) {
+    DevPool &d = pools()[dev];
+    if (!d.pool) continue;
+    ok = cudaSetDevice(dev) == cudaSuccess && ok;
+    ok = cudaDeviceSynchronize() == cudaSuccess && ok;
+    ok = cudaMemPoolTrimTo(d.pool, 0) == cudaSuccess && ok;
+  }
+  cudaSetDevice(cur);
+  return ok ? SMAT_OK : SMAT_ERR_CUDA;
 }
 
 void smat_test_fail_alloc_after(int32_t k) {

@@ -52,6 +52,7 @@ def test_valid_edge_cases_are_accepted():
 def test_allocation_failure_returns_alloc_and_leaks_nothing():
     A = synth.powerlaw(50000, 1.8, 2000, 1)
     torch.cuda.synchronize()
+    assert smat.lib().smat_release_cached_memory() == smat.SMAT_OK
     free0 = torch.cuda.mem_get_info()[0]
     seen = set()
     for k in range(1, 12):
@@ -71,6 +72,7 @@ def test_allocation_failure_returns_alloc_and_leaks_nothing():
         assert st in (smat.SMAT_OK, smat.SMAT_ERR_ALLOC), smat.smat_status_string(st)
     assert smat.SMAT_ERR_ALLOC in seen
     torch.cuda.synchronize()
+    assert smat.lib().smat_release_cached_memory() == smat.SMAT_OK   # the pool's cached blocks are not leaks
     assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)   # nothing left allocated
 
 

@@ -217,6 +217,7 @@ def test_learned_mode_times_cheaper_further_formats():
 def test_ext_allocation_failures_leak_nothing():
     A = synth.blockdiag(50000, 8, 1)
     torch.cuda.synchronize()
+    assert smat.lib().smat_release_cached_memory() == smat.SMAT_OK
     free0 = torch.cuda.mem_get_info()[0]
     seen = set()
     for k in range(1, 14):
@@ -233,6 +234,7 @@ def test_ext_allocation_failures_leak_nothing():
         M.close()
     assert smat.SMAT_ERR_ALLOC in seen
     torch.cuda.synchronize()
+    assert smat.lib().smat_release_cached_memory() == smat.SMAT_OK   # the pool's cached blocks are not leaks
     assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
 
 
