@@ -167,6 +167,11 @@ typedef struct {
                               in the process-wide plan cache for this structure
                               when it is admissible and allowed, else tune and
                               record the result; default 0                    */
+  float trial_race;        /* trials: a candidate whose median over its first 3
+                              timed products exceeds this many times the best
+                              so far is not timed further (its timing is that
+                              median); 0 times every candidate fully;
+                              default 1.3                                     */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */
@@ -289,7 +294,8 @@ void smat_plan_cache_clear(void);
 int64_t smat_plan_cache_size(void);
 
 /* Median trial time per variant in ms from the last smat_tune (-1 = not run),
- * for all SMAT_NUM_ALL_VARIANTS variants. */
+ * for all SMAT_NUM_ALL_VARIANTS variants; a candidate stopped by racing
+ * (opts.trial_race) reports the median of its first 3 timed products. */
 smat_status_t smat_get_timings(smat_handle_t h, float ms[SMAT_NUM_ALL_VARIANTS]);
 
 /* Build format `fmt` on the device now (CSR is always there).  UNSUPPORTED if

@@ -804,16 +804,38 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     if (ps == SMAT_ERR_UNSUPPORTED || ps == SMAT_ERR_ALLOC) continue;  // skip, keep searching
     TRYS(ps);
     for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
-    for (int r = 0; r < reps; ++r) {
-      TRY(cudaEventRecord(ev[2 * r], s));
-      TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
-      TRY(cudaEventRecord(ev[2 * r + 1], s));
+    // racing: a candidate whose first few products already take trial_race
+    // times the best so far stops there (its median of those is kept)
+    const int first = (o.trial_race > 0.0f && best_ms < 1e30f) ? std::min(reps, 3) : reps;
+    int done = 0;
+    auto timed = [&](int upto) -> cudaError_t {
+      for (int r = done; r < upto; ++r) {
+        cudaError_t e = cudaEventRecord(ev[2 * r], s);
+        if (e == cudaSuccess) e = launch_spmv(h, v, a, x.p, b, y.p, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], s);
+        if (e != cudaSuccess) return e;
+      }
+      done = upto;
+      return cudaStreamSynchronize(s);
+    };
+    auto median = [&](std::vector<float> &ms) -> cudaError_t {
+      ms.resize((size_t)done);
+      for (int r = 0; r < done; ++r) {
+        cudaError_t e = cudaEventElapsedTime(&ms[(size_t)r], ev[2 * r], ev[2 * r + 1]);
+        if (e != cudaSuccess) return e;
+      }
+      std::nth_element(ms.begin(), ms.begin() + done / 2, ms.end());
+      return cudaSuccess;
+    };
+    std::vector<float> ms;
+    TRY(timed(first));
+    TRY(median(ms));
+    float med = ms[(size_t)done / 2];
+    if (done < reps && !(med > o.trial_race * best_ms)) {
+      TRY(timed(reps));
+      TRY(median(ms));
+      med = ms[(size_t)done / 2];
     }
-    TRY(cudaStreamSynchronize(s));
-    std::vector<float> ms((size_t)reps);
-    for (int r = 0; r < reps; ++r) TRY(cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]));
-    std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
-    float med = ms[(size_t)reps / 2];
     h->timings[v] = med;
     if (med < best_ms) {
       best_ms = med;
@@ -901,6 +923,8 @@ void smat_tune_opts_default(smat_tune_opts_t *o) {
   o->keep_formats = 0;
   o->sell_sigma = 256;
   o->trial_extended = 1;
+  o->plan_cache = 0;
+  o->trial_race = 1.3f;
 }
 
 const char *smat_status_string(smat_status_t s) {

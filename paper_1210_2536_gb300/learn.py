@@ -80,7 +80,9 @@ def label(out_path, count=synth.DATASET_SIZE, start=0, reps=7, budget_ms=20000.0
             M.tune("rules")
             rules_pick = M.plan()["variant"]
             # the selector's 8 classes only (the further formats are not classes)
-            M.tune("exhaustive", trial_reps=reps, trial_warmup=2, trial_budget_ms=budget_ms, allowed=0xFF)
+            # every class timed fully (no racing): the labels are all 8 medians
+            M.tune("exhaustive", trial_reps=reps, trial_warmup=2, trial_budget_ms=budget_ms, allowed=0xFF,
+                   trial_race=0.0)
             tm = M.timings()[:8]
             tune_ms = M.plan()["tune_ms"]
             M.close()

@@ -172,3 +172,27 @@ def test_gather_rate_measurement():
     assert r64 <= 1.5 * r32
     with pytest.raises(smat.SmatError):
         smat.smat_measure_gather_rate(0, 100, "f64", 5)
+
+
+def test_trial_racing_keeps_the_pick_and_saves_time():
+    # racing stops timing a candidate after 3 products when it is already
+    # 1.3x the best so far; on a power-law matrix, where CSR-scalar and the
+    # long-row kernels are several times slower than the best, the exhaustive
+    # search then finds an equally fast plan in less time
+    A = synth.powerlaw(300000, 1.8, 5000, 4)
+    M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
+                      torch.from_numpy(A.val).to(DEV), "f64")
+    M.tune("exhaustive", trial_race=0.0)          # warm: formats and kernels loaded once
+    M.tune("exhaustive", trial_race=0.0)
+    full, t_full = M.timings(), M.plan()["tune_ms"]
+    pick_full = M.plan()["variant"]
+    M.tune("exhaustive")                          # default: racing at 1.3
+    raced, t_raced = M.timings(), M.plan()["tune_ms"]
+    pick_raced = M.plan()["variant"]
+    assert raced[pick_raced] <= 1.15 * full[pick_full], (smat.VARIANT_NAMES[pick_raced], smat.VARIANT_NAMES[pick_full])
+    assert t_raced < t_full, (t_raced, t_full)
+    # every candidate still has a timing, and the stopped ones are the slow ones
+    ran = full > 0
+    assert np.array_equal(raced > 0, ran)
+    assert raced[ran].min() == raced[pick_raced]
+    M.close()
