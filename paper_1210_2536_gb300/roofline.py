@@ -98,11 +98,20 @@ def fp64_ops(f: dict, variant: int) -> float:
 
 def l2_sectors(f: dict, variant: int, dtype: str) -> float:
     """32-byte L2 sector requests of one product on a matrix with random
-    columns: one per gathered slot (a random x element is one sector that L1
-    does not hold), plus the format's streamed index and value bytes and the y
-    write, in sectors.  Banded matrices gather x in coalesced runs, so this
-    count holds for random-column matrices only."""
-    byts = algorithmic_bytes(f, variant, dtype) - (8 if dtype == "f64" else 4) * f["n"]   # x comes by gathers
+    columns (a lower bound):
+    - one per gathered slot (a random x element is one sector that L1 does
+      not hold);
+    - the format's streamed index and value bytes, in sectors;
+    - y: formats that write rows one at a time from lanes far apart (COO and
+      SPLIT tiles, SELL through its row permutation) spend a whole sector per
+      row; the others write y in full sectors;
+    - FP32 / BF16 COO and SPLIT tiles also load each thread's next row (one
+      sector per 8 entries; FP64 takes it from the next lane).
+    Banded matrices gather x in coalesced runs, so this count holds for
+    random-column matrices only."""
+    sy = 8 if dtype == "f64" else 4
+    byts = algorithmic_bytes(f, variant, dtype) - sy * f["n"]   # x comes by gathers
+    extra = 0.0
     if variant == V_SELL:
         gathers = f["sell_slots"]
     elif variant == V_HYB:
@@ -111,7 +120,12 @@ def l2_sectors(f: dict, variant: int, dtype: str) -> float:
         gathers = f["max_rd"] * f["m"]
     else:
         gathers = f["nnz"]
-    return float(gathers) + byts / 32.0
+    if variant in (V_COO, V_SPLIT, V_SELL):
+        byts -= sy * f["m"]
+        extra += f["m"]
+    if variant in (V_COO, V_SPLIT) and dtype != "f64":
+        extra += (f["nnz"] if variant == V_COO else f["split_ns"]) / 8.0
+    return float(gathers) + byts / 32.0 + extra
 
 
 def bound(f: dict, variant: int, dtype: str, seconds: float, hbm_gbs: float) -> dict:

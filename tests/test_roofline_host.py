@@ -23,13 +23,18 @@ def test_algorithmic_bytes_closed_forms(dt, sv, sx):
 
 
 def test_l2_sectors_on_random_columns():
-    # COO in FP64: one sector per gather, 16 streamed bytes per entry and an
-    # 8-byte y write per row, in 32-byte sectors
-    assert R.l2_sectors(F, R.V_COO, "f64") == 5000 + (16 * 5000 + 8 * 1000) / 32
-    # FP32 CSR: 8 bytes per entry, the row pointers, a 4-byte y
+    # COO in FP64: one sector per gather, 16 streamed bytes per entry, and a
+    # whole sector per row written (rows are written one at a time)
+    assert R.l2_sectors(F, R.V_COO, "f64") == 5000 + (16 * 5000) / 32 + 1000
+    # FP32 COO also loads each thread's next row: one sector per 8 entries
+    assert R.l2_sectors(F, R.V_COO, "f32") == 5000 + (12 * 5000) / 32 + 1000 + 5000 / 8
+    # FP32 CSR: 8 bytes per entry, the row pointers, a coalesced 4-byte y
     assert R.l2_sectors(F, 0, "f32") == 5000 + (8 * 5000 + 4 * 1001 + 4 * 1000) / 32
-    # SELL gathers once per slot, padding included
-    assert R.l2_sectors(F, R.V_SELL, "f64") == 6400 + (R.algorithmic_bytes(F, R.V_SELL, "f64") - 8 * 800) / 32
+    # SELL gathers once per slot, padding included, and writes y through its permutation
+    assert R.l2_sectors(F, R.V_SELL, "f64") == 6400 + (R.algorithmic_bytes(F, R.V_SELL, "f64") - 8 * 800 - 8 * 1000) / 32 + 1000
+    # SPLIT FP32: its short rows' tiles load next rows too
+    split = (R.algorithmic_bytes(F, R.V_SPLIT, "f32") - 4 * 800 - 4 * 1000) / 32
+    assert R.l2_sectors(F, R.V_SPLIT, "f32") == 5000 + split + 1000 + 3000 / 8
 
 
 def test_bound_picks_the_slower_roof():
