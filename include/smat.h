@@ -36,7 +36,9 @@
  * be its first stream; otherwise the product reports SMAT_ERR_CUDA).
  * smat_tune, smat_convert, smat_destroy and the host-buffer products
  * (smat_spmv_host*, which share the handle's staging buffers) must not overlap
- * with other calls on the handle.
+ * with other calls on the handle.  The selector model and the plan cache are
+ * process-wide and guarded: smat_load_model / smat_set_model may run while
+ * other threads tune (a tuning predicts from a copy of the model).
  */
 #ifndef SMAT_H
 #define SMAT_H

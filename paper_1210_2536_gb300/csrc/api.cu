@@ -146,6 +146,26 @@ Model &model() {
   return m;
 }
 
+// The selector model is process-wide: it is replaced under this lock, and a
+// tuning reads a copy taken under it, so loading a model while other threads
+// tune is safe.
+std::mutex &model_mu() {
+  static std::mutex mu;
+  return mu;
+}
+
+bool model_loaded() {
+  std::lock_guard<std::mutex> lk(model_mu());
+  return model().loaded;
+}
+
+bool model_copy(Model *out) {
+  std::lock_guard<std::mutex> lk(model_mu());
+  if (!model().loaded) return false;
+  *out = model();
+  return true;
+}
+
 namespace {
 
 // A temporary device buffer used on one stream, freed in that stream's order.
@@ -872,7 +892,8 @@ int rules_select(const smat_features_t &f, uint32_t ok) {
 
 smat_status_t mlp_probs(const smat_s *h, float probs[SMAT_NUM_VARIANTS], cudaStream_t s) {
   Range r("mlp");
-  const Model &M = model();
+  Model M;
+  if (!model_copy(&M)) return SMAT_ERR_MODEL;
   float v[12];
   feature_vector(h->f, v);
   for (int i = 0; i < 12; ++i) v[i] = (v[i] - M.mean[i]) / (M.stdv[i] > 0 ? M.stdv[i] : 1.0f);
@@ -1020,7 +1041,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
   TRYS(check_handle(h));
   cudaStream_t s = (cudaStream_t)stream;
   smat_tune_opts_t o;
-  if (opts_in) o = *opts_in; else { smat_tune_opts_default(&o); if (!model().loaded) o.mode = SMAT_TUNE_EXHAUSTIVE; }
+  if (opts_in) o = *opts_in; else { smat_tune_opts_default(&o); if (!model_loaded()) o.mode = SMAT_TUNE_EXHAUSTIVE; }
   if (o.mode < SMAT_TUNE_LEARNED || o.mode > SMAT_TUNE_FIXED) return SMAT_ERR_INVALID_ARG;
   if (o.tau_den <= 0 || o.tau_num < 0 || o.fill_ratio_max <= 0) return SMAT_ERR_INVALID_ARG;
   if (o.sell_sigma == 0) o.sell_sigma = 256;
@@ -1100,7 +1121,7 @@ smat_status_t smat_tune(smat_handle_t h, const smat_tune_opts_t *opts_in, void *
         h->trialled = 1;
         break;
       case SMAT_TUNE_LEARNED: {
-        if (!model().loaded) return SMAT_ERR_MODEL;
+        if (!model_loaded()) return SMAT_ERR_MODEL;
         float p[SMAT_NUM_VARIANTS];
         TRYS(mlp_probs(h, p, s));
         int arg = -1;
@@ -1338,6 +1359,7 @@ smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *id
 }
 
 smat_status_t smat_set_model(const float *params, const float *mean, const float *stdv) {
+  std::lock_guard<std::mutex> lk(model_mu());
   Model &M = model();
   if (!params) {
     M.loaded = false;

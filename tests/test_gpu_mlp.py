@@ -112,3 +112,46 @@ def test_learned_mode_selects_an_admissible_variant():
         M.close()
     finally:
         smat.smat_set_model(None, None, None)
+
+
+def test_model_reloads_while_other_threads_tune():
+    # the selector model is process-wide; reloading it while other threads
+    # tune their own handles is allowed (tuning predicts from a copy taken
+    # under the model's lock)
+    import threading
+    assert smat.smat_load_model(smat.MODEL_PATH) == smat.SMAT_OK
+    mats = [synth.stencil3d7(40), synth.powerlaw(60000, 1.8, 2000, 3)]
+    hs = [smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64") for A in mats]
+    stop = threading.Event()
+    errors = []
+
+    def reload():
+        while not stop.is_set():
+            if smat.smat_load_model(smat.MODEL_PATH) != smat.SMAT_OK:
+                errors.append("load")
+
+    def tune(M, stream):
+        try:
+            for _ in range(20):
+                M.tune("learned", stream=stream, trial_extended=0)
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errors.append(repr(e))
+
+    t0 = threading.Thread(target=reload)
+    streams = [torch.cuda.Stream() for _ in hs]
+    ts = [threading.Thread(target=tune, args=(M, st)) for M, st in zip(hs, streams)]
+    t0.start()
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    stop.set()
+    t0.join()
+    assert not errors, errors
+    for A, M in zip(mats, hs):   # every plan chosen under the reloads still computes the product
+        x = synth.uniform(0, 1, A.n)
+        y = M.spmv(torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = oracle.spmv_csr(A.m, A.rowptr, A.colidx, A.val, x, threads=8)
+        scale = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(A.val), np.abs(x), threads=8)
+        assert np.all(np.abs(y - ref) <= 1e-12 * scale + 1e-300), M.plan()["name"]
+        M.close()
