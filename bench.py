@@ -120,6 +120,22 @@ class Clocks:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
+def e2e_issue_order(times):
+    """Issue order of the end-to-end step, from each product's time alone:
+    shortest first, except that the second-longest goes second and the
+    longest halfway.  The long kernels then start while later inputs are
+    still arriving, do not hold the SMs at the same moment, and their
+    outputs return while short kernels run (structures suite, one box, 5
+    interleaved runs each: 389 GFLOP/s median against 357 shortest first)."""
+    order = sorted(range(len(times)), key=lambda j: times[j])
+    if len(order) >= 4:
+        longest, second = order[-1], order[-2]
+        rest = order[:-2]
+        half = len(order) // 2 - 1
+        order = rest[:1] + [second] + rest[1:half] + [longest] + rest[half:]
+    return order
+
+
 def dram_traffic_record(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     source is unchanged since the capture (else None)."""
@@ -416,18 +432,9 @@ def run_ours(args):
     # each product's copy in, kernel and copy out go to a stream of its own, so
     # no product's copy in waits behind another's copy out and the transfers
     # of one product overlap the kernels of the others; the step ends when
-    # every stream is done (y is then on the host).  Issue order, by each
-    # product's measured time alone: shortest first, except that the
-    # second-longest goes second and the longest halfway.  The long kernels
-    # then start while later inputs are still arriving, do not hold the SMs
-    # at the same moment, and their outputs return while short kernels run
-    # (structures suite, one box, 5 interleaved runs each: 389 GFLOP/s median
-    # against 357 shortest first)
-    order = sorted(range(len(prods)), key=lambda j: prods[j]["pick_ms"])
-    if len(order) >= 4:
-        longest, second = order[-1], order[-2]
-        rest = order[:-2]
-        order = rest[:1] + [second] + rest[1:len(order) // 2 - 1] + [longest] + rest[len(order) // 2 - 1:]
+    # every stream is done (y is then on the host); issued in
+    # e2e_issue_order's order
+    order = e2e_issue_order([p["pick_ms"] for p in prods])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
