@@ -110,7 +110,7 @@ def load(path):
 
 def split(recs, every=5):
     """Held-out split stratified by generator kind: within each kind, every
-    `every`-th matrix (by id) is held out (1600 / 400 for 2000 matrices)."""
+    `every`-th matrix (by id) is held out (1922 / 478 for the 2400 matrices)."""
     by = {}
     for r in recs:
         by.setdefault(r["kind"], []).append(r)
