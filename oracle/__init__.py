@@ -14,6 +14,8 @@ Every function restates a definition of the paper:
                   in Sec. 8 (HYB, SELL-C-sigma, BCSR; published definitions)
   split_rows      rows split by length: long rows in chunks, short rows as COO
   mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
+  admissible      the 20x fill rule plus a byte cap (Sec. 2.3)
+  rules_select    the observations of Sec. 4 as an ordered rule set (Sec. 6)
 Readings taken where the paper is silent are listed in ``oracle.c``.
 """
 from __future__ import annotations
@@ -376,3 +378,71 @@ def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     gg, pg = _c(g, np.float64)
     lib().oracle_adam(p.size, p.ctypes.data, pg, m.ctypes.data, v.ctypes.data, int(t), lr, b1, b2, eps)
+
+
+# ---------------------------------------------------------------------------
+# Admissible formats and the paper's rule set (Sec. 2.3, Sec. 4, Sec. 6)
+# ---------------------------------------------------------------------------
+
+#: the eight classes a format is chosen from, in the order of their ids
+CLASSES = ("csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo")
+
+
+def admissible(m, nnz, max_rd, ndiags, value_bytes, fill_ratio_max=20, bytes_cap=4.0) -> int:
+    """Bit mask over CLASSES (bit c set = class c may be used).
+
+    CSR, in every kernel, and COO store only the entries: always admissible.
+    Sec. 2.3 keeps the zero-filling formats only while the slots they store
+    are at most 20 times the entries (one stored slot in twenty at least is an
+    entry): ELL while max_RD * M <= 20 NNZ, DIA while Ndiags * M <= 20 NNZ,
+    both tested in integers.  Besides, their arrays, padded to the pitch P =
+    roundup(M, 32) rows, may move at most ``bytes_cap`` times the bytes of the
+    CSR arrays (values, int32 columns, int32 row pointers):
+      ELL  (value_bytes + 4) * max_RD * P
+      DIA  value_bytes * Ndiags * P + 4 * Ndiags   (values plus the offsets)
+    """
+    mask = 0
+    for c in ("csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "coo"):
+        mask |= 1 << CLASSES.index(c)
+    P = pitch(m)
+    csr_bytes = max((value_bytes + 4) * nnz + 4 * (m + 1), 1)
+    if m > 0 and max_rd > 0 and max_rd * m <= fill_ratio_max * nnz and \
+            (value_bytes + 4) * max_rd * P <= bytes_cap * csr_bytes:
+        mask |= 1 << CLASSES.index("ell")
+    if m > 0 and ndiags > 0 and ndiags * m <= fill_ratio_max * nnz and \
+            value_bytes * ndiags * P + 4 * ndiags <= bytes_cap * csr_bytes:
+        mask |= 1 << CLASSES.index("dia")
+    return mask
+
+
+def rules_select(f, mask) -> int:
+    """The format the observations of Sec. 4 choose, tried in the order Sec. 6
+    gives the rule subsets (DIA, ELL, then CSR and COO); returns a class id.
+
+    ``f`` holds the features of ``features()`` (aver_rd, max_rd, var_rd,
+    ndiags, er_dia, er_ell, ntdiags_ratio, r, r_valid); ``mask`` is
+    ``admissible()``.  Readings:
+      DIA  at most 500 diagonals (few matrices gain beyond), and any of: fewer
+           than 25 diagonals, ER_DIA above 60 %, NTdiags_ratio above 40 %;
+      ELL  max_RD below 5 or ER_ELL above 90 %, and var_RD below 0.5 in
+           either case;
+      CSR or COO: the observations give no CSR rule, so R decides between
+           them: a row-degree histogram fitted by a power law with R in
+           [1, 4) marks a small-world matrix, stored as COO; otherwise CSR,
+           whose GPU kernel is CSR-vector with the lane count that fits the
+           mean row length (4 below 8 entries, 8 below 24, else 32).
+    A rule whose format is not admissible does not fire."""
+    def ok(name):
+        return (mask >> CLASSES.index(name)) & 1
+
+    nd = f["ndiags"]
+    if ok("dia") and nd <= 500 and (nd < 25 or f["er_dia"] > 0.6 or f["ntdiags_ratio"] > 0.4):
+        return CLASSES.index("dia")
+    if ok("ell") and (f["max_rd"] < 5 or f["er_ell"] > 0.9) and f["var_rd"] < 0.5:
+        return CLASSES.index("ell")
+    if ok("coo") and f["r_valid"] and 1.0 <= f["r"] < 4.0:
+        return CLASSES.index("coo")
+    lanes = "csr_vec4" if f["aver_rd"] < 8.0 else ("csr_vec8" if f["aver_rd"] < 24.0 else "csr_vec32")
+    if ok(lanes):
+        return CLASSES.index(lanes)
+    return next(c for c in range(len(CLASSES)) if (mask >> c) & 1)

@@ -43,3 +43,15 @@ def assert_close_rows(y, ref, scale, tol, what=""):
         i = int(np.argmax(np.where(bad, err / np.maximum(scale, 1e-300), 0)))
         raise AssertionError(f"{what}: {int(bad.sum())} rows out of bound; row {i}: y={y[i]!r} ref={ref[i]!r} "
                              f"scale={scale[i]!r} tol={tol}")
+
+
+def csr_from_degrees(deg, n, seed):
+    """A CSR matrix whose rows have the given lengths, columns drawn uniformly
+    without replacement from [0, n), values 1."""
+    rng = np.random.default_rng(seed)
+    deg = np.asarray(deg, dtype=np.int64)
+    rowptr = np.zeros(len(deg) + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum(deg)
+    cols = [np.sort(rng.choice(n, size=int(d), replace=False)) for d in deg]
+    colidx = np.concatenate(cols).astype(np.int32) if len(cols) else np.zeros(0, np.int32)
+    return CSR(len(deg), n, rowptr, colidx, np.ones(len(colidx)))
