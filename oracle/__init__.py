@@ -16,6 +16,7 @@ Every function restates a definition of the paper:
   mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
   admissible      the 20x fill rule plus a byte cap (Sec. 2.3)
   rules_select    the observations of Sec. 4 as an ordered rule set (Sec. 6)
+  selector_inputs/learned_select  the learned selector's inputs and pick
 Readings taken where the paper is silent are listed in ``oracle.c``.
 """
 from __future__ import annotations
@@ -446,3 +447,37 @@ def rules_select(f, mask) -> int:
     if ok(lanes):
         return CLASSES.index(lanes)
     return next(c for c in range(len(CLASSES)) if (mask >> c) & 1)
+
+
+# ---------------------------------------------------------------------------
+# The learned selector's decision (replacing the ruleset search of Sec. 6)
+# ---------------------------------------------------------------------------
+
+def selector_inputs(f) -> np.ndarray:
+    """The 12 network inputs from the features of Table "Feature parameters"
+    (Sec. 4) plus N and aver_RD, in FP64: log(1 + v) of M, N, NNZ, aver_RD,
+    max_RD, min_RD, var_RD and Ndiags (counts spanning decades), then
+    NTdiags_ratio, ER_DIA and ER_ELL as they are (already in [0, 1]), then R,
+    limited to [-100, 100], or 0 when the fit is undefined (``r_valid`` 0)."""
+    logs = [f[k] for k in ("m", "n", "nnz", "aver_rd", "max_rd", "min_rd", "var_rd", "ndiags")]
+    r = min(100.0, max(-100.0, f["r"])) if f["r_valid"] else 0.0
+    return np.array([np.log1p(float(v)) for v in logs] + [f["ntdiags_ratio"], f["er_dia"], f["er_ell"], r])
+
+
+def learned_select(f, mask, params, mean, std):
+    """(class id, probabilities over CLASSES): the inputs standardised by the
+    model's mean and standard deviation (a deviation of 0 leaves the input
+    unscaled), the network's logits, a softmax over the admissible classes
+    only (others get probability 0), and the most probable class (the lowest
+    id among equals).  FP64 throughout."""
+    x = selector_inputs(f)
+    sd = np.where(np.asarray(std, np.float64) > 0, np.asarray(std, np.float64), 1.0)
+    xs = (x - np.asarray(mean, np.float64)) / sd
+    z = mlp_forward(np.asarray(params, np.float64), xs.reshape(1, -1))[0]
+    live = np.array([(mask >> c) & 1 for c in range(len(CLASSES))], dtype=bool)
+    p = np.zeros(len(CLASSES))
+    if live.any():
+        e = np.exp(z[live] - z[live].max())
+        p[live] = e / e.sum()
+    best = int(np.argmax(np.where(live, p, -1.0)))
+    return best, p

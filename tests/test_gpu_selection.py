@@ -1,7 +1,8 @@
-"""The library's admissibility filter (Sec. 2.3) and its paper-rules selector
-(Sec. 4, in the order of Sec. 6) against the oracle's, on the same seeded
-matrices in each storage type: the admissible mask over the eight classes,
-and the format the rules pick (``tune("rules")``)."""
+"""The library's format selection against the oracle's, on the same seeded
+matrices in each storage type: the admissibility filter (Sec. 2.3) as a mask
+over the eight classes, the paper-rules pick (Sec. 4, in the order of Sec. 6;
+``tune("rules")``) and the learned selector's pick and confidence without
+trials (``tune("learned")`` with a confidence threshold of 0)."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,21 @@ def matrices():
     return [(A, oracle.features(A.m, A.n, A.rowptr, A.colidx)) for A in _matrices()]
 
 
+def _oracle_mask(A, f, dtype):
+    want = oracle.admissible(A.m, A.nnz, f["max_rd"], f["ndiags"], VALUE_BYTES[dtype])
+    if f["ndiags"] > DIA_MAX_OFFSETS:
+        want &= ~(1 << oracle.CLASSES.index("dia"))
+    return want
+
+
+def _handle(A, dtype):
+    vals, _ = stored_values(A, dtype)
+    if dtype == "bf16":
+        vals = vals.view(np.int16)
+    return smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
+                         torch.from_numpy(np.ascontiguousarray(vals)).to(DEV), dtype)
+
+
 def _lib_mask(oracle_mask):
     return sum(1 << LIB_ID[c] for i, c in enumerate(oracle.CLASSES) if (oracle_mask >> i) & 1)
 
@@ -68,15 +84,9 @@ def _lib_mask(oracle_mask):
 def test_admissible_and_rules_pick_match_the_oracle(matrices, dtype):
     seen = set()
     for A, f in matrices:
-        want = oracle.admissible(A.m, A.nnz, f["max_rd"], f["ndiags"], VALUE_BYTES[dtype])
-        if f["ndiags"] > DIA_MAX_OFFSETS:
-            want &= ~(1 << oracle.CLASSES.index("dia"))
+        want = _oracle_mask(A, f, dtype)
         want_pick = LIB_ID[oracle.CLASSES[oracle.rules_select(f, want)]]
-        vals, _ = stored_values(A, dtype)
-        if dtype == "bf16":
-            vals = vals.view(np.int16)
-        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
-                          torch.from_numpy(np.ascontiguousarray(vals)).to(DEV), dtype)
+        M = _handle(A, dtype)
         assert M.features()["admissible"] & 0xFF == _lib_mask(want), (A.name, dtype)
         M.tune("rules", plan_cache=0)
         assert M.plan()["variant"] == want_pick, (A.name, dtype, M.plan()["name"])
@@ -85,3 +95,25 @@ def test_admissible_and_rules_pick_match_the_oracle(matrices, dtype):
     # the set reaches every rule: DIA, ELL, COO and CSR-vector
     assert {smat.SMAT_V_DIA, smat.SMAT_V_ELL, smat.SMAT_V_COO} <= seen
     assert seen & {smat.SMAT_V_CSR_VEC4, smat.SMAT_V_CSR_VEC8, smat.SMAT_V_CSR_VEC32}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_learned_pick_matches_the_oracle(matrices, dtype):
+    # the network runs in FP32 on the GPU and in FP64 in the oracle: where
+    # the oracle's top probabilities lie within 1e-3 of each other, any of
+    # them is the same decision
+    assert smat.smat_load_model(smat.MODEL_PATH) == smat.SMAT_OK
+    params, mean, std = smat.read_model(smat.MODEL_PATH)
+    cls_of = {v: c for c, v in LIB_ID.items()}
+    for A, f in matrices:
+        want = _oracle_mask(A, f, dtype)
+        best, p = oracle.learned_select(f, want, params, mean, std)
+        M = _handle(A, dtype)
+        M.tune("learned", conf_threshold=0.0, trial_extended=0, plan_cache=0)
+        plan = M.plan()
+        assert plan["trialled"] == 0, (A.name, dtype)
+        c = oracle.CLASSES.index(cls_of[plan["variant"]])
+        near = [k for k in range(len(oracle.CLASSES)) if p[k] >= p[best] - 1e-3]
+        assert c in near, (A.name, dtype, plan["name"], oracle.CLASSES[best], p)
+        assert abs(plan["confidence"] - p[c]) < 1e-3, (A.name, dtype, plan["confidence"], p[c])
+        M.close()
