@@ -8,6 +8,7 @@ leg of ``bench.py`` may import this package; the library under
 Every function restates a definition of the paper:
   spmv_csr        y = alpha*A*x + beta*y in CSR, fixed ascending order (Sec. 2.1, 3)
   spmv_csr_threads  the same on T threads, nonzero-balanced row split (Sec. 6)
+  segment_starts  that split on 8-row boundaries, for per-segment plans (Sec. 6)
   features        Table "Feature parameters of a sparse matrix" (Sec. 4)
   to_ell/to_dia/to_coo  the four basic storage formats (Sec. 2.1)
   to_hyb/sell_layout/to_sell/to_bcsr  further GPU formats left to future work
@@ -143,6 +144,20 @@ def partition_rows(m, rowptr, nthreads):
     b = np.zeros(nthreads + 1, dtype=np.int64)
     lib().oracle_partition_rows(m, prp, nthreads, b.ctypes.data)
     return b
+
+
+def segment_starts(m, rowptr, nseg):
+    """Row starts of the per-segment plans (Sec. 6: the nonzeros divided
+    evenly, at whole rows): the nonzero-balanced bounds of ``partition_rows``,
+    each moved down to a multiple of 8 rows; a bound that does not pass the
+    previous one, or reaches M, is dropped.  Returns [0, ..., M]."""
+    b = partition_rows(m, rowptr, nseg)
+    starts = [0]
+    for r in b[1:-1]:
+        r8 = int(r) // 8 * 8
+        if starts[-1] < r8 < m:
+            starts.append(r8)
+    return starts + [m]
 
 
 def spmv_rows_sampled(rowptr, colidx, val, x, rows, alpha=1.0, beta=0.0, y_in=None):

@@ -28,12 +28,14 @@ def test_segments_choose_per_part_and_match_oracle(dtype):
     # choice is deterministic: DIA for the banded rows, another format for
     # the power-law rows (timed picks on parts this small are within noise)
     R = smat.Segments(M, 4, "rules")
+    assert R.info()["row_starts"] == oracle.segment_starts(A.m, A.rowptr, 4)
     vr = R.info()["variants"]
     assert vr[0] == "dia" and vr[-1] != "dia", vr
     R.close()
     S = smat.Segments(M, 4, "exhaustive", trial_reps=3)
     info = S.info()
     rs = info["row_starts"]
+    assert rs == oracle.segment_starts(A.m, A.rowptr, 4)
     assert rs[0] == 0 and rs[-1] == A.m and all(r % 8 == 0 for r in rs[:-1]) and len(rs) >= 3
     npdt = np.float64 if dtype == "f64" else np.float32
     x = synth.uniform(0, 1, A.n).astype(npdt)

@@ -141,3 +141,30 @@ def test_sampled_rows_match_full():
     rows = np.array([0, 5, 999, 500, 17])
     part = oracle.spmv_rows_sampled(A.rowptr, A.colidx, A.val, x, rows, 1.25, -0.5, y0)
     assert np.array_equal(full[rows], part)
+
+
+def test_segment_starts_closed_forms():
+    # constant rows: the balanced bounds are M t / k, already on 8-row multiples
+    A = synth.blockdiag(4096, 8, 0)
+    assert oracle.segment_starts(A.m, A.rowptr, 4) == [0, 1024, 2048, 3072, 4096]
+    # bounds off the 8-row grid move down: 1000 rows of 5 entries, 3 parts ->
+    # targets 1666, 3333 entries reached at rows 334, 667 -> 328, 664
+    rp = np.arange(1001, dtype=np.int32) * 5
+    assert oracle.segment_starts(1000, rp, 3) == [0, 328, 664, 1000]
+    # every entry in the first row: each bound is row 1, moved down to 0 and dropped
+    rp = np.array([0] + [100] * 50, dtype=np.int32)
+    assert oracle.segment_starts(50, rp, 4) == [0, 50]
+    # fewer than 8 rows: one segment
+    assert oracle.segment_starts(7, np.arange(8, dtype=np.int32), 3) == [0, 7]
+
+
+def test_segment_starts_stay_within_eight_rows_of_balance():
+    A = synth.powerlaw(50000, 1.8, 2000, 9)
+    for k in (2, 3, 4, 7, 16):
+        s = oracle.segment_starts(A.m, A.rowptr, k)
+        assert s[0] == 0 and s[-1] == A.m and all(a < b for a, b in zip(s, s[1:]))
+        assert all(r % 8 == 0 for r in s[:-1])
+        for r in s[1:-1]:
+            # some balanced bound t NNZ / k is first reached within the 8 rows from r
+            hit = [t for t in range(1, k) if r <= np.searchsorted(A.rowptr, A.nnz * t // k) < r + 8]
+            assert hit, (k, r)
