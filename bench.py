@@ -136,6 +136,15 @@ def e2e_issue_order(times):
     return order
 
 
+def break_even_calls(tune_ms, csr_ms, pick_ms):
+    """Products after which tuning has paid for itself (Sec. 7.3, Eq.
+    "num_iter"): n with tune + n * t_pick = n * t_CSR, i.e. tune / (t_CSR -
+    t_pick); None when the pick is not faster than CSR-scalar."""
+    if not csr_ms > pick_ms:
+        return None
+    return tune_ms / (csr_ms - pick_ms)
+
+
 def dram_traffic_record(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     source is unchanged since the capture (else None)."""
@@ -387,6 +396,7 @@ def run_ours(args):
         d = statistics.mean(kev[i][j][0].elapsed_time(kev[i][j][1]) for i in sampled)
         byts = algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"])
         csr_bytes = algorithmic_bytes(p["f"], smat.SMAT_V_CSR_SCALAR, p["dt"])
+        be = break_even_calls(p["plan"]["tune_ms"], p["csr_ms"], p["pick_ms"])
         per.append({"matrix": p["A"].name, "dtype": p["dt"], "nnz": p["A"].nnz, "variant": p["plan"]["name"],
                     "confidence": round(p["plan"]["confidence"], 3), "trialled": p["plan"]["trialled"],
                     "ms_in_step": round(d, 5), "gflops": round(2 * p["A"].nnz / d / 1e6, 2),
@@ -399,8 +409,7 @@ def run_ours(args):
                     "speedup_vs_csr_scalar": round(p["csr_ms"] / p["pick_ms"], 3),
                     "tune_ms": round(p["plan"]["tune_ms"], 2),
                     "tune_overhead_csr_spmvs": round(p["plan"]["tune_ms"] / p["csr_ms"], 1),
-                    "break_even_calls": (round(p["plan"]["tune_ms"] / (p["csr_ms"] - p["pick_ms"]), 1)
-                                         if p["csr_ms"] > p["pick_ms"] else None),
+                    "break_even_calls": None if be is None else round(be, 1),
                     "max_err_normalized": p["max_err"], "alg_bytes": byts, "_d": d})
     dom_i = max(range(len(per)), key=lambda j: per[j]["_d"])
     dom, dp = per[dom_i], prods[dom_i]

@@ -49,3 +49,14 @@ def test_traffic_record_needs_the_current_kernel_source(tmp_path, monkeypatch):
     assert bench.dram_traffic_record("split:f64:m") == 123.0
     assert bench.dram_traffic_record("coo:f64:m") is None     # recorded for another source
     assert bench.dram_traffic_record("sell:f64:m") is None    # not recorded
+
+
+def test_break_even_reproduces_the_papers_count():
+    # Sec. 7.3: tuning costs 19 CSR products and the tuned product takes a
+    # third of CSR's time; it pays after n > 19 / (1 - 1/3) = 28.5 products,
+    # the paper's 29
+    n = bench.break_even_calls(19.0, 1.0, 1.0 / 3.0)
+    assert abs(n - 28.5) < 1e-12 and int(n) + 1 == 29
+    assert bench.break_even_calls(5.0, 1.0, 1.0) is None      # no gain, never pays
+    assert bench.break_even_calls(5.0, 1.0, 2.0) is None
+    assert bench.break_even_calls(0.0, 2.0, 1.0) == 0.0
