@@ -292,7 +292,10 @@ smat_status_t smat_plan_cache_save(const char *path);
  * nothing and returns SMAT_ERR_INVALID_ARG. */
 smat_status_t smat_plan_cache_load(const char *path);
 
+/* Drop every recorded plan (handles keep the plans they already chose). */
 void smat_plan_cache_clear(void);
+
+/* Number of recorded plans (structures) in the process-wide table. */
 int64_t smat_plan_cache_size(void);
 
 /* Median trial time per variant in ms from the last smat_tune (-1 = not run),
@@ -408,6 +411,8 @@ typedef struct {
   double per_matrix_ms; /* median time of the per-matrix launches (-1: not timed) */
 } smat_batch_info_t;
 
+/* Defaults: tile_scale 0 and ctas_per_sm 0 (both autotuned), trial_reps 10,
+ * mode SMAT_BATCH_AUTO.  NULL is a no-op. */
 void smat_batch_opts_default(smat_batch_opts_t *opts);
 
 /* Group `count` handles of one storage dtype.  The handles stay owned by the
@@ -436,6 +441,8 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
 smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *const *xs, const void *betas,
                               void *const *ys, void *stream);
 
+/* The batch's shape and its tuning outcome (fields of smat_batch_info_t).
+ * INVALID_ARG for a NULL batch or info. */
 smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info);
 
 /* Free the batch (not its handles).  NULL is a no-op. */
@@ -469,6 +476,8 @@ smat_status_t smat_segments_spmv(smat_segments_t s, const void *alpha, const voi
  * (row_starts[nseg + 1]); the arrays may be NULL. */
 smat_status_t smat_segments_info(smat_segments_t s, int32_t *nseg, int32_t *variants, int64_t *row_starts);
 
+/* Free the segments' handles, streams and batch (not the parent handle).
+ * NULL is a no-op. */
 smat_status_t smat_segments_destroy(smat_segments_t s);
 
 /* ------------------------------------------------------------------------ */
