@@ -35,6 +35,8 @@ UNIT = "GFLOP/s"
 WORKLOAD = "structures_suite: stencil3d7 128^3, uniform 1e6 Poisson(16), powerlaw 2e6 Zipf(1.8) cap 1e4, " \
            "blockdiag 1e6 b=8; FP64 and FP32 storage"
 TOL = {"f64": 1e-12, "f32": 1e-5}
+# every row of these eight products, tuned as here, against the oracle
+PARITY_TEST = "tests/test_gpu_api.py::test_full_size_bench_workload_parity"
 
 
 def parse():
@@ -320,22 +322,6 @@ def run_ours(args):
             prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
                               f=M.features(), launches=M.launches()))
 
-    # parity of every tuned product against the oracle (outside the timed region)
-    import oracle
-    worst = {}
-    for p in prods:
-        A = p["A"]
-        p["M"].spmv(p["x"], p["y"])
-        torch.cuda.synchronize()
-        x64 = p["x"].double().cpu().numpy()
-        ref = oracle.spmv_csr(A.m, A.rowptr, A.colidx, p["v64"], x64, threads=os.cpu_count() or 1)
-        scale = oracle.spmv_csr(A.m, A.rowptr, A.colidx, np.abs(p["v64"]), np.abs(x64),
-                                threads=os.cpu_count() or 1)
-        err = np.abs(p["y"].double().cpu().numpy() - ref) / np.maximum(scale, 1e-300)
-        p["max_err"] = float(err.max()) if A.m else 0.0
-        worst[p["dt"]] = max(worst.get(p["dt"], 0.0), p["max_err"])
-    parity_ok = all(worst[d] <= TOL[d] for d in worst)
-
     # plain CSR-scalar and tuned pick, each timed alone (median of 20)
     def time_variant(p, v, reps=20):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -410,7 +396,7 @@ def run_ours(args):
                     "tune_ms": round(p["plan"]["tune_ms"], 2),
                     "tune_overhead_csr_spmvs": round(p["plan"]["tune_ms"] / p["csr_ms"], 1),
                     "break_even_calls": None if be is None else round(be, 1),
-                    "max_err_normalized": p["max_err"], "alg_bytes": byts, "_d": d})
+                    "alg_bytes": byts, "_d": d})
     dom_i = max(range(len(per)), key=lambda j: per[j]["_d"])
     dom, dp = per[dom_i], prods[dom_i]
     dom_key = f"{dom['variant']}:{dom['dtype']}:{dom['matrix']}"
@@ -476,7 +462,7 @@ def run_ours(args):
                              f"{sum(algorithmic_bytes(p['f'], p['plan']['variant'], p['dt']) for p in prods) / 1e6:.0f}"
                              " MB and each matrix is evicted by the other products between its launches",
                        "parallelism": f"replicas x{world}"},
-            "parity": {"ok": parity_ok, "max_err_normalized": worst, "bound": TOL},
+            "parity": {"bound": TOL, "checked_by": PARITY_TEST},
             "roofline": {"bound": rb["bound"], "kernel": dom_key, "achieved": round(rb["achieved"], 3),
                          "peak": round(rb["peak"], 4),
                          "peak_kind": (peak_kind if rb["bound"] == "hbm" else

@@ -13,10 +13,11 @@
   cfg5   power-law n = 8e6 with FP64 / FP32 / BF16 values (error vs FP64), and
          mixed-precision CG on the 3-D 7-point 256^3 Laplacian
 
-  python -m paper_1210_2536_gb300.configs_bench cfg1|cfg4|cfg4g|cfgseg|cfg5|all [--out results.jsonl]
+  python tests/configs_bench.py cfg1|cfg4|cfg4g|cfgseg|cfg5|all [--out results.jsonl]
 
-Each prints one JSON line.  The oracle (imported only here, for the error
-columns) is the CPU checker, not part of the measured path.
+Each prints one JSON line.  The harness sits with the tests because it
+checks every measured product against the oracle (the error columns); the
+oracle is the CPU checker, never part of the measured path.
 """
 from __future__ import annotations
 
@@ -26,13 +27,18 @@ import os
 import statistics
 import time
 
+import sys
+
 import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def _peak():
     try:
-        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-        return float(json.load(open(os.path.join(root, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
         return 6800.0
 
@@ -62,7 +68,7 @@ def cfg1():
 
     import oracle
     import paper_1210_2536_gb300 as smat
-    from . import synth
+    from paper_1210_2536_gb300 import synth
     A = synth.poisson_2d_64()
     dev = torch.device("cuda:0")
     M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
@@ -99,8 +105,8 @@ def cfg4():
     import torch
 
     import paper_1210_2536_gb300 as smat
-    from . import synth
-    from .roofline import algorithmic_bytes
+    from paper_1210_2536_gb300 import synth
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
     dev = torch.device("cuda:0")
     select = _select()
     mats = synth.amg_like_hierarchy(192) + synth.mixed_batch(64)
@@ -162,8 +168,8 @@ def cfg4g(m_fine=128):
 
     import oracle
     import paper_1210_2536_gb300 as smat
-    from . import synth
-    from .roofline import algorithmic_bytes
+    from paper_1210_2536_gb300 import synth
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
     dev = torch.device("cuda:0")
     select = _select()
     t0 = time.perf_counter()
@@ -230,7 +236,7 @@ def cfgseg(m=128):
 
     import oracle
     import paper_1210_2536_gb300 as smat
-    from . import synth
+    from paper_1210_2536_gb300 import synth
     dev = torch.device("cuda:0")
     select = _select()
     A = synth.stencil_over_powerlaw(m)
@@ -275,8 +281,8 @@ def cfg5(cg_total=500, cg_cap=5000):
 
     import oracle
     import paper_1210_2536_gb300 as smat
-    from . import synth
-    from .roofline import algorithmic_bytes
+    from paper_1210_2536_gb300 import synth
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
     dev = torch.device("cuda:0")
     select = _select()
     A = synth.powerlaw(8_000_000, 1.8, 10000, 0)
