@@ -1,19 +1,25 @@
 """Measurements of the parity/feature configurations beside the main bench:
 
-  cfg1   2-D 5-point 64x64 FP64: features, exhaustive trial, every variant's
-         latency (the matrix lives in L2: a latency case, not a roofline one)
-  cfg4   27-point hierarchy 192^3..12^3 + 64 mixed matrices, FP64: one batched
-         graph launch vs per-matrix launches (plain and graph-captured)
-  cfg4g  Galerkin AMG hierarchy (smoothed aggregation, P^T A P) of the 27-point
-         operator on 128^3, FP64 and FP32: each level's own plan, one batched
-         launch vs per-matrix launches, every level checked against the oracle
-  cfgseg per-segment plans (Sec. 6) on the 7-point 128^3 stencil stacked over
-         a 2e6-row power-law graph, FP64 and FP32: the whole-matrix plan
-         against 2, 4 and 8 nonzero-balanced segments, each with its own format
-  cfg5   power-law n = 8e6 with FP64 / FP32 / BF16 values (error vs FP64), and
-         mixed-precision CG on the 3-D 7-point 256^3 Laplacian
+  poisson64          2-D 5-point 64x64 FP64: features, exhaustive trial, every
+                     variant's latency (the matrix lives in L2: a latency
+                     case, not a roofline one)
+  batched_hierarchy  27-point hierarchy 192^3..12^3 + 64 mixed matrices, FP64:
+                     one batched graph launch vs per-matrix launches (plain
+                     and graph-captured)
+  galerkin           Galerkin AMG hierarchy (smoothed aggregation, P^T A P) of
+                     the 27-point operator on 128^3, FP64 and FP32: each
+                     level's own plan, one batched launch vs per-matrix
+                     launches, every level checked against the oracle
+  segments           per-segment plans (Sec. 6) on the 7-point 128^3 stencil
+                     stacked over a 2e6-row power-law graph, FP64 and FP32:
+                     the whole-matrix plan against 2, 4 and 8 nonzero-balanced
+                     segments, each with its own format
+  precision          power-law n = 8e6 with FP64 / FP32 / BF16 values (error
+                     vs FP64), and mixed-precision CG on the 3-D 7-point 256^3
+                     Laplacian
 
-  python tests/configs_bench.py cfg1|cfg4|cfg4g|cfgseg|cfg5|all [--out results.jsonl]
+  python tests/configs_bench.py poisson64|batched_hierarchy|galerkin|segments|precision|all \
+      [--out results.jsonl]
 
 Each prints one JSON line.  The harness sits with the tests because it
 checks every measured product against the oracle (the error columns); the
@@ -63,7 +69,7 @@ def _select():
     return "exhaustive"
 
 
-def cfg1():
+def poisson64():
     import torch
 
     import oracle
@@ -101,7 +107,7 @@ def cfg1():
     return out
 
 
-def cfg4():
+def batched_hierarchy():
     import torch
 
     import paper_1210_2536_gb300 as smat
@@ -163,7 +169,7 @@ def cfg4():
     return out
 
 
-def cfg4g(m_fine=128):
+def galerkin(m_fine=128):
     import torch
 
     import oracle
@@ -231,7 +237,7 @@ def cfg4g(m_fine=128):
     return out
 
 
-def cfgseg(m=128):
+def segments(m=128):
     import torch
 
     import oracle
@@ -276,7 +282,7 @@ def cfgseg(m=128):
     return out
 
 
-def cfg5(cg_total=500, cg_cap=5000):
+def precision(cg_total=500, cg_cap=5000):
     import torch
 
     import oracle
@@ -349,14 +355,15 @@ def cfg5(cg_total=500, cg_cap=5000):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["cfg1", "cfg4", "cfg4g", "cfgseg", "cfg5", "all"])
+    ap.add_argument("which", choices=["poisson64", "batched_hierarchy", "galerkin", "segments", "precision", "all"])
     ap.add_argument("--out")
     a = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
-    todo = ["cfg1", "cfg4", "cfg4g", "cfgseg", "cfg5"] if a.which == "all" else [a.which]
+    todo = ["poisson64", "batched_hierarchy", "galerkin", "segments", "precision"] if a.which == "all" else [a.which]
     for w in todo:
-        res = {"cfg1": cfg1, "cfg4": cfg4, "cfg4g": cfg4g, "cfgseg": cfgseg, "cfg5": cfg5}[w]()
+        res = {"poisson64": poisson64, "batched_hierarchy": batched_hierarchy, "galerkin": galerkin,
+               "segments": segments, "precision": precision}[w]()
         line = json.dumps(res)
         print(line, flush=True)
         if a.out:
