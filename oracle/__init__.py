@@ -2,8 +2,9 @@
 
 Thin ctypes/numpy front end to ``oracle.c`` (plain C, FP64, no FMA
 contraction).  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may import this package; the library under
-``paper_1210_2536_gb300`` never does, and the two share no code.
+leg and reference arm (``--impl reference``) of ``bench.py`` may import this
+package; the library under ``paper_1210_2536_gb300`` never does, and the two
+share no code.
 
 Every function restates a definition of the paper:
   spmv_csr        y = alpha*A*x + beta*y in CSR, fixed ascending order (Sec. 2.1, 3)

@@ -3,8 +3,9 @@
  *
  * Plain, slow, obviously correct C, in FP64, compiled with -ffp-contract=off so
  * that every multiply and add below is one IEEE round-to-nearest operation in
- * the order written.  Only the test suite, the smoke check and the CPU-baseline
- * leg of the benchmark may load this library; the product path never does.
+ * the order written.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg and reference arm may load this library; the product path
+ * never does.
  * It shares no code, header or table with the CUDA library.
  *
  * Each function cites the passage of the paper it follows.  Where the paper is
