@@ -60,3 +60,11 @@ def test_break_even_reproduces_the_papers_count():
     assert bench.break_even_calls(5.0, 1.0, 1.0) is None      # no gain, never pays
     assert bench.break_even_calls(5.0, 1.0, 2.0) is None
     assert bench.break_even_calls(0.0, 2.0, 1.0) == 0.0
+
+
+def test_configuration_harness_loads_and_lists_its_workloads():
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "configs_bench.py"), "--help"],
+                         capture_output=True, text=True, check=True).stdout
+    for name in ("poisson64", "batched_hierarchy", "galerkin", "segments", "precision", "all"):
+        assert name in out
