@@ -238,3 +238,31 @@ def test_split_reconstructs_dense(mk, L):
         ch = [(a, b) for rr, a, b in zip(s["crow"], s["cstart"], s["cend"]) if rr == r]
         assert ch[0][0] == A.rowptr[r] and ch[-1][1] == A.rowptr[r + 1]
         assert all(ch[k][1] == ch[k + 1][0] for k in range(len(ch) - 1))
+
+
+def _csr_from_mask(mask):
+    rows, cols = np.nonzero(mask)
+    rowptr = np.zeros(mask.shape[0] + 1, dtype=np.int32)
+    np.add.at(rowptr, rows + 1, 1)
+    return CSR(mask.shape[0], mask.shape[1], np.cumsum(rowptr).astype(np.int32), cols.astype(np.int32),
+               np.ones(len(cols)))
+
+
+def test_bcsr_choose_breaks_ties_and_counts_row_pointers():
+    # a 7 x 11 pattern with 20 blocks of 2x2, 6 of 4x4 and 2 of 8x8: at 4-byte
+    # values both 2 and 4 cost 420 bytes (20*20 + 4*5 = 6*68 + 4*3), 8 costs
+    # 528: the tie goes to the smaller block
+    tie = np.array([[0, 0, 0, 1, 0, 0, 0, 0, 0, 1, 1], [0, 1, 0, 0, 0, 1, 1, 0, 1, 0, 0],
+                    [1, 0, 0, 0, 0, 0, 0, 0, 1, 1, 0], [0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 1],
+                    [0, 1, 1, 1, 1, 0, 1, 0, 1, 1, 0], [0] * 11, [0, 1, 1, 0, 1, 0, 0, 1, 1, 1, 0]], bool)
+    A = _csr_from_mask(tie)
+    assert [int(_bcsr_blocks_brute(tie, c).sum()) for c in (2, 4, 8)] == [20, 6, 2]
+    assert oracle.bcsr_choose(A.m, A.n, A.rowptr, A.colidx, 4) == (2, 20)
+    # an 11 x 4 pattern with 11 / 3 / 2 blocks: at 8-byte values the blocks
+    # alone cost 396 for both 2 and 4, and the row pointers (4 * 7 against
+    # 4 * 4 bytes) make 4 the smaller: 424 against 412
+    rp = np.array([[0, 0, 1, 0], [1, 0, 0, 0], [0, 1, 1, 0], [1, 0, 0, 1], [0, 0, 1, 1], [0, 0, 1, 1],
+                   [0, 0, 0, 1], [1, 1, 0, 1], [0, 1, 0, 1], [1, 0, 0, 0], [1, 1, 0, 1]], bool)
+    A = _csr_from_mask(rp)
+    assert [int(_bcsr_blocks_brute(rp, c).sum()) for c in (2, 4, 8)] == [11, 3, 2]
+    assert oracle.bcsr_choose(A.m, A.n, A.rowptr, A.colidx, 8) == (4, 3)

@@ -168,3 +168,13 @@ def test_segment_starts_stay_within_eight_rows_of_balance():
             # some balanced bound t NNZ / k is first reached within the 8 rows from r
             hit = [t for t in range(1, k) if r <= np.searchsorted(A.rowptr, A.nnz * t // k) < r + 8]
             assert hit, (k, r)
+
+
+def test_partition_bounds_round_targets_down():
+    # one entry per row, 10 rows over 3 threads: the bounds are the first rows
+    # whose start reaches floor(10 t / 3) = 3 and 6 entries
+    assert oracle.partition_rows(10, np.arange(11, dtype=np.int32), 3).tolist() == [0, 3, 6, 10]
+    # rows of 1, 5, 1, 1, 1, 1 entries (10 in all), 4 threads: targets 2, 5, 7
+    # are first reached at rows 2 (start 6), 2 and 3 (start 7)
+    rp = np.array([0, 1, 6, 7, 8, 9, 10], dtype=np.int32)
+    assert oracle.partition_rows(6, rp, 4).tolist() == [0, 2, 2, 3, 6]
