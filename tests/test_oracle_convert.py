@@ -124,3 +124,14 @@ def test_bf16_rounding_against_exact():
 def test_bf16_specials():
     got = oracle.round_bf16(np.array([np.inf, -np.inf, np.nan]))
     assert got[0] == 0x7F80 and got[1] == 0xFF80 and (got[2] & 0x7F80) == 0x7F80 and (got[2] & 0x7F)
+
+
+def test_bf16_overflow_boundary():
+    # the largest finite bfloat16 is (2 - 2^-7) 2^127 (0x7F7F); the halfway
+    # point to 2^128, (2 - 2^-8) 2^127, ties to the even neighbour, which is
+    # 2^128 and therefore +inf; anything in [2^128, 2^129) is +inf too
+    top = (2.0 - 2.0 ** -7) * 2.0 ** 127
+    half = (2.0 - 2.0 ** -8) * 2.0 ** 127
+    got = oracle.round_bf16(np.array([top, np.nextafter(half, 0.0), half, 2.0 ** 128, 1.5 * 2.0 ** 128,
+                                      -1.5 * 2.0 ** 128]))
+    assert got.tolist() == [0x7F7F, 0x7F7F, 0x7F80, 0x7F80, 0x7F80, 0xFF80]
