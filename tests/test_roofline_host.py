@@ -20,6 +20,14 @@ def test_algorithmic_bytes_closed_forms(dt, sv, sx):
     assert R.algorithmic_bytes(F, R.V_HYB, dt) == (sv + 4) * 4 * 1000 + (sv + 8) * 1200 + xy
     assert R.algorithmic_bytes(F, R.V_BCSR, dt) == (sv * 4 + 4) * 1800 + 4 * 501 + xy
     assert R.algorithmic_bytes(F, R.V_SPLIT, dt) == (sv + 4) * 2000 + 20 * 5 + (sv + 8) * 3000 + 4 * 3 + xy
+    # SELL: slots, a 4-byte row index per position (32 per slice), a width and
+    # a slice pointer per slice, and the closing pointer
+    assert R.algorithmic_bytes(F, R.V_SELL, dt) == (sv + 4) * 6400 + 4 * 32 * 32 + 12 * 32 + 8 + xy
+    # every CSR kernel moves the same arrays
+    for v in (1, 2, 3, 4, 8):
+        assert R.algorithmic_bytes(F, v, dt) == R.algorithmic_bytes(F, 0, dt)
+    with pytest.raises(ValueError):
+        R.algorithmic_bytes(F, 13, dt)
 
 
 def test_l2_sectors_on_random_columns():
