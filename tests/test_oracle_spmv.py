@@ -154,6 +154,9 @@ def test_segment_starts_closed_forms():
     # every entry in the first row: each bound is row 1, moved down to 0 and dropped
     rp = np.array([0] + [100] * 50, dtype=np.int32)
     assert oracle.segment_starts(50, rp, 4) == [0, 50]
+    # every entry in the last of 16 rows: each bound is row 16 = M, dropped
+    rp = np.array([0] * 16 + [100], dtype=np.int32)
+    assert oracle.segment_starts(16, rp, 4) == [0, 16]
     # fewer than 8 rows: one segment
     assert oracle.segment_starts(7, np.arange(8, dtype=np.int32), 3) == [0, 7]
 
