@@ -485,7 +485,8 @@ def learned_select(f, mask, params, mean, std):
     model's mean and standard deviation (a deviation of 0 leaves the input
     unscaled), the network's logits, a softmax over the admissible classes
     only (others get probability 0), and the most probable class (the lowest
-    id among equals).  FP64 throughout."""
+    id among equals; with no admissible class, all probabilities are 0 and
+    the id is 0, a case the library refuses).  FP64 throughout."""
     x = selector_inputs(f)
     sd = np.where(np.asarray(std, np.float64) > 0, np.asarray(std, np.float64), 1.0)
     xs = (x - np.asarray(mean, np.float64)) / sd

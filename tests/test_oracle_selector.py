@@ -106,3 +106,9 @@ def test_network_sees_the_standardised_inputs_in_order():
     assert oracle.learned_select(f, ALL8, p, mean2, std)[0] == C["coo"]
     rest = [c for c in range(8) if c != C["coo"]]
     assert oracle.learned_select(f, ALL8 & ~(1 << C["coo"]), p, mean2, std)[0] == rest[int(np.argmax(want[rest]))]
+
+
+def test_no_admissible_class():
+    f = oracle.features(10, 10, np.arange(11, dtype=np.int32), np.arange(10, dtype=np.int32))
+    v, p = oracle.learned_select(f, 0, _bias_net(np.arange(8.0)), np.zeros(12), np.ones(12))
+    assert v == 0 and not p.any()
