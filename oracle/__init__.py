@@ -448,7 +448,9 @@ def rules_select(f, mask) -> int:
            [1, 4) marks a small-world matrix, stored as COO; otherwise CSR,
            whose GPU kernel is CSR-vector with the lane count that fits the
            mean row length (4 below 8 entries, 8 below 24, else 32).
-    A rule whose format is not admissible does not fire."""
+    A rule whose format is not admissible does not fire; when none fires and
+    the CSR-vector width is not admissible either, the lowest admissible id
+    is the pick (ValueError when no class is admissible)."""
     def ok(name):
         return (mask >> CLASSES.index(name)) & 1
 
@@ -462,7 +464,10 @@ def rules_select(f, mask) -> int:
     lanes = "csr_vec4" if f["aver_rd"] < 8.0 else ("csr_vec8" if f["aver_rd"] < 24.0 else "csr_vec32")
     if ok(lanes):
         return CLASSES.index(lanes)
-    return next(c for c in range(len(CLASSES)) if (mask >> c) & 1)
+    live = [c for c in range(len(CLASSES)) if (mask >> c) & 1]
+    if not live:
+        raise ValueError("no admissible class")   # the library refuses to tune then
+    return live[0]
 
 
 # ---------------------------------------------------------------------------

@@ -225,3 +225,8 @@ def test_rule_order_and_inadmissible_formats():
     assert oracle.rules_select(both, ALWAYS) == C["coo"]                   # then COO before CSR
     only_scalar = 1 << C["csr_scalar"]
     assert oracle.rules_select(_f(), only_scalar) == C["csr_scalar"]
+
+
+def test_no_admissible_class_is_an_error():
+    with pytest.raises(ValueError):
+        oracle.rules_select(_f(), 0)
