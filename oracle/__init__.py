@@ -16,7 +16,7 @@ Every function restates a definition of the paper:
                   in Sec. 8 (HYB, SELL-C-sigma, BCSR; published definitions)
   split_rows      rows split by length: long rows in chunks, short rows as COO
   mlp_*           the learned replacement of the ruleset classifier (Sec. 5)
-  admissible      the 20x fill rule plus a byte cap (Sec. 2.3)
+  admissible      the 20x fill rule plus a byte cap and a diagonal-count cap (Sec. 2.3)
   rules_select    the observations of Sec. 4 as an ordered rule set (Sec. 6)
   selector_inputs/learned_select  the learned selector's inputs and pick
 Readings taken where the paper is silent are listed in ``oracle.c``.
@@ -405,7 +405,14 @@ def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 CLASSES = ("csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo")
 
 
-def admissible(m, nnz, max_rd, ndiags, value_bytes, fill_ratio_max=20, bytes_cap=4.0) -> int:
+# Reading: the paper bounds the diagonals only through the 20x fill rule; a
+# GPU DIA product keeps its offsets in on-chip memory, and this build's reading
+# caps them at 8192 (32 KB of int32 offsets) however the fill rule falls.
+DIA_MAX_OFFSETS = 8192
+
+
+def admissible(m, nnz, max_rd, ndiags, value_bytes, fill_ratio_max=20, bytes_cap=4.0,
+               dia_max_offsets=DIA_MAX_OFFSETS) -> int:
     """Bit mask over CLASSES (bit c set = class c may be used).
 
     CSR, in every kernel, and COO store only the entries: always admissible.
@@ -417,6 +424,8 @@ def admissible(m, nnz, max_rd, ndiags, value_bytes, fill_ratio_max=20, bytes_cap
     CSR arrays (values, int32 columns, int32 row pointers):
       ELL  (value_bytes + 4) * max_RD * P
       DIA  value_bytes * Ndiags * P + 4 * Ndiags   (values plus the offsets)
+    and DIA takes at most ``dia_max_offsets`` diagonals (8192 by default), a
+    reading stated beside DIA_MAX_OFFSETS: the paper sets no such number.
     """
     mask = 0
     for c in ("csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "coo"):
@@ -426,7 +435,7 @@ def admissible(m, nnz, max_rd, ndiags, value_bytes, fill_ratio_max=20, bytes_cap
     if m > 0 and max_rd > 0 and max_rd * m <= fill_ratio_max * nnz and \
             (value_bytes + 4) * max_rd * P <= bytes_cap * csr_bytes:
         mask |= 1 << CLASSES.index("ell")
-    if m > 0 and ndiags > 0 and ndiags * m <= fill_ratio_max * nnz and \
+    if m > 0 and 0 < ndiags <= dia_max_offsets and ndiags * m <= fill_ratio_max * nnz and \
             value_bytes * ndiags * P + 4 * ndiags <= bytes_cap * csr_bytes:
         mask |= 1 << CLASSES.index("dia")
     return mask

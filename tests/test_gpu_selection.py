@@ -18,8 +18,6 @@ VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
 LIB_ID = {"csr_scalar": smat.SMAT_V_CSR_SCALAR, "csr_vec4": smat.SMAT_V_CSR_VEC4, "csr_vec8": smat.SMAT_V_CSR_VEC8,
           "csr_vec32": smat.SMAT_V_CSR_VEC32, "csr_merge": smat.SMAT_V_CSR_MERGE, "ell": smat.SMAT_V_ELL,
           "dia": smat.SMAT_V_DIA, "coo": smat.SMAT_V_COO}
-# the DIA kernel stages its offsets in shared memory and takes at most 8192
-DIA_MAX_OFFSETS = 8192
 
 
 def _est_nnz(kind, p):
@@ -62,10 +60,7 @@ def matrices():
 
 
 def _oracle_mask(A, f, dtype):
-    want = oracle.admissible(A.m, A.nnz, f["max_rd"], f["ndiags"], VALUE_BYTES[dtype])
-    if f["ndiags"] > DIA_MAX_OFFSETS:
-        want &= ~(1 << oracle.CLASSES.index("dia"))
-    return want
+    return oracle.admissible(A.m, A.nnz, f["max_rd"], f["ndiags"], VALUE_BYTES[dtype])
 
 
 def _handle(A, dtype):
