@@ -540,15 +540,18 @@ smat_status_t smat_cast_f64_to_bf16(const double *in, uint16_t *out, int64_t n, 
  * colidx[nnz], vals[nnz] of the storage type), x[n] and y[m], all DEVICE
  * pointers, and alpha/beta as HOST pointers to one scalar of the compute type
  * (FP64 for SMAT_F64, FP32 otherwise).  The input must be canonical CSR; it is
- * not validated.
+ * not validated.  alpha == 0 gives y = beta*y (0 when beta == 0) without
+ * reading A or x, and beta == 0 makes y write-only, as in smat_spmv.
  * The kernels' only scratch, one carry and one merge-path coordinate per
  * tile of 2048 merge items, lives in a fixed 1.25 MiB array in the library's
  * device memory, held by every GPU that loads the library until the process
  * exits.  Limit: ceil((m + nnz) /
  * 2048) <= 65536, i.e. m + nnz <= 134,217,728; larger inputs return
  * SMAT_ERR_UNSUPPORTED without launching anything.  The first call on each
- * device looks up the array's address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Every call shares the array, so calls
+ * device looks up the array's address (cudaGetSymbolAddress) and keeps it for
+ * the rest of the process; make that first call before any stream capture,
+ * and do not call this entry point again after a cudaDeviceReset of a device
+ * it has used (the kept address would be stale).  Every call shares the array, so calls
  * whose kernels overlap on the GPU race: order them on one stream or
  * synchronise between them.  Asynchronous on `stream`; only launch errors are
  * reported. */

@@ -975,12 +975,15 @@ cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, con
 namespace smat {
 namespace {
 
+// The array holds three regions, for at most 65,536 tiles of 2048 merge items:
 constexpr long long NOALLOC_MAX_TILES = 65536;
-// per tile: an int32 row (256 KiB in all) and a value of up to 8 bytes (512 KiB)
+// [0, 256 KiB): each tile's carry row, int32
 constexpr size_t NOALLOC_ROW_BYTES = NOALLOC_MAX_TILES * 4;
-// then a value of up to 8 bytes per tile (512 KiB), then the tile boundaries'
-// merge-path coordinates, 8 bytes each (512 KiB + 8)
-constexpr size_t NOALLOC_COORD_OFFSET = NOALLOC_ROW_BYTES + NOALLOC_MAX_TILES * 8;
+// [256 KiB, 768 KiB): each tile's carry value, 8 bytes (FP64) or 4 (FP32)
+constexpr size_t NOALLOC_VAL_BYTES = NOALLOC_MAX_TILES * 8;
+// [768 KiB, 1.25 MiB + 8 B): the merge-path coordinate (row, entry) of each
+// of the tiles + 1 tile boundaries, int2
+constexpr size_t NOALLOC_COORD_OFFSET = NOALLOC_ROW_BYTES + NOALLOC_VAL_BYTES;
 constexpr size_t NOALLOC_BYTES = NOALLOC_COORD_OFFSET + (NOALLOC_MAX_TILES + 1) * 8;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -988,7 +991,10 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch array for the current device (looked up once).
+// Device address of the scratch array for the current device, looked up on
+// the first call with that device current and kept for the process's life:
+// after cudaDeviceReset the kept address is stale, so this entry point must
+// not be called again in a process that has reset a device it used.
 cudaError_t noalloc_scratch(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1031,6 +1037,13 @@ cudaError_t merge_noalloc_typed(long long m, long long nnz, const int32_t *rowpt
                                 void *y_p, unsigned char *scratch, cudaStream_t s) {
   typedef typename Compute<V>::T T;
   const T alpha = *(const T *)alpha_p, beta = *(const T *)beta_p;
+  // alpha == 0: y = beta*y (0 when beta == 0), reading neither A nor x, as in
+  // smat_spmv, so that non-finite values in x cannot reach y
+  if (alpha == (T)0) {
+    if (beta == (T)0) return cudaMemsetAsync(y_p, 0, (size_t)m * sizeof(T), s);
+    beta_only_kernel<T><<<grid_for(m, 256, 152 * 8), 256, 0, s>>>((T *)y_p, m, beta);
+    return cudaGetLastError();
+  }
   switch (epi_mode((double)alpha, (double)beta)) {
     case EPI_COPY: return merge_noalloc_mode<V, EPI_COPY>(m, nnz, rowptr, colidx, vals, alpha, x_p, beta, y_p, scratch, s);
     case EPI_SCALE: return merge_noalloc_mode<V, EPI_SCALE>(m, nnz, rowptr, colidx, vals, alpha, x_p, beta, y_p, scratch, s);
