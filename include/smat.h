@@ -229,6 +229,24 @@ smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const
 smat_status_t smat_spmv_variant(smat_handle_t h, smat_variant_t v, const void *alpha,
                                 const void *x, const void *beta, void *y, void *stream);
 
+/* The kernel behind a variant whose format has more than one implementation
+ * (the per-format choice of implementation, Sec. 3).  The library times the
+ * candidates when it builds the format and keeps the faster; smat_get_kernel
+ * reads that choice and smat_set_kernel pins one for later products:
+ *   SMAT_V_DIA  0: direct 16-byte loads; 1..2: the stripes of each tile of
+ *               rows staged in shared memory by bulk asynchronous copies, a
+ *               producer warp feeding a ring of stages, in two launch
+ *               shapes (consumer warps, CTAs per SM, stages, stage size):
+ *               1 (16, 1, 4, 48 KB), 2 (16, 2, 3, 32 KB); a shape needs 32
+ *               rows of every stripe within its stage;
+ *   SMAT_V_ELL  0: consecutive rows per thread; 1: lane-striped rows.
+ * Returns SMAT_ERR_UNSUPPORTED when the variant's format is not built yet (a
+ * tune picked it, or a product through smat_spmv_variant built it) or the
+ * kernel cannot run this matrix; SMAT_ERR_INVALID_ARG for other variants or
+ * kernel ids.  Must not overlap products on the handle. */
+smat_status_t smat_set_kernel(smat_handle_t h, smat_variant_t v, int32_t kernel);
+smat_status_t smat_get_kernel(smat_handle_t h, smat_variant_t v, int32_t *kernel);
+
 /* Same product with x and y in HOST memory (pinned or pageable): x is copied to
  * a device staging buffer, the product runs through the plan, y is copied
  * back (and, when beta != 0, copied in first).  Returns after `stream` has
@@ -349,6 +367,24 @@ smat_status_t smat_export_format(smat_handle_t h, smat_format_t fmt, int32_t *id
  * INVALID_ARG (n < 1, n > 2^31 - 1, nidx < 8, reps < 1), ALLOC, CUDA. */
 smat_status_t smat_measure_gather_rate(int64_t n, int64_t nidx, smat_dtype_t dtype, int32_t reps,
                                        double *gathers_per_s);
+
+/* Measured ceiling for FP64-arithmetic-bound products (no counterpart in the
+ * paper): a kernel of 8 CTAs of 256 threads per SM runs eight independent
+ * chains of 4096 FP64 fused multiply-adds per thread and nothing else.  Runs
+ * 3 untimed and `reps` timed passes on the legacy default stream and writes
+ * the median rate in fused multiply-adds per second (2 flops each).  An FP64
+ * product spends one such operation per stored slot, so it cannot run faster
+ * than slots / rate; the benchmark uses this as the FP64 roof.  Allocates and
+ * frees its own small device buffers.  Errors: INVALID_ARG (reps < 1), ALLOC,
+ * CUDA. */
+smat_status_t smat_measure_fp64_rate(int32_t reps, double *fma_per_s);
+
+/* Bounded waits in the library's pipelined kernels (the staged DIA product)
+ * that ran out since the library was loaded, on the current device: each such
+ * wait means a product whose y is not valid (its kernel gave up after about
+ * one second instead of hanging).  Stays 0 in correct operation.  Copies the
+ * device counter to *count (synchronous).  Errors: INVALID_ARG (NULL), CUDA. */
+smat_status_t smat_get_wait_timeouts(uint64_t *count);
 
 /* ------------------------------------------------------------------------ */
 /* Learned selector (replaces the ruleset classifier of Sec. 5)             */

@@ -96,6 +96,8 @@ _SIGS = {
     "smat_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _I32]),
+    "smat_get_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_spmv_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_launches": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
@@ -109,6 +111,8 @@ _SIGS = {
     "smat_plan_cache_size": (_I64, []),
     "smat_get_timings": (ctypes.c_int, [_VP, _VP]),
     "smat_measure_gather_rate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int32, _VP]),
+    "smat_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int32, _VP]),
+    "smat_get_wait_timeouts": (ctypes.c_int, [_VP]),
     "smat_convert": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_format_dims": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_export_format": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
@@ -281,6 +285,20 @@ def smat_measure_gather_rate(n: int, nidx: int, dtype: str = "f64", reps: int = 
     r = ctypes.c_double(0.0)
     _check(lib().smat_measure_gather_rate(n, nidx, DTYPES[dtype], reps, ctypes.byref(r)), "smat_measure_gather_rate")
     return float(r.value)
+
+
+def smat_measure_fp64_rate(reps: int = 10) -> float:
+    """FP64 fused multiply-adds per second this GPU sustains (see smat.h)."""
+    r = ctypes.c_double(0.0)
+    _check(lib().smat_measure_fp64_rate(reps, ctypes.byref(r)), "smat_measure_fp64_rate")
+    return float(r.value)
+
+
+def smat_get_wait_timeouts() -> int:
+    """Bounded waits in the pipelined kernels that ran out so far (0 when all is well)."""
+    c = ctypes.c_uint64(0)
+    _check(lib().smat_get_wait_timeouts(ctypes.byref(c)), "smat_get_wait_timeouts")
+    return int(c.value)
 
 
 def smat_format_dims(h, fmt):
@@ -612,6 +630,17 @@ class SpMatrix:
 
     def timings(self) -> np.ndarray:
         return smat_get_timings(self.h)
+
+    def kernel(self, variant) -> int:
+        """The kernel behind ``variant`` (DIA: 0 direct, 1 staged; ELL: 0
+        consecutive rows, 1 lane-striped); its format must be built."""
+        k = ctypes.c_int32(0)
+        _check(lib().smat_get_kernel(self.h, int(variant), ctypes.byref(k)), "smat_get_kernel")
+        return int(k.value)
+
+    def set_kernel(self, variant, kernel: int):
+        """Pin the kernel behind ``variant`` for later products (see kernel())."""
+        _check(lib().smat_set_kernel(self.h, int(variant), int(kernel)), "smat_set_kernel")
 
     def convert(self, fmt, stream=None):
         _check(smat_convert(self.h, fmt, _stream_ptr(stream)), "smat_convert")

@@ -528,14 +528,16 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
 
 // Kernel search for ELL / DIA (the paper's per-format implementation choice,
 // Sec. 3): time the candidate batch widths once on zero vectors, keep the
-// faster; for ELL then time the lane-striped row mapping at that width.  Run
-// when the format is built.
+// faster; for ELL then time the lane-striped row mapping at that width, for
+// DIA the kernel whose stripes are staged by bulk copies.  Run when the
+// format is built.
 smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   int cand[2];
   const int nc = batch_width_candidates(h, variant, cand);
   int &slot = variant == SMAT_V_DIA ? h->dia_u : h->ell_u;
   const bool try_lane = variant == SMAT_V_ELL;
-  if (nc == 1 && !try_lane) {
+  const bool try_staged = variant == SMAT_V_DIA && dia_staged_ok(h, 1);
+  if (nc == 1 && !try_lane && !try_staged) {
     slot = cand[0];
     return SMAT_OK;
   }
@@ -579,6 +581,15 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
     TRYS(time_it(best_u, 1, &med));
     h->ell_lane = med < best ? 1 : 0;
   }
+  if (try_staged) {
+    h->dia_staged = 0;
+    for (int k = 1; k <= dia_staged_kernels(); ++k) {
+      if (!dia_staged_ok(h, k)) continue;
+      float med;
+      TRYS(time_it(best_u, 1 + k, &med));
+      if (med < best) { best = med; h->dia_staged = k; }
+    }
+  }
   return SMAT_OK;
 }
 
@@ -611,6 +622,7 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
     TRY(launch_to_dia(h, h->dia_off, nd, h->dia_val, s));
     TRY(cudaStreamSynchronize(s));  // the host offsets buffer must outlive the copy
     h->dia_u = 0;
+    h->dia_staged = 0;
     return measure_batch_width(h, SMAT_V_DIA, s);
   }
   if (fmt == SMAT_FMT_COO) {
@@ -1173,6 +1185,39 @@ smat_status_t smat_get_plan_source(smat_handle_t h, int32_t *from_cache) {
   if (!from_cache) return SMAT_ERR_INVALID_ARG;
   *from_cache = h->plan_cached ? 1 : 0;
   return SMAT_OK;
+}
+
+smat_status_t smat_set_kernel(smat_handle_t h, smat_variant_t v, int32_t kernel) {
+  TRYS(check_handle(h));
+  if (v == SMAT_V_DIA) {
+    if (kernel < 0 || kernel > dia_staged_kernels()) return SMAT_ERR_INVALID_ARG;
+    if (!h->dia_val || (kernel > 0 && !dia_staged_ok(h, kernel))) return SMAT_ERR_UNSUPPORTED;
+    h->dia_staged = kernel;
+    return SMAT_OK;
+  }
+  if (v == SMAT_V_ELL) {
+    if (kernel != 0 && kernel != 1) return SMAT_ERR_INVALID_ARG;
+    if (!h->ell_val) return SMAT_ERR_UNSUPPORTED;
+    h->ell_lane = kernel;
+    return SMAT_OK;
+  }
+  return SMAT_ERR_INVALID_ARG;
+}
+
+smat_status_t smat_get_kernel(smat_handle_t h, smat_variant_t v, int32_t *kernel) {
+  TRYS(check_handle(h));
+  if (!kernel) return SMAT_ERR_INVALID_ARG;
+  if (v == SMAT_V_DIA) {
+    if (!h->dia_val) return SMAT_ERR_UNSUPPORTED;
+    *kernel = h->dia_staged;
+    return SMAT_OK;
+  }
+  if (v == SMAT_V_ELL) {
+    if (!h->ell_val) return SMAT_ERR_UNSUPPORTED;
+    *kernel = h->ell_lane;
+    return SMAT_OK;
+  }
+  return SMAT_ERR_INVALID_ARG;
 }
 
 smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const void *beta, void *y,

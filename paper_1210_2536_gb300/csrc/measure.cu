@@ -5,6 +5,9 @@
 // gathers x at those indices, 8 per thread, with nothing else to do: its rate
 // is the ceiling a product's gathers can reach on this GPU.  The paper has no
 // counterpart (it measures on CPUs); this is measurement support only.
+// Beside it, the FP64 arithmetic ceiling: GB300 runs FP64 fused multiply-adds
+// at a small fraction of its FP32 rate, low enough to bind FP64 products
+// whose bytes stream at close to HBM speed.
 #include <algorithm>
 #include <vector>
 
@@ -69,8 +72,71 @@ cudaError_t run_gather(long long n, long long nidx, int reps, double *rate) {
   return cudaSuccess;
 }
 
+// FP64 fused multiply-adds: eight independent chains per thread, operands
+// loaded at run time so nothing folds, one store per thread at the end.
+__global__ void __launch_bounds__(256) fp64_fma_kernel(const double *__restrict__ bc, double *__restrict__ out,
+                                                       int iters) {
+  const double b = bc[0], c = bc[1];
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1e-3 * (double)(threadIdx.x + k);
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t run_fp64(int reps, double *rate) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)sms * 8u;
+  const int iters = 4096;
+  void *pbc = nullptr, *po = nullptr;
+  e = dev_alloc(&pbc, 2 * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc(&po, (size_t)grid * 256 * sizeof(double));
+  const double bc[2] = {0.999, 1e-3};
+  if (e == cudaSuccess) e = cudaMemcpy(pbc, bc, sizeof(bc), cudaMemcpyHostToDevice);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<float> ms;
+  for (int r = -3; r < reps && e == cudaSuccess; ++r) {  // three untimed passes first
+    cudaEventRecord(e0);
+    fp64_fma_kernel<<<grid, 256>>>((const double *)pbc, (double *)po, iters);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && r >= 0) ms.push_back(t);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dev_free(pbc); dev_free(po);
+  if (e != cudaSuccess) return e;
+  std::sort(ms.begin(), ms.end());
+  *rate = (double)grid * 256.0 * iters * 8.0 / (ms[ms.size() / 2] * 1e-3);
+  return cudaSuccess;
+}
+
 }  // namespace
 }  // namespace smat
+
+extern "C" smat_status_t smat_measure_fp64_rate(int32_t reps, double *fma_per_s) {
+  if (!fma_per_s || reps < 1) return SMAT_ERR_INVALID_ARG;
+  const cudaError_t e = smat::run_fp64(reps, fma_per_s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SMAT_ERR_ALLOC;
+  }
+  return e == cudaSuccess ? SMAT_OK : SMAT_ERR_CUDA;
+}
 
 extern "C" smat_status_t smat_measure_gather_rate(int64_t n, int64_t nidx, smat_dtype_t dtype, int32_t reps,
                                                   double *gathers_per_s) {

@@ -83,6 +83,7 @@ struct smat_s {
   int64_t ell_K = 0;
   int ell_u = 0, dia_u = 0;  // measured batch widths (0: not measured yet)
   int ell_lane = 0;          // measured ELL row mapping: 0 consecutive rows per thread, 1 lane-striped
+  int dia_staged = 0;        // measured DIA kernel: 0 direct loads, 1.. stripes staged by bulk copies (shape id)
   int32_t *ell_col = nullptr;
   void *ell_val = nullptr;
   // DIA
@@ -218,10 +219,18 @@ int spmv_launch_count(const smat_s *h, int variant);
 // Candidate batch widths of an ELL / DIA product (returns how many: 1 or 2).
 int batch_width_candidates(const smat_s *h, int variant, int out[2]);
 // ELL / DIA product with an explicit batch width and (ELL) row mapping
-// (lane: -1 the handle's, 0 consecutive rows per thread, 1 lane-striped), for
-// measuring them.
+// (lane: -1 the handle's, 0 consecutive rows per thread, 1 lane-striped; for
+// DIA 2 + k is staged shape k), for measuring them.
 cudaError_t launch_spmv_width(const smat_s *h, int variant, int u, int lane, const void *alpha, const void *x,
                               const void *beta, void *y, cudaStream_t s);
+// DIA with its stripes staged in shared memory by bulk copies (staged.cu),
+// in launch shapes 1..dia_staged_kernels(): whether the handle's DIA arrays
+// fit shape `kernel`'s tiles, and the product (alpha/beta host scalars of the
+// compute type; wait_limit in SM cycles, 0 for the default of about one second).
+int dia_staged_kernels();
+bool dia_staged_ok(const smat_s *h, int kernel);
+cudaError_t launch_dia_staged(const smat_s *h, int kernel, const void *alpha, const void *x, const void *beta,
+                              void *y, cudaStream_t s, long long wait_limit = 0);
 // SpMV through one variant; alpha/beta are host scalars of the compute type.
 // claim: as in stream_scratch (false for the tuner's timing products).
 cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const void *x,

@@ -784,6 +784,8 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
       launch_ell_dia<V, MODE, false>(h, x, ep, y, s, u_req, lane_req);
       break;
     case SMAT_V_DIA:
+      if (lane_req >= 2 || (lane_req < 0 && h->dia_staged))
+        return launch_dia_staged(h, lane_req >= 2 ? lane_req - 1 : h->dia_staged, &alpha, x, &beta, y, s);
       launch_ell_dia<V, MODE, true>(h, x, ep, y, s, u_req, lane_req);
       break;
     case SMAT_V_COO: {

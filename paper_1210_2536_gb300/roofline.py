@@ -128,19 +128,23 @@ def l2_sectors(f: dict, variant: int, dtype: str) -> float:
     return float(gathers) + byts / 32.0 + extra
 
 
-def bound(f: dict, variant: int, dtype: str, seconds: float, hbm_gbs: float) -> dict:
+def bound(f: dict, variant: int, dtype: str, seconds: float, hbm_gbs: float,
+          fp64_tflops: float | None = None) -> dict:
     """The binding roofline of one launch: HBM bytes, or (FP64 storage) FP64
-    arithmetic, whichever needs more time at peak; achieved/peak for it."""
+    arithmetic, whichever needs more time at peak; achieved/peak for it.
+    fp64_tflops is the measured FP64 roof (smat_measure_fp64_rate x 2);
+    without it the derived FP64_PEAK_TFLOPS serves."""
     byts = algorithmic_bytes(f, variant, dtype)
     t_hbm = byts / (hbm_gbs * 1e9)
     out = {"bound": "hbm", "achieved": byts / seconds / 1e9, "peak": hbm_gbs, "unit": "GB/s",
            "alg_bytes": byts}
     if dtype == "f64":
+        roof = fp64_tflops if fp64_tflops else FP64_PEAK_TFLOPS
         ops = fp64_ops(f, variant)
-        t_alu = 2.0 * ops / (FP64_PEAK_TFLOPS * 1e12)
+        t_alu = 2.0 * ops / (roof * 1e12)
         out["fp64_frac"] = t_alu / seconds
         if t_alu > t_hbm:
-            out.update(bound="alu", achieved=2.0 * ops / seconds / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+            out.update(bound="alu", achieved=2.0 * ops / seconds / 1e12, peak=roof, unit="TFLOP/s",
                        alg_fp64_fma=ops)
     out["hbm_frac"] = t_hbm / seconds
     out["frac"] = out["achieved"] / out["peak"]

@@ -5,6 +5,7 @@ see roofline.py).  Used for kernel studies and profiler captures:
   python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --dtype f64 --variant all
   python -m paper_1210_2536_gb300.spmv_case --matrix powerlaw:2000000 --variant coo --reps 3
   python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --variant dia --cold
+  python -m paper_1210_2536_gb300.spmv_case --matrix stencil3d7:128 --variant dia --kernel all
 
 Matrices: stencil2d5:<m>, stencil3d7:<m>, stencil3d27:<m>, uniform:<n>[:lambda],
 powerlaw:<n>[:alpha], blockdiag:<n>[:b].
@@ -49,6 +50,9 @@ def main():
     ap.add_argument("--variant", default="all")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--kernel", default="measured",
+                    help="kernels behind DIA / ELL: 'measured' (the handle's choice), or 'all' to time each "
+                         "(DIA: direct / staged; ELL: consecutive / lane-striped)")
     ap.add_argument("--cold", action="store_true",
                     help="write a buffer of twice the L2 size between timed repetitions (x and the matrix "
                          "start from HBM)")
@@ -83,26 +87,41 @@ def main():
     if a.cold:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
         flush = torch.empty(2 * l2 // 4, dtype=torch.int32, device=dev)
+    kernel_names = {smat.SMAT_V_DIA: ("direct", "staged1", "staged2"),
+                    smat.SMAT_V_ELL: ("rows", "lanes")}
     for v in vs:
         try:
             M.spmv(x, y, variant=v)   # builds the format; further formats may not be admissible
         except smat.SmatError:
             continue
         f = M.features()
-        for _ in range(a.warmup):
-            M.spmv(x, y, variant=v)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
-        for s, e in ev:
-            if flush is not None:
-                flush.fill_(1)
-            s.record()
-            M.spmv(x, y, variant=v)
-            e.record()
-        torch.cuda.synchronize()
-        ms = statistics.median(s.elapsed_time(e) for s, e in ev)
-        b = algorithmic_bytes(f, v, a.dtype)
-        out["variants"][names[v]] = {"ms": round(ms, 5), "gflops": round(2 * A.nnz / ms / 1e6, 1),
-                                     "gbs": round(b / ms / 1e6, 1), "hbm_frac": round(b / ms / 1e6 / peak, 4)}
+        kernels = [None]
+        if v in kernel_names:
+            measured = M.kernel(v)
+            kernels = list(range(len(kernel_names[v]))) if a.kernel == "all" else [measured]
+        for k in kernels:
+            label = names[v]
+            if k is not None:
+                try:
+                    M.set_kernel(v, k)
+                except smat.SmatError:
+                    continue
+                label = f"{names[v]}:{kernel_names[v][k]}" + ("*" if k == measured else "")
+            for _ in range(a.warmup):
+                M.spmv(x, y, variant=v)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(a.reps)]
+            for s, e in ev:
+                if flush is not None:
+                    flush.fill_(1)
+                s.record()
+                M.spmv(x, y, variant=v)
+                e.record()
+            torch.cuda.synchronize()
+            ms = statistics.median(s.elapsed_time(e) for s, e in ev)
+            b = algorithmic_bytes(f, v, a.dtype)
+            out["variants"][label] = {"ms": round(ms, 5), "gflops": round(2 * A.nnz / ms / 1e6, 1),
+                                      "gbs": round(b / ms / 1e6, 1), "hbm_frac": round(b / ms / 1e6 / peak, 4)}
     print(json.dumps(out))
     M.close()
 

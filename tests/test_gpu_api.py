@@ -174,6 +174,15 @@ def test_gather_rate_measurement():
         smat.smat_measure_gather_rate(0, 100, "f64", 5)
 
 
+def test_fp64_rate_measurement():
+    # the FP64 roof: a GB300 runs a few hundred G fused multiply-adds per
+    # second (about 2 per clock per SM), far below its FP32 rate
+    r = smat.smat_measure_fp64_rate(5)
+    assert 1e11 < r < 3e12, r
+    with pytest.raises(smat.SmatError):
+        smat.smat_measure_fp64_rate(0)
+
+
 def test_trial_racing_keeps_the_pick_and_saves_time():
     # racing stops timing a candidate after 3 products when it is already
     # 1.3x the best so far; on a power-law matrix, where CSR-scalar and the
