@@ -9,9 +9,22 @@ step is eight products y = A x through each handle's tuned plan.  Tuning
 (feature extraction, selection, conversion) happens once per handle before the
 timed region and is reported as overhead in units of one CSR-scalar product.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 Under torchrun every rank runs its own replica (weak scaling, no collective on
 the data path); rank 0 prints one JSON line.
+
+--workload picks the configuration (default: structures, the suite above):
+  precision  power-law n = 8e6 (Zipf 1.8, cap 1e4) with values stored in FP64,
+             FP32 and BF16 (FP32 accumulation): three products per step
+  batched    the 27-point hierarchy 192^3 .. 12^3 plus 64 mixed matrices
+             (n 1e3 .. 1e6), FP64: one batched launch per step
+  cg         mixed-precision CG on the 3-D 7-point 256^3 Laplacian: FP32 inner
+             products, FP64 residual and update; one step = 500 inner
+             iterations from x = 0
+  selector   the learned selector on held-out matrices of its labelled set
+             (FP64): one product per matrix per step, each through its
+             learned plan, with the regret against an exhaustive timing of
+             the eight classes measured in the same run
 """
 from __future__ import annotations
 
@@ -32,11 +45,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMV GFLOP/s, HBM % of peak: tuned/learned pick vs plain CSR at stated error"
 UNIT = "GFLOP/s"
-WORKLOAD = "structures_suite: stencil3d7 128^3, uniform 1e6 Poisson(16), powerlaw 2e6 Zipf(1.8) cap 1e4, " \
-           "blockdiag 1e6 b=8; FP64 and FP32 storage"
-TOL = {"f64": 1e-12, "f32": 1e-5}
-# every row of these eight products, tuned as here, against the oracle
-PARITY_TEST = "tests/test_gpu_api.py::test_full_size_bench_workload_parity"
+WORKLOADS = {
+    "structures": "structures_suite: stencil3d7 128^3, uniform 1e6 Poisson(16), powerlaw 2e6 Zipf(1.8) cap 1e4, "
+                  "blockdiag 1e6 b=8; FP64 and FP32 storage",
+    "precision": "precision: powerlaw 8e6 Zipf(1.8) cap 1e4, values FP64 / FP32 / BF16 (FP32 accumulate)",
+    "batched": "batched: 27-point stencils 192^3, 96^3, 48^3, 24^3, 12^3 + 64 mixed matrices n 1e3..1e6, FP64, "
+               "one batched launch",
+    "cg": "cg: mixed-precision CG, 3-D 7-point 256^3 (n 16.8e6), FP32 inner / FP64 outer, 500 inner iterations "
+          "per step",
+    "selector": "selector: learned picks on held-out matrices of the labelled set (FP64)",
+}
+WORKLOAD = WORKLOADS["structures"]
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5}
+# every row of these products, tuned as here, against the oracle
+PARITY_TESTS = {
+    "structures": "tests/test_gpu_api.py::test_full_size_bench_workload_parity",
+    "precision": "tests/test_gpu_full_size.py::test_powerlaw_8m_full_size",
+    "batched": "tests/test_gpu_full_size.py::test_batched_hierarchy_full_size",
+    "cg": "tests/test_gpu_full_size.py::test_mixed_cg_256_full_size",
+    "selector": "tests/test_gpu_selection.py",
+}
+PARITY_TEST = PARITY_TESTS["structures"]
 
 
 def parse():
@@ -50,6 +79,9 @@ def parse():
     p.add_argument("--dtypes", default="f64,f32")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--workload", default="structures", choices=sorted(WORKLOADS))
+    p.add_argument("--selector-sample", type=int, default=48,
+                   help="held-out matrices in the selector workload")
     return p.parse_args()
 
 
@@ -69,11 +101,56 @@ def workload(scale):
     return mats, xs
 
 
+def selector_sample(count):
+    """Held-out matrices of the selector's labelled set (the split it was
+    trained with), every k-th of those with at most 6e6 entries."""
+    from paper_1210_2536_gb300 import learn, synth
+    recs = learn.load(os.path.join(ROOT, "paper_1210_2536_gb300", "selector_dataset.jsonl"))
+    _, held = learn.split(recs)
+    held = [r for r in held if r["nnz"] <= 6e6]
+    step = max(1, len(held) // max(1, count))
+    return [synth.dataset_matrix(r["id"]) for r in held[::step][:count]]
+
+
+def product_specs(args):
+    """(matrix, storage type, x in FP64) for every product of a step."""
+    from paper_1210_2536_gb300 import synth
+    if args.workload == "structures":
+        mats, xs = workload(args.scale)
+        return [(A, dt, x) for A, x in zip(mats, xs) for dt in args.dtypes.split(",")]
+    if args.workload == "precision":
+        A = synth.powerlaw(int(round(8_000_000 * args.scale)), 1.8, 10000, 0)
+        x = synth.uniform(0, 1, A.n)
+        return [(A, dt, x) for dt in ("f64", "f32", "bf16")]
+    if args.workload == "selector":
+        return [(A, "f64", synth.uniform(0, 1, A.n)) for A in selector_sample(args.selector_sample)]
+    raise ValueError(args.workload)
+
+
 def stored(A, dtype):
+    """Values as handed to the library (FP64 / FP32 host arrays; BF16 as the
+    FP64 values, which device_values rounds) and their FP64 widening."""
     if dtype == "f64":
         return A.val, A.val
     v = A.val.astype(np.float32)
     return v, v.astype(np.float64)
+
+
+def device_values(A, dtype, dev):
+    """(values on the device as the library stores them, the same values
+    widened to FP64 on the host).  BF16 rounding is the library's own cast."""
+    import torch
+    import paper_1210_2536_gb300 as smat
+    if dtype != "bf16":
+        vals, v64 = stored(A, dtype)
+        return torch.from_numpy(np.ascontiguousarray(vals)).to(dev), v64
+    d64 = torch.from_numpy(A.val).to(dev)
+    out = torch.empty(A.nnz, dtype=torch.int16, device=dev)
+    if smat.smat_cast_f64_to_bf16(d64.data_ptr(), out.data_ptr(), A.nnz, 0) != 0:
+        raise RuntimeError("smat_cast_f64_to_bf16 failed")
+    torch.cuda.synchronize()
+    bits = out.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    return out, bits.view(np.float32).astype(np.float64)
 
 
 class Clocks:
@@ -186,17 +263,14 @@ def cpu_model() -> str:
     return platform.machine()
 
 
-def cpu_baseline(mats, xs, dtypes, seconds):
+def cpu_baseline(specs, seconds):
     """The oracle (threaded, nonzero-balanced rows, FP64 accumulation) timed
-    on this host's cores over passes of the same products."""
+    on this host's cores over passes of the same products; specs are
+    (matrix, stored values widened to FP64, x as the product reads it)."""
     import oracle
     threads = os.cpu_count() or 1
-    prods = []
-    for A, x in zip(mats, xs):
-        for dt in dtypes:
-            _, v64 = stored(A, dt)
-            xx = x if dt == "f64" else x.astype(np.float32).astype(np.float64)
-            prods.append((A, np.ascontiguousarray(v64), np.ascontiguousarray(xx), np.zeros(A.m)))
+    prods = [(A, np.ascontiguousarray(v64), np.ascontiguousarray(np.asarray(x, dtype=np.float64)), np.zeros(A.m))
+             for A, v64, x in specs]
     flops = sum(2.0 * A.nnz for A, _, _, _ in prods)
     t0 = time.perf_counter()
     passes = 0
@@ -221,23 +295,47 @@ def cpu_baseline(mats, xs, dtypes, seconds):
                              "sample": f"one full pass over the {len(prods)} products, 1 thread, {st:.2f} s"}}
 
 
+def batched_mats(scale):
+    from paper_1210_2536_gb300 import synth
+    top = max(12, int(round(192 * scale ** (1.0 / 3.0))) // 16 * 16)
+    return synth.amg_like_hierarchy(top) + synth.mixed_batch(64)
+
+
+def cg_matrix(scale):
+    from paper_1210_2536_gb300 import synth
+    return synth.stencil3d7(max(8, int(round(256 * scale ** (1.0 / 3.0)))))
+
+
+def reference_specs(args):
+    """(matrix, stored values widened to FP64, x) of every product a step of
+    the workload runs, for the oracle arm."""
+    import oracle
+    from paper_1210_2536_gb300 import synth
+    if args.workload == "batched":
+        return [(A, A.val, synth.uniform(0, 1, A.n)) for A in batched_mats(args.scale)]
+    if args.workload == "cg":
+        L = cg_matrix(args.scale)
+        x = synth.uniform(0, 5, L.n)
+        return [(L, L.val, x), (L, L.val.astype(np.float32).astype(np.float64), x.astype(np.float32))]
+    out = []
+    for A, dt, x in product_specs(args):
+        if dt == "bf16":
+            v64 = oracle.bf16_to_double(oracle.round_bf16(A.val))
+        else:
+            v64 = stored(A, dt)[1]
+        out.append((A, v64, x if dt == "f64" else x.astype(np.float32)))
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    dtypes = args.dtypes.split(",")
-    mats, xs = workload(args.scale)
     threads = os.cpu_count() or 1
-    prods = []
-    for A, x in zip(mats, xs):
-        for dt in dtypes:
-            _, v64 = stored(A, dt)
-            xx = x if dt == "f64" else x.astype(np.float32).astype(np.float64)
-            prods.append([A, np.ascontiguousarray(v64), np.ascontiguousarray(xx), np.zeros(A.m), 0])
-    # each step: the same fraction of every product's rows, sized so that the
-    # whole run stays within about two minutes
+    prods = [[A, np.ascontiguousarray(v64), np.ascontiguousarray(np.asarray(x, dtype=np.float64)), np.zeros(A.m), 0]
+             for A, v64, x in reference_specs(args)]
     budget_s = 120.0 / max(1, args.steps + args.warmup)
     t0 = time.perf_counter()
     for A, v, x, y, _ in prods:
@@ -269,7 +367,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(1, args.steps), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "scale": args.scale},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "scale": args.scale},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
                              "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -283,9 +381,6 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1210_2536_gb300 as smat
-    from paper_1210_2536_gb300.roofline import algorithmic_bytes, l2_sectors
-    from paper_1210_2536_gb300.roofline import bound as roof_bound
-    from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -294,8 +389,6 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    dtypes = args.dtypes.split(",")
-    mats, xs = workload(args.scale)
 
     select = args.select
     model_path = os.path.join(ROOT, "paper_1210_2536_gb300", "selector_mlp.bin")
@@ -304,23 +397,82 @@ def run_ours(args):
     if select == "learned":
         if smat.smat_load_model(model_path) != 0:
             raise RuntimeError("selector model did not load")
+    ctx = dict(dev=dev, world=world, rank=rank, select=select)
+    if args.workload == "batched":
+        line = run_batched(args, ctx)
+    elif args.workload == "cg":
+        line = run_cg(args, ctx)
+    else:
+        line = run_products(args, ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def timed_region(K, W, step, world, dev, per_step_events=None):
+    """W untimed steps, then K steps between CUDA events on the current
+    stream, bracketed by a barrier (N > 1) and a device synchronisation,
+    with nvidia-smi clock samples taken meanwhile; returns (max-over-ranks
+    ms, clocks).  step(k) issues step k."""
+    import torch
+    import torch.distributed as dist
+    from paper_1210_2536_gb300.dist import max_over_ranks
+    for k in range(W):
+        step(-1)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = Clocks(vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device()))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    t_start.record()
+    for k in range(K):
+        step(k)
+    t_end.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    return max_over_ranks(t_start.elapsed_time(t_end), dev), ck
+
+
+def fp64_roof(smat):
+    """Measured FP64 roof in TFLOP/s (2 flops per fused multiply-add)."""
+    return 2.0 * smat.smat_measure_fp64_rate(10) / 1e12
+
+
+def run_products(args, ctx):
+    import torch
+    import torch.distributed as dist
+    import paper_1210_2536_gb300 as smat
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes, l2_sectors
+    from paper_1210_2536_gb300.roofline import bound as roof_bound
+    from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
+    dev, world, rank, select = ctx["dev"], ctx["world"], ctx["rank"], ctx["select"]
+    specs = product_specs(args)
+    dtypes = sorted({dt for _, dt, _ in specs}, key=["f64", "f32", "bf16"].index)
 
     prods = []
-    for A, x in zip(mats, xs):
-        for dt in dtypes:
-            vals, v64 = stored(A, dt)
-            tdt = torch.float64 if dt == "f64" else torch.float32
-            t0 = time.perf_counter()
-            M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
-                              torch.from_numpy(np.ascontiguousarray(vals)).to(dev), dt)
-            torch.cuda.synchronize()
-            create_ms = (time.perf_counter() - t0) * 1e3
-            M.tune(select, keep_formats=0)
-            plan = M.plan()
-            xd = torch.from_numpy(x).to(dev).to(tdt)
-            yd = torch.zeros(A.m, dtype=tdt, device=dev)
-            prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
-                              f=M.features(), launches=M.launches()))
+    for A, dt, x in specs:
+        vals, v64 = device_values(A, dt, dev)
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        t0 = time.perf_counter()
+        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                          vals, dt)
+        torch.cuda.synchronize()
+        create_ms = (time.perf_counter() - t0) * 1e3
+        del vals
+        M.tune(select, keep_formats=0)
+        plan = M.plan()
+        xd = torch.from_numpy(x).to(dev).to(tdt)
+        yd = torch.zeros(A.m, dtype=tdt, device=dev)
+        prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
+                          f=M.features(), launches=M.launches()))
 
     # plain CSR-scalar and tuned pick, each timed alone (median of 20)
     def time_variant(p, v, reps=20):
@@ -340,24 +492,15 @@ def run_ours(args):
 
     # ---- timed region: K steps of all products through their plans ----
     K, W = args.steps, args.warmup
-    stride = max(1, K // 200)
+    # per-product events on every other step (at most 200 steps): an event
+    # pair between two kernels costs about 4 us of idle GPU, which the steps
+    # without them do not pay
+    stride = max(2, K // 200)
     sampled = list(range(0, K, stride))
     kev = {i: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in prods] for i in sampled}
-    for _ in range(W):
-        for p in prods:
-            p["M"].spmv(p["x"], p["y"])
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    clocks = Clocks(vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device()))
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
-    t_start.record()
-    for k in range(K):
+
+    def step(k):
         evs = kev.get(k)
         for j, p in enumerate(prods):
             if evs:
@@ -365,18 +508,14 @@ def run_ours(args):
             p["M"].spmv(p["x"], p["y"])
             if evs:
                 evs[j][1].record()
-    t_end.record()
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ck = clocks.stop()
-    ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
+
+    ms, ck = timed_region(K, W, step, world, dev)
     flops_step = sum(2.0 * p["A"].nnz for p in prods)
     value = weak_scaling_throughput(flops_step * K, ms / 1e3, world) / 1e9
     launches_per_step = sum(p["launches"] for p in prods)
 
     peak, peak_kind = measured_peak()
+    fp64_tf = fp64_roof(smat)
     per = []
     for j, p in enumerate(prods):
         d = statistics.mean(kev[i][j][0].elapsed_time(kev[i][j][1]) for i in sampled)
@@ -384,11 +523,12 @@ def run_ours(args):
         csr_bytes = algorithmic_bytes(p["f"], smat.SMAT_V_CSR_SCALAR, p["dt"])
         be = break_even_calls(p["plan"]["tune_ms"], p["csr_ms"], p["pick_ms"])
         per.append({"matrix": p["A"].name, "dtype": p["dt"], "nnz": p["A"].nnz, "variant": p["plan"]["name"],
+                    "kernel": kernel_label(p["M"], p["plan"]["variant"]),
                     "confidence": round(p["plan"]["confidence"], 3), "trialled": p["plan"]["trialled"],
                     "ms_in_step": round(d, 5), "gflops": round(2 * p["A"].nnz / d / 1e6, 2),
                     "hbm_frac": round(byts / (d / 1e3) / 1e9 / peak, 4),
-                    "bound": roof_bound(p["f"], p["plan"]["variant"], p["dt"], d / 1e3, peak)["bound"],
-                    "roof_frac": round(roof_bound(p["f"], p["plan"]["variant"], p["dt"], d / 1e3, peak)["frac"], 4),
+                    "bound": roof_bound(p["f"], p["plan"]["variant"], p["dt"], d / 1e3, peak, fp64_tf)["bound"],
+                    "roof_frac": round(roof_bound(p["f"], p["plan"]["variant"], p["dt"], d / 1e3, peak, fp64_tf)["frac"], 4),
                     "pick_ms_alone": round(p["pick_ms"], 5), "csr_scalar_ms_alone": round(p["csr_ms"], 5),
                     "csr_scalar_gflops": round(2 * p["A"].nnz / p["csr_ms"] / 1e6, 2),
                     "csr_scalar_hbm_frac": round(csr_bytes / (p["csr_ms"] / 1e3) / 1e9 / peak, 4),
@@ -400,7 +540,7 @@ def run_ours(args):
     dom_i = max(range(len(per)), key=lambda j: per[j]["_d"])
     dom, dp = per[dom_i], prods[dom_i]
     dom_key = f"{dom['variant']}:{dom['dtype']}:{dom['matrix']}"
-    rb = roof_bound(dp["f"], dp["plan"]["variant"], dp["dt"], dom["_d"] / 1e3, peak)
+    rb = roof_bound(dp["f"], dp["plan"]["variant"], dp["dt"], dom["_d"] / 1e3, peak, fp64_tf)
     traffic = dram_traffic_record(dom_key)
     # random-column products are bound by x gathers before HBM: the measured
     # gather rate of this GPU over the dominant product's own x and count
@@ -451,22 +591,25 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
 
+    extra = selector_regret(prods, time_variant) if args.workload == "selector" else None
+    line = None
     if rank == 0:
-        cpu = cpu_baseline(mats, xs, dtypes, args.cpu_seconds) if world == 1 else None
+        cpu = cpu_baseline([(p["A"], p["v64"], p["x"].double().cpu().numpy()) for p in prods], args.cpu_seconds) \
+            if world == 1 else None
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "+".join(dtypes), "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scale": args.scale, "selector": select,
+            "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "selector": select,
                        "l2": "inputs larger than L2: the step streams "
                              f"{sum(algorithmic_bytes(p['f'], p['plan']['variant'], p['dt']) for p in prods) / 1e6:.0f}"
                              " MB and each matrix is evicted by the other products between its launches",
                        "parallelism": f"replicas x{world}"},
-            "parity": {"bound": TOL, "checked_by": PARITY_TEST},
+            "parity": {"bound": {dt: TOL[dt] for dt in dtypes}, "checked_by": PARITY_TESTS[args.workload]},
             "roofline": {"bound": rb["bound"], "kernel": dom_key, "achieved": round(rb["achieved"], 3),
                          "peak": round(rb["peak"], 4),
                          "peak_kind": (peak_kind if rb["bound"] == "hbm" else
-                                       "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"),
+                                       "measured: smat_measure_fp64_rate (FP64 fused multiply-adds x 2)"),
                          "unit": rb["unit"], "frac": round(rb["frac"], 4), "traffic": traffic,
                          "alg_bytes_per_launch": rb["alg_bytes"], "hbm_frac": round(rb["hbm_frac"], 4),
                          "fp64_frac": round(rb["fp64_frac"], 4) if "fp64_frac" in rb else None,
@@ -483,11 +626,276 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "per_matrix": per,
         }
-        print(json.dumps(line), flush=True)
+        if extra is not None:
+            line["selector"] = extra
     for p in prods:
         p["M"].close()
+    return line
+
+
+def batch_kind(variant):
+    """Format kind of the batched kernel a member's plan runs through."""
+    return {5: "ell", 6: "dia", 10: "sell"}.get(variant, "csr")
+
+
+def run_batched(args, ctx):
+    """One batched launch (the autotuned plan: persistent kernels per format
+    kind in a CUDA graph, or the members' own launches when faster) over the
+    multigrid-like hierarchy and 64 mixed matrices, FP64."""
+    import torch
+    import torch.distributed as dist
+    import paper_1210_2536_gb300 as smat
+    from paper_1210_2536_gb300 import synth
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
+    from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
+    dev, world, rank, select = ctx["dev"], ctx["world"], ctx["rank"], ctx["select"]
+    mats = batched_mats(args.scale)
+    hs, xs, ys, x64 = [], [], [], []
+    for A in mats:
+        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                          torch.from_numpy(A.val).to(dev), "f64")
+        M.tune(select, keep_formats=0)
+        hs.append(M)
+        x = synth.uniform(0, 1, A.n)
+        x64.append(x)
+        xs.append(torch.from_numpy(x).to(dev))
+        ys.append(torch.zeros(A.m, dtype=torch.float64, device=dev))
+    nnz = sum(A.nnz for A in mats)
+    plans = [M.plan()["variant"] for M in hs]
+    byts = sum(algorithmic_bytes(M.features(), v, "f64") for M, v in zip(hs, plans))
+    t0 = time.perf_counter()
+    B = smat.Batch(hs).tune()
+    tune_s = time.perf_counter() - t0
+    info = B.info()
+
+    def time_it(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    def per_matrix():
+        for M, x, y in zip(hs, xs, ys):
+            M.spmv(x, y)
+
+    t_loop = time_it(per_matrix)
+    K, W = args.steps, args.warmup
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
+    def step(k):
+        if k >= 0:
+            evs[k][0].record()
+        B.spmv(xs, ys)
+        if k >= 0:
+            evs[k][1].record()
+
+    ms, ck = timed_region(K, W, step, world, dev)
+    d = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    value = weak_scaling_throughput(2.0 * nnz * K, ms / 1e3, world) / 1e9
+    peak, peak_kind = measured_peak()
+    if info["per_matrix"]:
+        launches = sum(M.launches() for M in hs)
+    else:
+        launches = len({batch_kind(v) for v in plans})
+
+    # end to end: every member's x from pinned host memory, the batched
+    # product, every y back to pinned host memory, on one stream
+    xh = [x.cpu().pin_memory() for x in xs]
+    yh = [torch.zeros_like(y, device="cpu").pin_memory() for y in ys]
+
+    def e2e_step():
+        for h, x in zip(xh, xs):
+            x.copy_(h, non_blocking=True)
+        B.spmv(xs, ys)
+        for h, y in zip(yh, ys):
+            h.copy_(y, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    E = max(1, min(args.e2e_steps, 50))
     if world > 1:
-        dist.destroy_process_group()
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline([(A, A.val, x) for A, x in zip(mats, x64)], args.cpu_seconds) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batched"], "scale": args.scale, "selector": select,
+                       "matrices": len(mats), "nnz": nnz,
+                       "l2": f"inputs larger than L2: a step streams {byts / 1e6:.0f} MB",
+                       "parallelism": f"replicas x{world}"},
+            "parity": {"bound": {"f64": TOL["f64"]}, "checked_by": PARITY_TESTS["batched"]},
+            "roofline": {"bound": "hbm", "kernel": "batched launch (one persistent kernel per format kind, "
+                                                   "graph-replayed; or the members' own launches)",
+                         "achieved": round(byts / (d / 1e3) / 1e9, 3), "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": round(byts / (d / 1e3) / 1e9 / peak, 4), "traffic": None,
+                         "alg_bytes_per_launch": byts},
+            "gpu_launches": launches * K,
+            "clocks": ck,
+            "e2e": {"value": round(weak_scaling_throughput(2.0 * nnz * E, e2e_s, world) / 1e9, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": sum(h.numel() * 8 for h in xh),
+                    "d2h_bytes_per_step": sum(h.numel() * 8 for h in yh), "steps": E,
+                    "how": "every x copied from pinned host memory, one batched product, every y copied back; "
+                           "one stream, synced per step"},
+            "cpu_baseline": cpu,
+            "batched": {"batched_ms": round(d, 5), "per_matrix_launches_ms": round(t_loop, 5),
+                        "speedup_vs_per_matrix": round(t_loop / d, 3), "batch_info": info,
+                        "batch_tune_s": round(tune_s, 2),
+                        "picks": {smat.VARIANT_NAMES[v]: plans.count(v) for v in sorted(set(plans))}},
+        }
+    B.close()
+    for M in hs:
+        M.close()
+    return line
+
+
+def run_cg(args, ctx):
+    """Mixed-precision CG on the 3-D 7-point Laplacian: each step is a solve
+    from x = 0 capped at 500 inner FP32 iterations; the metric counts the
+    SpMV flops it ran (inner FP32 products plus the FP64 residual products)."""
+    import torch
+    import torch.distributed as dist
+    import paper_1210_2536_gb300 as smat
+    from paper_1210_2536_gb300 import synth
+    from paper_1210_2536_gb300.roofline import algorithmic_bytes
+    from paper_1210_2536_gb300.dist import max_over_ranks, weak_scaling_throughput
+    dev, world, rank, select = ctx["dev"], ctx["world"], ctx["rank"], ctx["select"]
+    L = cg_matrix(args.scale)
+    rp, ci = torch.from_numpy(L.rowptr).to(dev), torch.from_numpy(L.colidx).to(dev)
+    H64 = smat.SpMatrix(L.m, L.n, rp, ci, torch.from_numpy(L.val).to(dev), "f64").tune(select)
+    H32 = smat.SpMatrix(L.m, L.n, rp, ci, torch.from_numpy(L.val.astype(np.float32)).to(dev), "f32").tune(select)
+    xt = synth.uniform(0, 5, L.n)
+    bd = H64.spmv(torch.from_numpy(xt).to(dev))        # b = A x_true on the device
+    xd = torch.zeros(L.n, dtype=torch.float64, device=dev)
+    inner = 500
+    last = {}
+
+    def step(k):
+        xd.zero_()
+        last.update(smat.cg_mixed(H64, H32, bd, xd, max_total_inner=inner, rtol=1e-10, max_inner=inner))
+
+    K, W = args.steps, max(1, args.warmup)
+    ms, ck = timed_region(K, W, step, world, dev)
+    products32 = last["inner_total"]
+    products64 = last["outer"] + 1
+    flops_step = 2.0 * L.nnz * (products32 + products64)
+    value = weak_scaling_throughput(flops_step * K, ms / 1e3, world) / 1e9
+    # the inner FP32 product, timed alone, against its roof
+    x32 = torch.from_numpy(synth.uniform(1, 1, L.n).astype(np.float32)).to(dev)
+    y32 = torch.zeros(L.n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        H32.spmv(x32, y32)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in ev:
+        a.record()
+        H32.spmv(x32, y32)
+        b.record()
+    torch.cuda.synchronize()
+    t32 = statistics.median(a.elapsed_time(b) for a, b in ev)
+    peak, peak_kind = measured_peak()
+    f32 = H32.features()
+    b32 = algorithmic_bytes(f32, H32.plan()["variant"], "f32")
+    # the solve to 1e-10 (5000 inner iterations at most), once, outside the timed region
+    xd.zero_()
+    full = smat.cg_mixed(H64, H32, bd, xd, max_total_inner=5000, rtol=1e-10, max_inner=2000)
+    # end to end: b from pinned host memory, the capped solve, x back to the host
+    bh = bd.cpu().pin_memory()
+    xh = torch.zeros(L.n, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        bd.copy_(bh, non_blocking=True)
+        xd.zero_()
+        smat.cg_mixed(H64, H32, bd, xd, max_total_inner=inner, rtol=1e-10, max_inner=inner)
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    E = max(1, min(args.e2e_steps, 10))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline([(L, L.val, xt), (L, L.val.astype(np.float32).astype(np.float64),
+                                             xt.astype(np.float32).astype(np.float64))], args.cpu_seconds) \
+            if world == 1 else None
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["cg"], "scale": args.scale, "selector": select, "n": L.n,
+                       "nnz": L.nnz, "l2": "inputs larger than L2: each FP32 product streams "
+                                            f"{b32 / 1e6:.0f} MB",
+                       "parallelism": f"replicas x{world}"},
+            "parity": {"bound": {"f64": TOL["f64"], "f32": TOL["f32"], "relres": 1e-10},
+                       "checked_by": PARITY_TESTS["cg"]},
+            "roofline": {"bound": "hbm", "kernel": f"inner FP32 product ({H32.plan()['name']}), timed alone",
+                         "achieved": round(b32 / (t32 / 1e3) / 1e9, 3), "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": round(b32 / (t32 / 1e3) / 1e9 / peak, 4), "traffic": None,
+                         "alg_bytes_per_launch": b32},
+            "gpu_launches": None,
+            "clocks": ck,
+            "e2e": {"value": round(weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": L.n * 8, "d2h_bytes_per_step": L.n * 8, "steps": E,
+                    "how": "b from pinned host memory, the capped solve through smat_cg_mixed, x back to the host"},
+            "cpu_baseline": cpu,
+            "cg": {"inner_per_step": products32, "outer_per_step": last["outer"],
+                   "relres_after_step": last["relres"], "fp32_product_ms": round(t32, 5),
+                   "plans": {"f64": H64.plan()["name"], "f32": H32.plan()["name"]},
+                   "to_1e-10": {"inner_total": full["inner_total"], "outer": full["outer"],
+                                "relres": full["relres"], "seconds": round(full["seconds"], 4),
+                                "converged": full["converged"]}},
+        }
+    H64.close()
+    H32.close()
+    return line
+
+
+def kernel_label(M, variant):
+    """The kernel behind a DIA / ELL plan (measured per handle), else None."""
+    import paper_1210_2536_gb300 as smat
+    names = {smat.SMAT_V_DIA: ("direct", "staged1", "staged2"),
+             smat.SMAT_V_ELL: ("rows", "lanes")}
+    if variant not in names:
+        return None
+    try:
+        return names[variant][M.kernel(variant)]
+    except Exception:
+        return None
+
+
+def selector_regret(prods, time_variant):
+    """Regret of each learned pick against the fastest of the eight classes,
+    every admissible one timed alone here (median of 20): the paper's
+    accuracy and slowdown of the prediction (Sec. 7.3), live on this GPU."""
+    import paper_1210_2536_gb300 as smat
+    rows = []
+    for p in prods:
+        adm = p["f"]["admissible"]
+        t = {v: time_variant(p, v) for v in range(smat.SMAT_NUM_VARIANTS) if (adm >> v) & 1}
+        best_v = min(t, key=t.get)
+        pick_t = p["pick_ms"]
+        rows.append({"matrix": p["A"].name, "pick": p["plan"]["name"], "best": smat.VARIANT_NAMES[best_v],
+                     "regret": round(pick_t / t[best_v] - 1.0, 4), "hit": pick_t <= 1.02 * t[best_v],
+                     "trialled": p["plan"]["trialled"]})
+    reg = sorted(r["regret"] for r in rows)
+    return {"matrices": len(rows), "mean_regret": round(sum(reg) / len(reg), 4),
+            "p90_regret": reg[min(len(reg) - 1, int(0.9 * len(reg)))],
+            "accuracy_within_2pct": round(sum(r["hit"] for r in rows) / len(rows), 4), "rows": rows}
 
 
 def main():

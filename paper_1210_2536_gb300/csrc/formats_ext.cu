@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(256) sell_kernel(const long long *__restrict__
                                                    const V *__restrict__ sval, const typename Compute<V>::T *__restrict__ x,
                                                    Epi<typename Compute<V>::T, MODE> ep,
                                                    typename Compute<V>::T *__restrict__ y, long long ns) {
+  griddep_wait();
   const long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / SELL_C;
   if (sl >= ns) return;
   sell_slice<V, MODE, U>(sptr, width, perm, scol, sval, x, ep, y, sl, threadIdx.x & 31);
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(256) bcsr_kernel(const int32_t *__restrict__ b
                                                    Epi<typename Compute<V>::T, MODE> ep,
                                                    typename Compute<V>::T *__restrict__ y, long long m, long long n,
                                                    long long mb) {
+  griddep_wait();
   typedef typename Compute<V>::T T;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long I0 = gid / BS * R2;
@@ -501,18 +503,18 @@ cudaError_t ext_mode(const smat_s *h, int variant, typename Compute<V>::T alpha,
   if (variant == SMAT_V_SELL) {
     const long long ns = h->sell_ns;
     if (ns == 0) return cudaSuccess;
-    sell_kernel<V, MODE, SELL_U><<<grid_for(ns * SELL_C, 256, INT_MAX), 256, 0, s>>>(
+    (void)launch_pdl(sell_kernel<V, MODE, SELL_U>, dim3(grid_for(ns * SELL_C, 256, INT_MAX)), dim3(256), 0, s,
         h->sell_ptr, h->sell_width, h->sell_perm, h->sell_col, (const V *)h->sell_val, x, ep, y, ns);
     return cudaGetLastError();
   }
   const long long mb = h->bcsr_mb;
   const int g = grid_for((mb + BCSR_R2 - 1) / BCSR_R2 * h->bcsr_b, 256, INT_MAX);
   switch (h->bcsr_b) {
-    case 2: bcsr_kernel<V, 2, BCSR_R2, MODE><<<g, 256, 0, s>>>(h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
+    case 2: (void)launch_pdl(bcsr_kernel<V, 2, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
                                                                  ep, y, h->m, h->n, mb); break;
-    case 4: bcsr_kernel<V, 4, BCSR_R2, MODE><<<g, 256, 0, s>>>(h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
+    case 4: (void)launch_pdl(bcsr_kernel<V, 4, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
                                                                  ep, y, h->m, h->n, mb); break;
-    default: bcsr_kernel<V, 8, BCSR_R2, MODE><<<g, 256, 0, s>>>(h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
+    default: (void)launch_pdl(bcsr_kernel<V, 8, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
                                                                   ep, y, h->m, h->n, mb); break;
   }
   return cudaGetLastError();

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) csr_scalar_kernel(const int32_t *__restri
                                                          const int32_t *__restrict__ col,
                                                          const V *__restrict__ val, const T *__restrict__ x,
                                                          Epi<T, MODE, EXACT> ep, T *__restrict__ y, long long m) {
+  griddep_wait();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
     const int s = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) csr_vector_kernel(const int32_t *__restri
                                                          const int32_t *__restrict__ col,
                                                          const V *__restrict__ val, const T *__restrict__ x,
                                                          Epi<T, MODE> ep, T *__restrict__ y, long long m) {
+  griddep_wait();
   constexpr int RPW = 32 / W;  // rows per warp per step
   const int lane = threadIdx.x & 31, sub = lane % W;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
                                                        Epi<T, MODE> ep, T *__restrict__ y, long long m,
                                                        long long nnz, const int2 *__restrict__ coords,
                                                        int32_t *carry_row, T *carry_val) {
+  griddep_wait();
   constexpr int TILE = NT * IPT;
   __shared__ int32_t s_rowend[TILE + 1];
   __shared__ T s_v[TILE], s_x[TILE];
@@ -467,6 +470,7 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
                                                                 const V *__restrict__ val, const T *__restrict__ x,
                                                                 Epi<T, MODE> ep, T *__restrict__ y, long long nnz,
                                                                 int32_t *carry_row, T *carry_val) {
+  griddep_wait();
   coo_tile<V, T, NT, CH, MODE>(row, col, val, x, ep, y, nnz, carry_row, carry_val, blockIdx.x);
 }
 
@@ -541,6 +545,7 @@ __global__ void __launch_bounds__(COO_NT, SMAT_COO_MINB) split_main_kernel(
     const V *__restrict__ val, T *__restrict__ part, long long nc, const int32_t *__restrict__ srow,
     const int32_t *__restrict__ scol, const V *__restrict__ sval, long long ns, const T *__restrict__ x,
     Epi<T, MODE> ep, T *__restrict__ y, int32_t *carry_row, T *carry_val) {
+  griddep_wait();
   static_assert(COO_NT == 256, "the chunk path assumes 256 threads");
   if ((long long)blockIdx.x < nc)
     split_chunk<V, T>(blockIdx.x, cstart, cend, col, val, x, part);
@@ -577,6 +582,7 @@ __device__ __forceinline__ void carry_fixup(long long c, const int32_t *__restri
 template <typename T, int MODE>
 __global__ void carry_fixup_kernel(const int32_t *__restrict__ carry_row, const T *__restrict__ carry_val,
                                    long long ntiles, Epi<T, MODE> ep, T *__restrict__ y) {
+  griddep_wait();
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ntiles;
        c += (long long)gridDim.x * blockDim.x)
     carry_fixup<T, MODE>(c, carry_row, carry_val, ntiles, ep, y);
@@ -591,6 +597,7 @@ __global__ void split_finish_kernel(const int32_t *__restrict__ lrows, const int
                                     const T *__restrict__ carry_val, long long ntiles,
                                     const int32_t *__restrict__ empty, long long ne, Epi<T, MODE> ep,
                                     T *__restrict__ y) {
+  griddep_wait();
   const long long total = nl + ntiles + ne;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -608,6 +615,7 @@ __global__ void split_finish_kernel(const int32_t *__restrict__ lrows, const int
 template <typename T, int MODE>
 __global__ void scale_rows_kernel(const int32_t *__restrict__ rows, long long count, Epi<T, MODE> ep,
                                   T *__restrict__ y) {
+  griddep_wait();
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < count;
        c += (long long)gridDim.x * blockDim.x) {
     int r = rows[c];
@@ -628,6 +636,7 @@ __global__ void __launch_bounds__(256) ell_kernel(const int32_t *__restrict__ ec
                                                   const typename Compute<V>::T *__restrict__ x,
                                                   Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m) {
+  griddep_wait();
   if (LANE) {  // lane-striped rows (a per-handle measured choice)
     const long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32LL * R);
     if (base < m) ell_lane_group<V, R, MODE, U>(ecol, eval, P, K, x, ep, y, m, base, threadIdx.x & 31);
@@ -651,6 +660,7 @@ __global__ void __launch_bounds__(256) dia_kernel(const int32_t *__restrict__ of
                                                   Epi<typename Compute<V>::T, MODE> ep,
                                                   typename Compute<V>::T *__restrict__ y, long long m,
                                                   long long n) {
+  griddep_wait();
   extern __shared__ int32_t s_off[];
   for (int t = threadIdx.x; t < nd; t += blockDim.x) s_off[t] = off[t];
   __syncthreads();
@@ -678,10 +688,10 @@ cudaError_t launch_coo(const Scratch &sc, const int32_t *row, const int32_t *col
   const long long tiles = (nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
   int32_t *crow = (int32_t *)sc.carry;
   T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
-  coo_kernel<V, T, COO_NT, COO_CH, MODE><<<(unsigned)tiles, COO_NT, 0, s>>>(row, col, val, x, ep, y, nnz, crow, cval);
+  (void)launch_pdl(coo_kernel<V, T, COO_NT, COO_CH, MODE>, dim3((unsigned)tiles), dim3(COO_NT), 0, s, row, col, val, x, ep, y, nnz, crow, cval);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (tiles > 1) carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
+  if (tiles > 1) (void)launch_pdl(carry_fixup_kernel<T, MODE>, dim3(grid_for(tiles, 256, 152 * 8)), dim3(256), 0, s, crow, cval, tiles, ep, y);
   return cudaGetLastError();
 }
 
@@ -700,9 +710,9 @@ void launch_ell_u(const smat_s *h, const EllPart &e, bool lane, const typename C
   const long long m = h->m;
   const int g = grid_for((m + R - 1) / R, 256, 1 << 30);
   if (lane)
-    ell_kernel<V, R, MODE, U, true><<<g, 256, 0, s>>>(e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
+    (void)launch_pdl(ell_kernel<V, R, MODE, U, true>, dim3(g), dim3(256), 0, s, e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
   else
-    ell_kernel<V, R, MODE, U, false><<<g, 256, 0, s>>>(e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
+    (void)launch_pdl(ell_kernel<V, R, MODE, U, false>, dim3(g), dim3(256), 0, s, e.col, (const V *)e.val, h->P, e.K, x, ep, y, m);
 }
 
 template <typename V, int MODE, int U>
@@ -710,7 +720,7 @@ void launch_dia_u(const smat_s *h, const typename Compute<V>::T *x, const Epi<ty
                   typename Compute<V>::T *y, cudaStream_t s) {
   constexpr int R = 16 / (int)sizeof(V);
   const long long m = h->m;
-  dia_kernel<V, R, MODE, U><<<grid_for((m + R - 1) / R, 256, 1 << 30), 256, (size_t)h->dia_nd * 4, s>>>(
+  (void)launch_pdl(dia_kernel<V, R, MODE, U>, dim3(grid_for((m + R - 1) / R, 256, 1 << 30)), dim3(256), (size_t)h->dia_nd * 4, s,
       h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, x, ep, y, m, h->n);
 }
 
@@ -753,32 +763,32 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
   const long long m = h->m;
   switch (variant) {
     case SMAT_V_CSR_SCALAR:
-      csr_scalar_kernel<V, T, false, MODE><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x,
+      (void)launch_pdl(csr_scalar_kernel<V, T, false, MODE>, dim3(grid_for(m, 256, 1 << 20)), dim3(256), 0, s, h->rowptr, h->colidx, val, x,
                                                                                      Epi<T, MODE, false>{alpha, beta}, y, m);
       break;
     case SMAT_V_CSR_SCALAR_EXACT:
-      csr_scalar_kernel<V, T, true, MODE><<<grid_for(m, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x,
+      (void)launch_pdl(csr_scalar_kernel<V, T, true, MODE>, dim3(grid_for(m, 256, 1 << 20)), dim3(256), 0, s, h->rowptr, h->colidx, val, x,
                                                                                     Epi<T, MODE, true>{alpha, beta}, y, m);
       break;
     case SMAT_V_CSR_VEC4:
-      csr_vector_kernel<V, T, 4, MODE><<<grid_for(m * 4, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
+      (void)launch_pdl(csr_vector_kernel<V, T, 4, MODE>, dim3(grid_for(m * 4, 256, 1 << 20)), dim3(256), 0, s, h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_VEC8:
-      csr_vector_kernel<V, T, 8, MODE><<<grid_for(m * 8, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
+      (void)launch_pdl(csr_vector_kernel<V, T, 8, MODE>, dim3(grid_for(m * 8, 256, 1 << 20)), dim3(256), 0, s, h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_VEC32:
-      csr_vector_kernel<V, T, 32, MODE><<<grid_for(m * 32, 256, 1 << 20), 256, 0, s>>>(h->rowptr, h->colidx, val, x, ep, y, m);
+      (void)launch_pdl(csr_vector_kernel<V, T, 32, MODE>, dim3(grid_for(m * 32, 256, 1 << 20)), dim3(256), 0, s, h->rowptr, h->colidx, val, x, ep, y, m);
       break;
     case SMAT_V_CSR_MERGE: {
       long long tiles = (m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
       int32_t *crow = (int32_t *)sc.carry;
       T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
-      csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE><<<(unsigned)tiles, MERGE_NT, 0, s>>>(
+      (void)launch_pdl(csr_merge_kernel<V, T, MERGE_NT, MERGE_IPT, MODE>, dim3((unsigned)tiles), dim3(MERGE_NT), 0, s,
           h->rowptr, h->colidx, val, x, ep, y, m, h->nnz, (const int2 *)h->merge_coords, crow, cval);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       if (tiles > 1)
-        carry_fixup_kernel<T, MODE><<<grid_for(tiles, 256, 152 * 8), 256, 0, s>>>(crow, cval, tiles, ep, y);
+        (void)launch_pdl(carry_fixup_kernel<T, MODE>, dim3(grid_for(tiles, 256, 152 * 8)), dim3(256), 0, s, crow, cval, tiles, ep, y);
     } break;
     case SMAT_V_ELL:
       launch_ell_dia<V, MODE, false>(h, x, ep, y, s, u_req, lane_req);
@@ -790,7 +800,7 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
       break;
     case SMAT_V_COO: {
       if (h->coo_nempty > 0) {
-        scale_rows_kernel<T, MODE><<<grid_for(h->coo_nempty, 256, 152 * 8), 256, 0, s>>>(h->coo_empty, h->coo_nempty,
+        (void)launch_pdl(scale_rows_kernel<T, MODE>, dim3(grid_for(h->coo_nempty, 256, 152 * 8)), dim3(256), 0, s, h->coo_empty, h->coo_nempty,
                                                                                           ep, y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -818,7 +828,7 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
       int32_t *crow = (int32_t *)sc.carry;
       T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
       if (nc + tiles > 0) {
-        split_main_kernel<V, T, MODE><<<(unsigned)(nc + tiles), COO_NT, 0, s>>>(
+        (void)launch_pdl(split_main_kernel<V, T, MODE>, dim3((unsigned)(nc + tiles)), dim3(COO_NT), 0, s,
             h->split_cstart, h->split_cend, h->colidx, val, (T *)sc.part, nc, h->split_srow, h->split_scol,
             (const V *)h->split_sval, ns, x, ep, y, crow, cval);
         cudaError_t e = cudaGetLastError();
@@ -826,7 +836,7 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
       }
       const long long nl = nc > 0 ? h->split_nl : 0, nt = tiles > 1 ? tiles : 0;
       if (nl + nt + h->split_ne > 0)
-        split_finish_kernel<T, MODE><<<grid_for(nl + nt + h->split_ne, 256, 152 * 8), 256, 0, s>>>(
+        (void)launch_pdl(split_finish_kernel<T, MODE>, dim3(grid_for(nl + nt + h->split_ne, 256, 152 * 8)), dim3(256), 0, s,
             h->split_lrows, h->split_lchunk, (const T *)sc.part, nl, crow, cval, nt, h->split_empty, h->split_ne, ep,
             y);
     } break;
@@ -899,6 +909,7 @@ int spmv_launch_count(const smat_s *h, int variant) {
 // non-finite values in x cannot reach y (the BLAS convention).
 template <typename T>
 __global__ void beta_only_kernel(T *__restrict__ y, long long m, T beta) {
+  griddep_wait();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
     y[i] = mul_rn(beta, y[i]);
 }
@@ -908,7 +919,7 @@ cudaError_t beta_only(const smat_s *h, const void *beta_p, void *y, cudaStream_t
   const T beta = *(const T *)beta_p;
   if (h->m == 0) return cudaSuccess;
   if (beta == (T)0) return cudaMemsetAsync(y, 0, (size_t)h->m * sizeof(T), s);
-  beta_only_kernel<T><<<grid_for(h->m, 256, 152 * 8), 256, 0, s>>>((T *)y, h->m, beta);
+  (void)launch_pdl(beta_only_kernel<T>, dim3(grid_for(h->m, 256, 152 * 8)), dim3(256), 0, s, (T *)y, h->m, beta);
   return cudaGetLastError();
 }
 

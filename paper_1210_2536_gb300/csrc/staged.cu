@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
                       int S, long long ntiles, const typename Compute<V>::T *__restrict__ x,
                       Epi<typename Compute<V>::T, MODE> ep, typename Compute<V>::T *__restrict__ y, long long m,
                       long long n, long long wait_limit) {
+  griddep_wait();
   typedef typename Compute<V>::T T;
   constexpr int U = 8;  // diagonals whose loads are issued together
   extern __shared__ __align__(128) unsigned char smem[];
@@ -201,7 +202,7 @@ cudaError_t dia_staged_cfg(const smat_s *h, const StagedGeom &g, typename Comput
     dyn_max = lim;
   }
   if (g.smem > dyn_max) return cudaErrorNotSupported;
-  dia_staged_kernel<V, MODE, CFG><<<g.grid, 32 * (ST_CFG[CFG].warps + 1), g.smem, s>>>(
+  (void)launch_pdl(dia_staged_kernel<V, MODE, CFG>, dim3(g.grid), dim3(32 * (ST_CFG[CFG].warps + 1)), g.smem, s,
       h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, g.T, g.S, g.ntiles, (const T *)x,
       Epi<T, MODE>{alpha, beta}, (T *)y, h->m, h->n, wait_limit);
   return cudaGetLastError();

@@ -38,10 +38,21 @@ def test_package_never_imports_or_links_the_oracle():
                 assert "liboracle" not in src and "oracle.h" not in src and "oracle_" not in src, path
 
 
+def _callers(path, name):
+    """Top-level functions whose bodies call `name`."""
+    tree = ast.parse(open(path).read())
+    return {node.name for node in tree.body if isinstance(node, ast.FunctionDef)
+            and any(isinstance(n, ast.Call) and isinstance(n.func, ast.Name) and n.func.id == name
+                    for n in ast.walk(node))}
+
+
 def test_bench_runs_the_oracle_only_in_its_baseline_and_reference_arms():
-    users, top = _functions_using_oracle(os.path.join(ROOT, "bench.py"))
+    path = os.path.join(ROOT, "bench.py")
+    users, top = _functions_using_oracle(path)
     assert not top
-    assert users <= {"cpu_baseline", "run_reference"}, users
+    assert users <= {"cpu_baseline", "run_reference", "reference_specs"}, users
+    # the reference arm's input builder serves the reference arm alone
+    assert _callers(path, "reference_specs") <= {"run_reference"}
 
 
 def test_graft_entry_uses_the_oracle_only_to_build_it_and_in_smoke():
