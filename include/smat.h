@@ -174,6 +174,13 @@ typedef struct {
                               so far is not timed further (its timing is that
                               median); 0 times every candidate fully;
                               default 1.3                                     */
+  float trial_tie;         /* trials: candidates whose median is within this
+                              fraction of the fastest count as equally fast
+                              (Sec. 7.3 counts near-equal performance as a
+                              hit) and the lowest variant id among them is the
+                              pick, so that plans of matrices whose variants
+                              all run alike are reproducible; 0 keeps the
+                              strict fastest; default 0.02                    */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */

@@ -59,7 +59,8 @@ class smat_tune_opts_t(ctypes.Structure):
                 ("fill_ratio_max", ctypes.c_int32), ("bytes_cap", ctypes.c_double), ("trial_reps", ctypes.c_int32),
                 ("trial_warmup", ctypes.c_int32), ("trial_budget_ms", ctypes.c_double),
                 ("allowed", ctypes.c_uint32), ("keep_formats", ctypes.c_int32), ("sell_sigma", ctypes.c_int32),
-                ("trial_extended", ctypes.c_int32), ("plan_cache", ctypes.c_int32), ("trial_race", ctypes.c_float)]
+                ("trial_extended", ctypes.c_int32), ("plan_cache", ctypes.c_int32), ("trial_race", ctypes.c_float),
+                ("trial_tie", ctypes.c_float)]
 
 
 class smat_cg_opts_t(ctypes.Structure):

@@ -830,6 +830,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
   const double t_start = now_ms();
   float best_ms = 1e30f;
   *best = -1;
+  std::vector<std::pair<int, float>> timed_here;
   for (int v : cands) {
     if (*best >= 0 && now_ms() - t_start > o.trial_budget_ms) break;
     smat_status_t ps = prepare_variant(h, v, s);
@@ -869,6 +870,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
       med = ms[(size_t)done / 2];
     }
     h->timings[v] = med;
+    timed_here.emplace_back(v, med);
     if (med < best_ms) {
       best_ms = med;
       *best = v;
@@ -879,7 +881,27 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
         if (fmt != variant_format(*best)) free_format(h, fmt);
     }
   }
-  if (*best < 0) *best = SMAT_V_CSR_SCALAR;
+  if (*best < 0) {
+    *best = SMAT_V_CSR_SCALAR;
+    return SMAT_OK;
+  }
+  // near-ties: the lowest variant id within trial_tie of the fastest
+  if (o.trial_tie > 0.0f) {
+    const float lim = best_ms * (1.0f + o.trial_tie);
+    int pick = *best;
+    for (const auto &t : timed_here)
+      if (t.second <= lim && t.first < pick) pick = t.first;
+    if (pick != *best) {
+      const int fastest = *best;
+      smat_status_t ps = variant_ready(h, pick) ? SMAT_OK : prepare_variant(h, pick, s);
+      if (ps == SMAT_OK && variant_ready(h, pick)) {
+        *best = pick;
+        if (!o.keep_formats && variant_format(fastest) != variant_format(pick)) free_format(h, variant_format(fastest));
+      } else if (ps != SMAT_ERR_UNSUPPORTED && ps != SMAT_ERR_ALLOC) {
+        return ps;
+      }
+    }
+  }
   return SMAT_OK;
 }
 
@@ -958,6 +980,7 @@ void smat_tune_opts_default(smat_tune_opts_t *o) {
   o->trial_extended = 1;
   o->plan_cache = 0;
   o->trial_race = 1.3f;
+  o->trial_tie = 0.02f;
 }
 
 const char *smat_status_string(smat_status_t s) {

@@ -89,7 +89,8 @@ def test_tuning_modes():
     t = M.timings()
     tried = [v for v in range(8) if t[v] > 0]
     assert set(tried) == {0, 5, 6, 7}
-    assert t[M.plan()["variant"]] == min(t[v] for v in tried)   # the fastest (ties: any of them)
+    # the fastest, or a lower variant id within the 2 % near-tie tolerance
+    assert t[M.plan()["variant"]] <= 1.02 * min(t[v] for v in tried)
     smat.smat_set_model(None, None, None)
     with pytest.raises(smat.SmatError):
         M.tune("learned")                             # no model installed
@@ -122,6 +123,39 @@ def test_full_size_bench_workload_parity(dtype):
     smat.smat_set_model(None, None, None)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_every_variant_parity(dtype):
+    # every variant the tuner can pick for the bench's matrices, at full size
+    # (the pick itself depends on timings), and every kernel behind DIA and
+    # ELL, all rows against the oracle
+    for A in synth.structures_suite(1.0):
+        vals, v64 = stored_values(A, dtype)
+        M = smat.SpMatrix(A.m, A.n, torch.from_numpy(A.rowptr).to(DEV), torch.from_numpy(A.colidx).to(DEV),
+                          torch.from_numpy(np.ascontiguousarray(vals)).to(DEV), dtype)
+        x = synth.uniform(0, 1, A.n).astype(np.float64 if dtype == "f64" else np.float32)
+        xd = torch.from_numpy(x).to(DEV)
+        ref, scale = reference(A, v64, x, 1.0, 0.0, None)
+        ran = []
+        for v in range(smat.SMAT_NUM_ALL_VARIANTS):
+            try:
+                M.spmv(xd, variant=v)                 # builds the format when admissible
+            except smat.SmatError:
+                continue
+            kernels = {smat.SMAT_V_DIA: (0, 1, 2), smat.SMAT_V_ELL: (0, 1)}.get(v, (None,))
+            for k in kernels:
+                if k is not None:
+                    try:
+                        M.set_kernel(v, k)
+                    except smat.SmatError:            # a staged shape this matrix does not fit
+                        continue
+                y = M.spmv(xd, variant=v).cpu().numpy().astype(np.float64)
+                assert_close_rows(y, ref, scale, TOL[dtype], f"{A.name} {dtype} {smat.VARIANT_NAMES[v]} kernel {k}")
+                ran.append((v, k))
+        assert len({v for v, _ in ran}) >= 6, (A.name, ran)
+        M.close()
+    assert smat.smat_get_wait_timeouts() == 0
+
+
 def test_concurrent_products_on_one_handle():
     # products on one handle from two streams at once: the plans that carry
     # partial sums between CTAs (merge-path, COO, HYB, SPLIT) give each stream
@@ -145,6 +179,28 @@ def test_concurrent_products_on_one_handle():
             ref, scale = refs[k]
             for r in range(6):
                 assert_close_rows(ys[k][r].cpu().numpy(), ref, scale, TOL["f64"], f"{smat.VARIANT_NAMES[v]} s{k} r{r}")
+    M.close()
+
+
+def test_exhaustive_near_ties_take_the_lowest_variant_id():
+    # trial_tie: medians within that fraction of the fastest count as equal
+    # and the lowest variant id among them is the pick
+    A = synth.stencil2d5(64)    # every variant within a few us of the others
+    M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
+    M.tune("exhaustive", trial_reps=5, trial_race=0.0, trial_tie=100.0)
+    t = M.timings()
+    tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
+    assert M.plan()["variant"] == min(tried)
+    for tie in (0.0, 0.02, 0.25):
+        M.tune("exhaustive", trial_reps=5, trial_race=0.0, trial_tie=tie)
+        t = M.timings()
+        tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
+        best = min(t[v] for v in tried)
+        pick = M.plan()["variant"]
+        assert t[pick] <= (1.0 + tie) * best
+        assert pick == min(v for v in tried if t[v] <= (1.0 + tie) * best), (tie, pick, t)
+        y = M.spmv(torch.from_numpy(synth.uniform(0, 1, A.n)).to(DEV))   # the pick's format is in place
+        assert y.shape[0] == A.m
     M.close()
 
 
@@ -203,5 +259,5 @@ def test_trial_racing_keeps_the_pick_and_saves_time():
     # every candidate still has a timing, and the stopped ones are the slow ones
     ran = full > 0
     assert np.array_equal(raced > 0, ran)
-    assert raced[ran].min() == raced[pick_raced]
+    assert raced[pick_raced] <= 1.02 * raced[ran].min()
     M.close()

@@ -179,7 +179,7 @@ def test_ext_formats_in_the_search():
         if v != smat.SMAT_V_CSR_SCALAR_EXACT and (adm >> v) & 1:
             assert t[v] > 0, smat.VARIANT_NAMES[v]
     tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
-    assert t[M.plan()["variant"]] == min(t[v] for v in tried)
+    assert t[M.plan()["variant"]] <= 1.02 * min(t[v] for v in tried)   # within the near-tie tolerance
     # without them in `allowed`, none is timed
     M.tune("exhaustive", trial_reps=3, allowed=0xFF)
     assert np.all(M.timings()[8:] < 0)
@@ -206,7 +206,7 @@ def test_learned_mode_times_cheaper_further_formats():
         ext = (smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR)
         assert t[smat.SMAT_V_ELL] > 0 and all(t[v] > 0 for v in ext) and M.plan()["trialled"] == 1
         assert M.plan()["variant"] in (smat.SMAT_V_ELL,) + ext
-        assert t[M.plan()["variant"]] == min(t[v] for v in (smat.SMAT_V_ELL,) + ext)
+        assert t[M.plan()["variant"]] <= 1.02 * min(t[v] for v in (smat.SMAT_V_ELL,) + ext)
         M.tune("learned", conf_threshold=0.5, trial_extended=0)
         assert M.plan()["variant"] == smat.SMAT_V_ELL and M.plan()["trialled"] == 0
         M.close()
