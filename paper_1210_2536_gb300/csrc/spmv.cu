@@ -321,11 +321,35 @@ __global__ void __launch_bounds__(NT) csr_merge_kernel(const int32_t *__restrict
   }
 }
 
-// IPT consecutive int32 from p (16-byte aligned when `full`).
+// 32-byte streaming loads (sm_100 and later): one L1 request per 32-byte
+// sector.  Two 16-byte loads of one sector by the same thread are two
+// requests, and on a kernel bound by the rate of sector requests the second
+// one costs as much as the first (and comes back from L2 when the streamed
+// line was evicted in between).  p must be 32-byte aligned.
+__device__ __forceinline__ void ld32_i32(const int32_t *p, int *o) {
+  asm("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld32_f32(const float *p, float *o) {
+  asm("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld32_f64(const double *p, double *o) {
+  asm("ld.global.cs.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(o[0]), "=d"(o[1]), "=d"(o[2]), "=d"(o[3]) : "l"(p));
+}
+__device__ __forceinline__ bool aligned32(const void *p) { return ((uintptr_t)p & 31u) == 0; }
+
+// IPT consecutive int32 from p (16-byte aligned when `full`; 32-byte loads
+// when 32-byte aligned, uniform over a tile since runs start at multiples of 8).
 template <int IPT>
 __device__ __forceinline__ void load_i32_run(const int32_t *__restrict__ p, bool full, int valid, int (&o)[IPT],
                                              int fill) {
-  if (full) {
+  if (full && IPT % 8 == 0 && aligned32(p)) {
+#pragma unroll
+    for (int q = 0; q < IPT / 8; ++q) ld32_i32(p + 8 * q, o + 8 * q);
+  } else if (full) {
 #pragma unroll
     for (int q = 0; q < IPT / 4; ++q) {
       int4 v = __ldcs(reinterpret_cast<const int4 *>(p) + q);
@@ -341,6 +365,19 @@ template <typename V, int IPT>
 __device__ __forceinline__ void load_val_run(const V *__restrict__ p, bool full, int valid,
                                              typename Compute<V>::T (&o)[IPT]) {
   constexpr int R = 16 / (int)sizeof(V);
+  if constexpr (sizeof(V) == 8 && IPT % 4 == 0) {
+    if (full && aligned32(p)) {
+#pragma unroll
+      for (int q = 0; q < IPT / 4; ++q) ld32_f64(reinterpret_cast<const double *>(p) + 4 * q, o + 4 * q);
+      return;
+    }
+  } else if constexpr (sizeof(V) == 4 && IPT % 8 == 0) {
+    if (full && aligned32(p)) {
+#pragma unroll
+      for (int q = 0; q < IPT / 8; ++q) ld32_f32(reinterpret_cast<const float *>(p) + 8 * q, o + 8 * q);
+      return;
+    }
+  }
   if (full) {
 #pragma unroll
     for (int q = 0; q < IPT / R; ++q) {
