@@ -179,8 +179,8 @@ typedef struct {
                               (Sec. 7.3 counts near-equal performance as a
                               hit) and the lowest variant id among them is the
                               pick, so that plans of matrices whose variants
-                              all run alike are reproducible; 0 keeps the
-                              strict fastest; default 0.02                    */
+                              all run alike are reproducible; 0 breaks only
+                              exact ties that way; default 0.02               */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */
@@ -610,6 +610,15 @@ smat_status_t smat_spmv_csr_merge_noalloc(int64_t m, int64_t n, int64_t nnz, con
  * were out of memory; k = 0 disables.  Host-side only: lets tests check that
  * every entry point returns SMAT_ERR_ALLOC and frees what it had allocated. */
 void smat_test_fail_alloc_after(int32_t k);
+
+/* Make the pipelined kernels' bounded waits run out (on != 0), as if a copy
+ * never landed: their consumer warps wait on a barrier that nothing arrives
+ * on, for wait_cycles SM cycles (0 keeps the default of about one second),
+ * then give up; the kernel still waits for its own copies before it leaves,
+ * counts the timeout (smat_get_wait_timeouts) and returns, leaving the
+ * context usable.  The products run meanwhile are invalid.  on = 0 restores
+ * normal operation.  For tests of the failure path. */
+void smat_test_stall_pipelines(int32_t on, int64_t wait_cycles);
 
 /* ------------------------------------------------------------------------ */
 /* Device memory                                                             */

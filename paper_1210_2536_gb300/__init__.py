@@ -90,6 +90,7 @@ _SIGS = {
     "smat_tune_opts_default": (None, [ctypes.POINTER(smat_tune_opts_t)]),
     "smat_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "smat_test_fail_alloc_after": (None, [_I32]),
+    "smat_test_stall_pipelines": (None, [_I32, _I64]),
     "smat_release_cached_memory": (ctypes.c_int, []),
     "smat_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I64, _I64, _I64, _VP, _VP, _VP, ctypes.c_int]),
     "smat_destroy": (ctypes.c_int, [_VP]),

@@ -885,8 +885,9 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     *best = SMAT_V_CSR_SCALAR;
     return SMAT_OK;
   }
-  // near-ties: the lowest variant id within trial_tie of the fastest
-  if (o.trial_tie > 0.0f) {
+  // near-ties: the lowest variant id within trial_tie of the fastest (0:
+  // among exactly equal medians)
+  if (o.trial_tie >= 0.0f) {
     const float lim = best_ms * (1.0f + o.trial_tie);
     int pick = *best;
     for (const auto &t : timed_here)

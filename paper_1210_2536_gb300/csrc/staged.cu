@@ -12,6 +12,8 @@
 // through L1/L2, and write y once.  Tiles are dealt round-robin to the CTAs,
 // and the tile height is chosen so that every CTA gets the same number of
 // tiles within one.
+#include <atomic>
+
 #include "pipe.cuh"
 #include "smat_internal.h"
 #include "spmv_device.cuh"
@@ -36,12 +38,18 @@ constexpr long long ST_WAIT_CYCLES = 2000000000LL;
 // invalid).  Read by smat_get_wait_timeouts.
 __device__ unsigned long long g_wait_timeouts;
 
+// Test hook (smat_test_stall_pipelines): consumers wait on a barrier that
+// nothing arrives on, for `cycles`, so that the timeout path runs.
+std::atomic<int> g_stall_on{0};
+std::atomic<long long> g_stall_cycles{0};
+
 __device__ __forceinline__ double to_compute(double v) { return v; }
 __device__ __forceinline__ float to_compute(float v) { return v; }
 __device__ __forceinline__ float to_compute(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// full[S], empty[S], the test hook's stall barrier, then the offsets.
 __host__ __device__ inline size_t staged_head_bytes(int S, long long nd) {
-  return ((size_t)16 * S + (size_t)4 * nd + 127) / 128 * 128;
+  return ((size_t)16 * S + 8 + (size_t)4 * nd + 127) / 128 * 128;
 }
 
 template <typename V, int MODE, int CFG, int NW = ST_CFG[CFG].warps>
@@ -49,7 +57,7 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
     dia_staged_kernel(const int32_t *__restrict__ off, int nd, const V *__restrict__ dval, long long P, int T_rows,
                       int S, long long ntiles, const typename Compute<V>::T *__restrict__ x,
                       Epi<typename Compute<V>::T, MODE> ep, typename Compute<V>::T *__restrict__ y, long long m,
-                      long long n, long long wait_limit) {
+                      long long n, long long wait_limit, int stall) {
   griddep_wait();
   typedef typename Compute<V>::T T;
   constexpr int U = 8;  // diagonals whose loads are issued together
@@ -58,7 +66,8 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
   __shared__ long long s_issued;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);
   uint64_t *empty = full + S;
-  int32_t *s_off = reinterpret_cast<int32_t *>(empty + S);
+  uint64_t *stall_bar = empty + S;  // never arrived on: the test hook's wait
+  int32_t *s_off = reinterpret_cast<int32_t *>(stall_bar + 1);
   V *stages = reinterpret_cast<V *>(smem + staged_head_bytes(S, nd));
   const size_t stage_elems = (size_t)nd * T_rows;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,6 +77,7 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NW);
     }
+    mbar_init(stall_bar, 1);
     mbar_fence_init();
     s_err = 0;
     s_issued = 0;
@@ -98,7 +108,8 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
     long long j = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
       const int s = (int)(j % S);
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((j / S) & 1), wait_limit))) {
+      uint64_t *bar = stall ? stall_bar : &full[s];
+      if (!__all_sync(0xffffffffu, mbar_wait(bar, stall ? 0u : (unsigned)((j / S) & 1), wait_limit))) {
         if (lane == 0) s_err = 1;
         break;
       }
@@ -128,14 +139,15 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
     }
   }
   __syncthreads();
-  // No copy may still be landing when the CTA exits: wait (bounded) for the
+  // No copy may still be landing when the CTA exits: wait (bounded, with
+  // the full budget even when the test hook shortened the others) for the
   // last phase armed on every stage.  After a normal run all of them have
   // completed already.
   if (threadIdx.x == 0) {
     const long long J = s_issued;
     for (int s = 0; s < S && s < J; ++s) {
       const long long jl = s + (J - 1 - s) / S * S;
-      if (!mbar_wait(&full[s], (unsigned)((jl / S) & 1), wait_limit)) s_err = 1;
+      if (!mbar_wait(&full[s], (unsigned)((jl / S) & 1), ST_WAIT_CYCLES)) s_err = 1;
     }
     if (s_err) atomicAdd(&g_wait_timeouts, 1ull);
   }
@@ -204,7 +216,7 @@ cudaError_t dia_staged_cfg(const smat_s *h, const StagedGeom &g, typename Comput
   if (g.smem > dyn_max) return cudaErrorNotSupported;
   (void)launch_pdl(dia_staged_kernel<V, MODE, CFG>, dim3(g.grid), dim3(32 * (ST_CFG[CFG].warps + 1)), g.smem, s,
       h->dia_off, (int)h->dia_nd, (const V *)h->dia_val, h->P, g.T, g.S, g.ntiles, (const T *)x,
-      Epi<T, MODE>{alpha, beta}, (T *)y, h->m, h->n, wait_limit);
+      Epi<T, MODE>{alpha, beta}, (T *)y, h->m, h->n, wait_limit, g_stall_on.load() ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -243,6 +255,7 @@ cudaError_t launch_dia_staged(const smat_s *h, int kernel, const void *alpha, co
   const int cfg = kernel - 1;
   if (!h->dia_val || !staged_geom(cfg, h->m, h->dia_nd, h->esz, &g)) return cudaErrorNotSupported;
   if (wait_limit <= 0) wait_limit = ST_WAIT_CYCLES;
+  if (g_stall_on.load() && g_stall_cycles.load() > 0) wait_limit = g_stall_cycles.load();
   switch (h->dtype) {
     case SMAT_F64: return dia_staged_typed<double>(cfg, h, g, alpha, x, beta, y, s, wait_limit);
     case SMAT_F32: return dia_staged_typed<float>(cfg, h, g, alpha, x, beta, y, s, wait_limit);
@@ -255,6 +268,11 @@ cudaError_t wait_timeouts(unsigned long long *out) {
 }
 
 }  // namespace smat
+
+extern "C" void smat_test_stall_pipelines(int32_t on, int64_t wait_cycles) {
+  smat::g_stall_cycles = wait_cycles;
+  smat::g_stall_on = on ? 1 : 0;
+}
 
 extern "C" smat_status_t smat_get_wait_timeouts(uint64_t *count) {
   if (!count) return SMAT_ERR_INVALID_ARG;

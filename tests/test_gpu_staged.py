@@ -78,6 +78,7 @@ def _product(M, A, dtype, x, y0, alpha, beta):
 def test_staged_dia_matches_the_oracle(name):
     make, dtypes = CASES[name]
     A = make()
+    timeouts0 = smat.smat_get_wait_timeouts()
     for dtype in dtypes:
         M, vals64 = _handle(A, dtype)
         assert (M.features()["admissible"] >> smat.SMAT_V_DIA) & 1, (name, dtype)
@@ -98,7 +99,31 @@ def test_staged_dia_matches_the_oracle(name):
             staged = _product(M, A, dtype, x, y0, -0.5, 2.0)
             assert_close_rows(staged, direct, scale_d, 2 * TOL[dtype], f"{name} {dtype} staged {k} vs direct")
         M.close()
-    assert smat.smat_get_wait_timeouts() == 0
+    assert smat.smat_get_wait_timeouts() == timeouts0
+
+
+def test_staged_waits_that_run_out_leave_the_context_usable():
+    # the test hook makes the consumers wait on a barrier nothing arrives on,
+    # for 2e6 cycles (~1 ms): the kernel gives up, waits for its own copies,
+    # counts the timeout and returns; the next products are correct
+    A = synth.stencil3d7(64)
+    M, vals64 = _handle(A, "f32")
+    x = synth.uniform(9, 1, A.n).astype(np.float32)
+    y0 = np.zeros(A.m, np.float32)
+    _product(M, A, "f32", x, y0, 1.0, 0.0)
+    for k in STAGED_SHAPES:
+        M.set_kernel(smat.SMAT_V_DIA, k)
+        before = smat.smat_get_wait_timeouts()
+        smat.lib().smat_test_stall_pipelines(1, 2_000_000)
+        try:
+            _product(M, A, "f32", x, y0, 1.0, 0.0)
+        finally:
+            smat.lib().smat_test_stall_pipelines(0, 0)
+        assert smat.smat_get_wait_timeouts() > before, k
+        got = _product(M, A, "f32", x, y0, 1.0, 0.0)
+        ref, scale = reference(A, vals64, x, 1.0, 0.0, None)
+        assert_close_rows(got, ref, scale, TOL["f32"], f"staged {k} after a run-out wait")
+    M.close()
 
 
 def test_staged_dia_is_deterministic():
