@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--dtypes", default="f64,f32")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--concurrent", type=int, default=1,
+                   help="1: steps without per-product events run the products on a stream each")
     p.add_argument("--workload", default="structures", choices=sorted(WORKLOADS))
     p.add_argument("--selector-sample", type=int, default=48,
                    help="held-out matrices in the selector workload")
@@ -495,22 +497,42 @@ def run_products(args, ctx):
     # ---- timed region: K steps of all products through their plans ----
     K, W = args.steps, args.warmup
     # per-product events on every 4th step (at most 100 steps): an event
-    # pair between two kernels costs about 4 us of idle GPU (the step's eight
-    # products ran in 0.512 ms without them, 0.57 ms with them), which the
+    # between two kernels costs idle GPU time (the step's eight products ran
+    # in 0.512 ms without events, 0.57 ms with a pair around each), which the
     # steps without them do not pay
     stride = max(4, K // 100)
     sampled = list(range(stride // 2, K, stride)) or [0]
-    kev = {i: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in prods] for i in sampled}
+    # one event between consecutive products: product j runs between events
+    # j and j + 1 of its step
+    kev = {i: [torch.cuda.Event(enable_timing=True) for _ in range(len(prods) + 1)] for i in sampled}
+
+    # The products of a step are independent.  Steps that carry per-product
+    # events run them one after another on the current stream (those give
+    # each product's own time); the others, with --concurrent, on a stream
+    # each, forked from and joined back to the current stream, so that
+    # gather-bound and bandwidth-bound products overlap.
+    main = torch.cuda.current_stream()
+    side = [torch.cuda.Stream() for _ in prods] if args.concurrent else None
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in prods]
 
     def step(k):
         evs = kev.get(k)
+        if side is not None and not evs:
+            fork.record(main)
+            for j, p in enumerate(prods):
+                side[j].wait_event(fork)
+                p["M"].spmv(p["x"], p["y"], stream=side[j])
+                joins[j].record(side[j])
+            for e in joins:
+                main.wait_event(e)
+            return
+        if evs:
+            evs[0].record()
         for j, p in enumerate(prods):
-            if evs:
-                evs[j][0].record()
             p["M"].spmv(p["x"], p["y"])
             if evs:
-                evs[j][1].record()
+                evs[j + 1].record()
 
     ms, ck = timed_region(K, W, step, world, dev)
     flops_step = sum(2.0 * p["A"].nnz for p in prods)
@@ -521,7 +543,7 @@ def run_products(args, ctx):
     fp64_tf = fp64_roof(smat)
     per = []
     for j, p in enumerate(prods):
-        d = statistics.mean(kev[i][j][0].elapsed_time(kev[i][j][1]) for i in sampled)
+        d = statistics.mean(kev[i][j].elapsed_time(kev[i][j + 1]) for i in sampled)
         byts = algorithmic_bytes(p["f"], p["plan"]["variant"], p["dt"])
         csr_bytes = algorithmic_bytes(p["f"], smat.SMAT_V_CSR_SCALAR, p["dt"])
         be = break_even_calls(p["plan"]["tune_ms"], p["csr_ms"], p["pick_ms"])
@@ -604,6 +626,9 @@ def run_products(args, ctx):
             "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "+".join(dtypes), "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "selector": select,
+                       "streams": ("a stream per product on the steps without per-product events (every "
+                                   f"{stride}th step carries them and runs on one stream)")
+                       if args.concurrent else "one stream",
                        "l2": "inputs larger than L2: the step streams "
                              f"{sum(algorithmic_bytes(p['f'], p['plan']['variant'], p['dt']) for p in prods) / 1e6:.0f}"
                              " MB and each matrix is evicted by the other products between its launches",
