@@ -98,6 +98,7 @@ _SIGS = {
     "smat_spmv": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_many": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
     "smat_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _I32]),
     "smat_get_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_spmv_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
@@ -287,6 +288,25 @@ def smat_measure_gather_rate(n: int, nidx: int, dtype: str = "f64", reps: int = 
     r = ctypes.c_double(0.0)
     _check(lib().smat_measure_gather_rate(n, nidx, DTYPES[dtype], reps, ctypes.byref(r)), "smat_measure_gather_rate")
     return float(r.value)
+
+
+def spmv_many(mats, xs, ys, alphas=None, betas=None, stream=None):
+    """Independent products ys[i] = alphas[i]*mats[i]*xs[i] + betas[i]*ys[i],
+    each through its plan, side by side on library streams ordered after and
+    before `stream` (see smat_spmv_many).  Returns ys."""
+    n = len(mats)
+    if n == 0:
+        return ys
+    alphas = [1.0] * n if alphas is None else alphas
+    betas = [0.0] * n if betas is None else betas
+    scal = [M._scalars(a, b) for M, a, b in zip(mats, alphas, betas)]
+    hs = (_VP * n)(*[M.h for M in mats])
+    ap = (_VP * n)(*[ctypes.addressof(a) for a, _ in scal])
+    bp = (_VP * n)(*[ctypes.addressof(b) for _, b in scal])
+    xp = (_VP * n)(*[x.data_ptr() for x in xs])
+    yp = (_VP * n)(*[y.data_ptr() for y in ys])
+    _check(lib().smat_spmv_many(hs, n, ap, xp, bp, yp, _stream_ptr(stream)), "smat_spmv_many")
+    return ys
 
 
 def smat_measure_fp64_rate(reps: int = 10) -> float:

@@ -954,6 +954,38 @@ smat_status_t mlp_probs(const smat_s *h, float probs[SMAT_NUM_VARIANTS], cudaStr
 
 smat_status_t check_handle(const smat_s *h) { return h ? SMAT_OK : SMAT_ERR_INVALID_ARG; }
 
+// Streams on which smat_spmv_many runs independent products side by side,
+// one set per device, created on first use and kept for the process.
+struct ForkPool {
+  static constexpr int N = 16;
+  cudaStream_t s[N] = {};
+  cudaEvent_t join[N] = {};
+  cudaEvent_t fork = nullptr;
+  std::mutex mu;
+};
+
+cudaError_t fork_pool(ForkPool **out) {
+  static ForkPool pools[64];
+  static std::mutex init_mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  ForkPool &p = pools[dev];
+  std::lock_guard<std::mutex> lock(init_mu);
+  if (!p.fork) {
+    for (int k = 0; k < ForkPool::N; ++k) {
+      if (!p.s[k]) e = cudaStreamCreateWithFlags(&p.s[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess && !p.join[k]) e = cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  *out = &p;
+  return cudaSuccess;
+}
+
 }  // namespace
 }  // namespace smat
 
@@ -1242,6 +1274,36 @@ smat_status_t smat_get_kernel(smat_handle_t h, smat_variant_t v, int32_t *kernel
     return SMAT_OK;
   }
   return SMAT_ERR_INVALID_ARG;
+}
+
+smat_status_t smat_spmv_many(const smat_handle_t *hs, int32_t count, const void *const *alphas,
+                             const void *const *xs, const void *const *betas, void *const *ys, void *stream) {
+  if (count < 0 || (count > 0 && (!hs || !alphas || !xs || !betas || !ys))) return SMAT_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < count; ++i) {
+    const smat_s *h = hs[i];
+    TRYS(check_handle(h));
+    if (!alphas[i] || !betas[i] || (h->m > 0 && !ys[i]) || (h->n > 0 && !xs[i])) return SMAT_ERR_INVALID_ARG;
+    if (!variant_ready(h, h->variant)) return SMAT_ERR_UNSUPPORTED;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  if (count == 1) {
+    TRY(launch_spmv(hs[0], hs[0]->variant, alphas[0], xs[0], betas[0], ys[0], user));
+    return SMAT_OK;
+  }
+  if (count == 0) return SMAT_OK;
+  ForkPool *pool = nullptr;
+  TRY(fork_pool(&pool));
+  std::lock_guard<std::mutex> lock(pool->mu);
+  TRY(cudaEventRecord(pool->fork, user));
+  const int used = std::min<int>(count, ForkPool::N);
+  for (int k = 0; k < used; ++k) TRY(cudaStreamWaitEvent(pool->s[k], pool->fork, 0));
+  for (int32_t i = 0; i < count; ++i)
+    TRY(launch_spmv(hs[i], hs[i]->variant, alphas[i], xs[i], betas[i], ys[i], pool->s[i % ForkPool::N]));
+  for (int k = 0; k < used; ++k) {
+    TRY(cudaEventRecord(pool->join[k], pool->s[k]));
+    TRY(cudaStreamWaitEvent(user, pool->join[k], 0));
+  }
+  return SMAT_OK;
 }
 
 smat_status_t smat_spmv(smat_handle_t h, const void *alpha, const void *x, const void *beta, void *y,
