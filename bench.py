@@ -508,24 +508,16 @@ def run_products(args, ctx):
 
     # The products of a step are independent.  Steps that carry per-product
     # events run them one after another on the current stream (those give
-    # each product's own time); the others, with --concurrent, on a stream
-    # each, forked from and joined back to the current stream, so that
+    # each product's own time); the others, with --concurrent, go through
+    # smat_spmv_many, which runs them side by side on the library's streams,
+    # ordered after and before the current stream's work, so that
     # gather-bound and bandwidth-bound products overlap.
-    main = torch.cuda.current_stream()
-    side = [torch.cuda.Stream() for _ in prods] if args.concurrent else None
-    fork = torch.cuda.Event()
-    joins = [torch.cuda.Event() for _ in prods]
+    many = ([p["M"] for p in prods], [p["x"] for p in prods], [p["y"] for p in prods])
 
     def step(k):
         evs = kev.get(k)
-        if side is not None and not evs:
-            fork.record(main)
-            for j, p in enumerate(prods):
-                side[j].wait_event(fork)
-                p["M"].spmv(p["x"], p["y"], stream=side[j])
-                joins[j].record(side[j])
-            for e in joins:
-                main.wait_event(e)
+        if args.concurrent and not evs:
+            smat.spmv_many(*many)
             return
         if evs:
             evs[0].record()
@@ -591,30 +583,39 @@ def run_products(args, ctx):
     d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
     # each product's copy in, kernel and copy out go to a stream of its own, so
     # no product's copy in waits behind another's copy out and the transfers
-    # of one product overlap the kernels of the others; the step ends when
-    # every stream is done (y is then on the host); issued in
-    # e2e_issue_order's order
+    # of one product overlap the kernels of the others; issued in
+    # e2e_issue_order's order.  Steps are pipelined: the next step's copies in
+    # are issued without waiting for this step's copies out (the host link is
+    # full duplex), each product's stream keeping its own buffers in order;
+    # the timed region ends when every stream is done (all y on the host).
+    # The same steps synchronised one by one are reported beside it.
     order = e2e_issue_order([p["pick_ms"] for p in prods])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
 
-    def e2e_step():
+    def e2e_step(sync):
         for j in order:
             xh, yh = pinned[j]
             prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
+        if sync:
+            for st in streams:
+                st.synchronize()
+
+    e2e_step(True)
+    E = max(1, args.e2e_steps)
+    e2e_rates = {}
+    for mode in ("pipelined", "synced"):
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(E):
+            e2e_step(mode == "synced")
         for st in streams:
             st.synchronize()
-
-    e2e_step()
-    E = max(1, args.e2e_steps)
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(E):
-        e2e_step()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
-    e2e_value = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e_rates[mode] = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
+    e2e_value = e2e_rates["pipelined"]
 
     extra = selector_regret(prods, time_variant) if args.workload == "selector" else None
     line = None
@@ -626,8 +627,9 @@ def run_products(args, ctx):
             "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "+".join(dtypes), "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "selector": select,
-                       "streams": ("a stream per product on the steps without per-product events (every "
-                                   f"{stride}th step carries them and runs on one stream)")
+                       "streams": ("smat_spmv_many (the products side by side on library streams) on the "
+                                   f"steps without per-product events; every {stride}th step carries them and "
+                                   "runs its products one after another on one stream")
                        if args.concurrent else "one stream",
                        "l2": "inputs larger than L2: the step streams "
                              f"{sum(algorithmic_bytes(p['f'], p['plan']['variant'], p['dt']) for p in prods) / 1e6:.0f}"
@@ -650,7 +652,10 @@ def run_products(args, ctx):
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": E,
-                    "how": "smat_spmv_host_async per product from pinned host x/y, a stream per product, issued shortest first with the two longest at the second and middle places, all synced per step"},
+                    "how": "smat_spmv_host_async per product from pinned host x/y, a stream per product, issued "
+                           "shortest first with the two longest at the second and middle places; steps pipelined "
+                           "(all streams synced at the end of the timed region)",
+                    "synced_per_step": round(e2e_rates["synced"], 3)},
             "cpu_baseline": cpu,
             "per_matrix": per,
         }
@@ -736,21 +741,25 @@ def run_batched(args, ctx):
     xh = [x.cpu().pin_memory() for x in xs]
     yh = [torch.zeros_like(y, device="cpu").pin_memory() for y in ys]
 
-    def e2e_step():
+    def e2e_step(sync):
         for h, x in zip(xh, xs):
             x.copy_(h, non_blocking=True)
         B.spmv(xs, ys)
         for h, y in zip(yh, ys):
             h.copy_(y, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        if sync:
+            torch.cuda.current_stream().synchronize()
 
-    e2e_step()
+    # one stream keeps each step's copies, product and copies out in order;
+    # steps are issued back to back and the stream synchronised at the end
+    e2e_step(True)
     E = max(1, min(args.e2e_steps, 50))
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(E):
-        e2e_step()
+        e2e_step(False)
+    torch.cuda.current_stream().synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     line = None
     if rank == 0:
@@ -775,7 +784,7 @@ def run_batched(args, ctx):
                     "h2d_bytes_per_step": sum(h.numel() * 8 for h in xh),
                     "d2h_bytes_per_step": sum(h.numel() * 8 for h in yh), "steps": E,
                     "how": "every x copied from pinned host memory, one batched product, every y copied back; "
-                           "one stream, synced per step"},
+                           "one stream, steps issued back to back and synced at the end"},
             "cpu_baseline": cpu,
             "batched": {"batched_ms": round(d, 5), "per_matrix_launches_ms": round(t_loop, 5),
                         "speedup_vs_per_matrix": round(t_loop / d, 3), "batch_info": info,
