@@ -462,6 +462,13 @@ typedef struct {
   int32_t ctas_per_sm;  /* resident CTAs per SM; 0 = autotune over {2,4,8}       */
   int32_t trial_reps;   /* timed launches per autotuning candidate             */
   int32_t mode;         /* smat_batch_mode_t; default SMAT_BATCH_AUTO          */
+  int32_t own_launches; /* graph plans: members running their own plans'
+                           kernels on side branches of the graph, beside the
+                           persistent kernels: 0 none, 1 the members whose
+                           plan has no batch kind (SPLIT, COO, HYB, BCSR,
+                           merge-path), 2 all; -1 (default) times 0, 1 (when
+                           there are members of both sorts) and, in AUTO
+                           mode, 2, and keeps the fastest                     */
 } smat_batch_opts_t;
 
 typedef struct {
@@ -470,6 +477,9 @@ typedef struct {
   int32_t per_matrix;   /* 1: the members' own launches won the tuning         */
   double graph_ms;      /* median time of the best graph plan (-1: not timed)  */
   double per_matrix_ms; /* median time of the per-matrix launches (-1: not timed) */
+  int32_t own_launches; /* members running their own plans' kernels on side
+                           branches of the graph: 0 none, 1 those whose plan
+                           has no batch kind, 2 all                         */
 } smat_batch_info_t;
 
 /* Defaults: tile_scale 0 and ctas_per_sm 0 (both autotuned), trial_reps 10,
@@ -484,7 +494,10 @@ smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int3
 
 /* Build the work table (row tiles of every product, largest first), capture
  * the persistent launch in a CUDA graph and autotune tile size and CTAs per
- * SM by timing the graph.  In SMAT_BATCH_AUTO mode the members' own launches,
+ * SM by timing the graph.  Members whose plan the persistent kernel has no
+ * body for can instead run their own plan's kernels on side branches of the
+ * same graph (opts.own_launches); their pointers and scalars are then part of
+ * the graph, which smat_batch_spmv captures again when they change.  In SMAT_BATCH_AUTO mode the members' own launches,
  * one after another, are timed too and kept when faster, so a batch is never
  * slower than the loop it replaces (a few large members in formats whose
  * single-matrix kernels outrun the persistent kernel's bodies).  Returns

@@ -76,13 +76,14 @@ class smat_cg_info_t(ctypes.Structure):
 
 class smat_batch_opts_t(ctypes.Structure):
     _fields_ = [("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("trial_reps", ctypes.c_int32),
-                ("mode", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("own_launches", ctypes.c_int32)]
 
 
 class smat_batch_info_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("tiles", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("tile_scale", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tuned_ms", ctypes.c_double),
-                ("per_matrix", ctypes.c_int32), ("graph_ms", ctypes.c_double), ("per_matrix_ms", ctypes.c_double)]
+                ("per_matrix", ctypes.c_int32), ("graph_ms", ctypes.c_double), ("per_matrix_ms", ctypes.c_double),
+                ("own_launches", ctypes.c_int32)]
 
 
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64

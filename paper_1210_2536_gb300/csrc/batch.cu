@@ -198,8 +198,17 @@ struct smat_batch_s {
   int kind_tiles[smat::NKIND] = {}, kind_first[smat::NKIND] = {}, kind_grid[smat::NKIND] = {};
   double tuned_ms = -1.0, graph_ms = -1.0, loop_ms = -1.0;
   bool loop = false;  // the members' own launches in turn won the tuning
-  cudaStream_t cap = nullptr, fork[smat::NKIND - 1] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[smat::NKIND - 1] = {};
+  // Which members run their own plan's kernels inside the graph, on the
+  // side branches own_st (0: none; 1: those whose plan has no batch kind;
+  // 2: all), and the pointers and scalars baked into those launches.
+  int own_mode = 0;
+  std::vector<char> own;
+  std::vector<const void *> own_x;
+  std::vector<void *> own_y;
+  std::vector<double> own_a, own_b;
+  static constexpr int OWN_N = 4;
+  cudaStream_t cap = nullptr, fork[smat::NKIND - 1] = {}, own_st[OWN_N] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[smat::NKIND - 1] = {}, ev_own[OWN_N] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ready = false;
@@ -257,7 +266,7 @@ std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
   const int R = 16 / elem_size(b->dtype);
   for (size_t i = 0; i < b->mats.size(); ++i) {
     const BatchMat &M = b->mats[i];
-    if (M.m == 0) continue;
+    if (M.m == 0 || (!b->own.empty() && b->own[i])) continue;
     if (M.kind == KIND_CSR) {
       const std::vector<int32_t> &rp = b->rowptrs[i];
       const long long target = 2048LL * scale;
@@ -301,8 +310,50 @@ std::vector<BatchTile> make_tiles(const smat_batch_s *b, int scale) {
   return out;
 }
 
-smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
+// A member the persistent kernel runs natively: CSR-scalar / vector, ELL,
+// DIA, SELL (the others run there through a CSR row kernel).
+bool batch_native(const smat_s *h) {
+  switch (h->variant) {
+    case SMAT_V_CSR_SCALAR: case SMAT_V_CSR_VEC4: case SMAT_V_CSR_VEC8: case SMAT_V_CSR_VEC32:
+    case SMAT_V_ELL: case SMAT_V_DIA: case SMAT_V_SELL:
+      return true;
+  }
+  return false;
+}
+
+// A member's own product (its plan's kernels) on stream st.
+cudaError_t own_launch(const smat_batch_s *b, size_t i, cudaStream_t st) {
+  const smat_s *h = b->hs[i];
+  const double a = b->own_a[i], c = b->own_b[i];
+  const float af = (float)a, cf = (float)c;
+  const bool f64 = b->dtype == SMAT_F64;
+  return launch_spmv(h, h->variant, f64 ? (const void *)&a : (const void *)&af, b->own_x[i],
+                     f64 ? (const void *)&c : (const void *)&cf, b->own_y[i], st);
+}
+
+smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm, int own_mode) {
   free_graph(b);
+  const size_t n = b->hs.size();
+  b->own_mode = own_mode;
+  b->own.assign(n, 0);
+  for (size_t i = 0; i < n; ++i)
+    b->own[i] = b->mats[i].m > 0 && (own_mode == 2 || (own_mode == 1 && !batch_native(b->hs[i])));
+  // the own launches' pointers and scalars, as the descriptors hold them now
+  b->own_x.assign(n, nullptr);
+  b->own_y.assign(n, nullptr);
+  b->own_a.assign(n, 1.0);
+  b->own_b.assign(n, 0.0);
+  int k_own = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (b->own[i]) {
+      b->own_x[i] = b->mats[i].x; b->own_y[i] = b->mats[i].y;
+      b->own_a[i] = b->mats[i].alpha; b->own_b[i] = b->mats[i].beta;
+      // carries of merge / COO / SPLIT plans: the branch stream's own scratch,
+      // allocated now, outside the capture
+      Scratch sc{};
+      BTRY(stream_scratch(b->hs[i], b->own_st[k_own % smat_batch_s::OWN_N], &sc, true));
+      ++k_own;
+    }
   dev_free(b->d_tiles);
   b->d_tiles = nullptr;
   std::vector<BatchTile> tiles = make_tiles(b, scale);
@@ -342,6 +393,18 @@ smat_status_t build_plan(smat_batch_s *b, int scale, int ctas_per_sm) {
     err = cudaEventRecord(b->ev_join[k - 1], st[k]);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, b->ev_join[k - 1], 0);
   }
+  // the members that run their own plans, round robin on the side branches
+  if (k_own > 0) {
+    const int used = std::min(k_own, smat_batch_s::OWN_N);
+    for (int k = 0; k < used && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(b->own_st[k], b->ev_fork, 0);
+    int j = 0;
+    for (size_t i = 0; i < n && err == cudaSuccess; ++i)
+      if (b->own[i]) err = own_launch(b, i, b->own_st[j++ % smat_batch_s::OWN_N]);
+    for (int k = 0; k < used && err == cudaSuccess; ++k) {
+      err = cudaEventRecord(b->ev_own[k], b->own_st[k]);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, b->ev_own[k], 0);
+    }
+  }
   cudaError_t e3 = cudaStreamEndCapture(b->cap, &b->graph);
   BTRY(err);
   BTRY(e3);
@@ -375,6 +438,10 @@ smat_status_t smat_batch_create(smat_batch_t *out, const smat_handle_t *hs, int3
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
   for (int k = 0; k < NKIND - 1 && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  for (int k = 0; k < smat_batch_s::OWN_N && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->own_st[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_own[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) return fail(SMAT_ERR_CUDA);
   void *p = nullptr;
   if ((e = dev_alloc(&p, NKIND * sizeof(unsigned int))) != cudaSuccess) return fail(st_of(e));
@@ -395,6 +462,10 @@ smat_status_t smat_batch_destroy(smat_batch_t b) {
   for (int k = 0; k < NKIND - 1; ++k) {
     if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
     if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  for (int k = 0; k < smat_batch_s::OWN_N; ++k) {
+    if (b->own_st[k]) cudaStreamDestroy(b->own_st[k]);
+    if (b->ev_own[k]) cudaEventDestroy(b->ev_own[k]);
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -453,13 +524,41 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
   BTRY(cudaEventCreate(&e1));
   struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
   double best = 1e30;
-  int best_s = scales[0], best_c = ctas[0];
+  int best_s = scales[0], best_c = ctas[0], best_own = 0;
   const int reps = std::max(1, o.trial_reps);
   if (o.mode == SMAT_BATCH_PER_MATRIX) scales.clear();
-  for (int sc : scales) {
-    for (int cp : ctas) {
+  // own-launch modes worth timing: the non-native members on side branches
+  // (when there are both kinds), and every member on them (AUTO only)
+  bool any_own = false, any_native = false;
+  for (int i = 0; i < n; ++i) {
+    if (b->mats[(size_t)i].m == 0) continue;
+    if (batch_native(b->hs[(size_t)i])) any_native = true; else any_own = true;
+  }
+  std::vector<int> owns;
+  if (o.own_launches >= 0 && o.own_launches <= 2) {
+    owns.push_back(o.own_launches);
+  } else if (o.own_launches != -1) {
+    return SMAT_ERR_INVALID_ARG;
+  } else {
+    owns.push_back(0);
+    if (any_own && any_native) owns.push_back(1);
+    if (o.mode == SMAT_BATCH_AUTO) owns.push_back(2);
+  }
+  struct Cand { int sc, cp, own; };
+  std::vector<Cand> cands;
+  for (int ow : owns) {
+    if (ow == 2) {  // no persistent kernels: one shape only
+      if (!scales.empty()) cands.push_back({scales[0], ctas[0], 2});
+      continue;
+    }
+    for (int sc : scales)
+      for (int cp : ctas) cands.push_back({sc, cp, ow});
+  }
+  for (const Cand &cd : cands) {
+    {
+      const int sc = cd.sc, cp = cd.cp;
       {
-        smat_status_t st = build_plan(b, sc, cp);
+        smat_status_t st = build_plan(b, sc, cp, cd.own);
         if (st != SMAT_OK) return st;
       }
       for (int w = 0; w < 2; ++w) BTRY(cudaGraphLaunch(b->exec, s));
@@ -473,7 +572,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
       }
       std::nth_element(ms.begin(), ms.begin() + reps / 2, ms.end());
       const double med = ms[(size_t)reps / 2];
-      if (med < best) { best = med; best_s = sc; best_c = cp; }
+      if (med < best) { best = med; best_s = sc; best_c = cp; best_own = cd.own; }
     }
   }
   b->graph_ms = scales.empty() ? -1.0 : best;
@@ -513,7 +612,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
     b->tuned_ms = b->loop_ms;
     b->ready = true;
   } else {
-    smat_status_t st = build_plan(b, best_s, best_c);
+    smat_status_t st = build_plan(b, best_s, best_c, best_own);
     if (st != SMAT_OK) return st;
     b->tuned_ms = best;
   }
@@ -554,6 +653,21 @@ smat_status_t smat_batch_spmv(smat_batch_t b, const void *alphas, const void *co
     }
     return SMAT_OK;
   }
+  // members with their own launches in the graph carry their pointers and
+  // scalars in it: a change there means capturing the graph again (the
+  // previous graph launch on `s` is finished with them once `s` reaches here)
+  bool recapture = false;
+  for (int i = 0; i < n && !recapture; ++i) {
+    if (b->own.empty() || !b->own[(size_t)i]) continue;
+    const BatchMat &M = b->mats[(size_t)i];
+    recapture = M.x != b->own_x[(size_t)i] || M.y != b->own_y[(size_t)i] || M.alpha != b->own_a[(size_t)i] ||
+                M.beta != b->own_b[(size_t)i];
+  }
+  if (recapture) {
+    BTRY(cudaStreamSynchronize(s));
+    smat_status_t st = build_plan(b, b->tile_scale, b->ctas_per_sm, b->own_mode);
+    if (st != SMAT_OK) return st;
+  }
   if (changed)
     BTRY(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * (size_t)n, cudaMemcpyHostToDevice, s));
   BTRY(cudaGraphLaunch(b->exec, s));
@@ -571,6 +685,7 @@ smat_status_t smat_batch_get_info(smat_batch_t b, smat_batch_info_t *info) {
   info->per_matrix = b->loop ? 1 : 0;
   info->graph_ms = b->graph_ms;
   info->per_matrix_ms = b->loop_ms;
+  info->own_launches = b->loop ? 0 : b->own_mode;
   return SMAT_OK;
 }
 
@@ -581,6 +696,7 @@ void smat_batch_opts_default(smat_batch_opts_t *o) {
   o->ctas_per_sm = 0;
   o->trial_reps = 10;
   o->mode = SMAT_BATCH_AUTO;
+  o->own_launches = -1;
 }
 
 }  // extern "C"

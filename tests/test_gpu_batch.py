@@ -71,6 +71,43 @@ def test_batch_matches_oracle_and_single_products(dtype, mode):
         M.close()
 
 
+@pytest.mark.parametrize("own", [0, 1, 2])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_own_launches_on_side_branches(dtype, own):
+    # members whose plan has no batch kind (here COO, merge-path and, when
+    # admissible, SPLIT) run their own kernels on side branches of the graph
+    # (own = 1), or every member does (own = 2); the graph is captured again
+    # when those members' vectors or scalars change between calls
+    mats = _members()
+    hs = _handles(mats, dtype)
+    hs[4].tune("fixed", variant=smat.SMAT_V_COO)
+    hs[5].tune("fixed", variant=smat.SMAT_V_CSR_MERGE)
+    for M in hs[6:]:
+        if (M.features()["admissible"] >> smat.SMAT_V_SPLIT) & 1:
+            M.tune("fixed", variant=smat.SMAT_V_SPLIT)
+            break
+    B = smat.Batch(hs).tune(trial_reps=3, mode=smat.SMAT_BATCH_GRAPH, own_launches=own)
+    info = B.info()
+    assert info["per_matrix"] == 0 and info["own_launches"] == own
+    npdt = np.float64 if dtype == "f64" else np.float32
+    for call, seed in enumerate((1, 4, 4)):
+        xs = [torch.from_numpy(synth.uniform(seed + i, 1, A.n).astype(npdt)).to(DEV) for i, A in enumerate(mats)]
+        y0 = [synth.uniform(seed + i, 2, A.m).astype(npdt) for i, A in enumerate(mats)]
+        ys = [torch.from_numpy(v.copy()).to(DEV) for v in y0]
+        alphas = [0.5 + 0.25 * i for i in range(len(mats))]
+        betas = [0.0 if (i + call) % 2 else 1.5 for i in range(len(mats))]
+        B.spmv(xs, ys, alphas, betas)
+        torch.cuda.synchronize()
+        for i, A in enumerate(mats):
+            _, v64 = stored_values(A, dtype)
+            ref, scale = reference(A, v64, xs[i].cpu().numpy(), alphas[i], betas[i], y0[i] if betas[i] else None)
+            assert_close_rows(ys[i].cpu().numpy().astype(np.float64), ref, scale, TOL[dtype],
+                              f"own {own} call {call} member {i} ({A.name}, {hs[i].plan()['name']})")
+    B.close()
+    for M in hs:
+        M.close()
+
+
 def test_batch_rejects_mixed_dtypes_and_untuned_use():
     A = synth.stencil3d7(6)
     h64 = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
