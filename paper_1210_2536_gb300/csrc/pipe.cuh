@@ -56,6 +56,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
   return true;
 }
 
+// Orders this thread's earlier generic-proxy accesses to shared memory
+// before later asynchronous-proxy accesses (the bulk copies).  A consumer
+// runs it before releasing a stage: the copy that refills the stage is an
+// async-proxy write, and the mbarrier release alone does not order it after
+// the consumer's reads.  A ring released without it handed consumers data
+// of the wrong tile when stages were refilled quickly.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // L2 policy for data read exactly once (the matrix arrays): evict first, so
 // that x, which every product gathers from, keeps its place in L2.
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(32 * (ST_CFG[CFG].warps + 1), ST_CFG[CFG].ctas
         }
         y[i] = ep(acc, y, i);
       }
+      fence_proxy_async_smem();  // reads of the stage before the copy that refills it
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }

@@ -102,6 +102,51 @@ def test_staged_dia_matches_the_oracle(name):
     assert smat.smat_get_wait_timeouts() == timeouts0
 
 
+def full_bands(m, offsets, seed):
+    """Every row i holds the columns i + d, d in `offsets`, that land in [0, m); values N(0, 1)."""
+    offs = np.sort(np.asarray(offsets, dtype=np.int64))
+    cols = np.arange(m, dtype=np.int64)[:, None] + offs[None, :]
+    keep = (cols >= 0) & (cols < m)
+    rowptr = np.zeros(m + 1, np.int32)
+    rowptr[1:] = np.cumsum(keep.sum(axis=1))
+    colidx = cols[keep].astype(np.int32)
+    val = np.random.default_rng(seed).standard_normal(len(colidx))
+    return CSR(m, m, rowptr, colidx, val, name=f"bands_{m}_{len(offs)}")
+
+
+LIGHT = {
+    # one or two stripes over millions of rows: a consumer does little work per
+    # stage, so a released stage is refilled within microseconds, and every CTA
+    # reuses each stage of its ring several times (5 to 18 tiles per CTA)
+    "diag_f32": (1 << 24, [0], "f32"),
+    "bidiag_f64": (1 << 23, [-1, 0], "f64"),
+    "diag_bf16": (1 << 24, [0], "bf16"),
+}
+
+
+@pytest.mark.parametrize("name", list(LIGHT))
+def test_staged_dia_light_stages_repeated(name):
+    # a stage released by the consumers and refilled by the next bulk copy
+    # must never hand a consumer data of another tile: repeated products on
+    # the lightest stages, every row checked each time
+    m, offsets, dtype = LIGHT[name]
+    A = full_bands(m, offsets, 11)
+    M, vals64 = _handle(A, dtype)
+    np_t = np.float64 if dtype == "f64" else np.float32
+    x = synth.uniform(13, 1, A.n).astype(np_t)
+    y0 = np.zeros(A.m, np_t)
+    _product(M, A, dtype, x, y0, 1.0, 0.0)
+    ref, scale = reference(A, vals64, x, 1.0, 0.0, None)
+    timeouts0 = smat.smat_get_wait_timeouts()
+    for k in STAGED_SHAPES:
+        M.set_kernel(smat.SMAT_V_DIA, k)
+        for rep in range(6):
+            got = _product(M, A, dtype, x, y0, 1.0, 0.0)
+            assert_close_rows(got, ref, scale, TOL[dtype], f"{name} staged {k} repeat {rep}")
+    assert smat.smat_get_wait_timeouts() == timeouts0
+    M.close()
+
+
 def test_staged_waits_that_run_out_leave_the_context_usable():
     # the test hook makes the consumers wait on a barrier nothing arrives on,
     # for 2e6 cycles (~1 ms): the kernel gives up, waits for its own copies,
