@@ -403,6 +403,7 @@ void free_format(smat_s *h, int fmt) {
   } else if (fmt == SMAT_FMT_BCSR) {  // the 64-bit block row starts stay
     dev_free(h->bcsr_rowptr); dev_free(h->bcsr_col); dev_free(h->bcsr_val);
     h->bcsr_rowptr = h->bcsr_col = nullptr; h->bcsr_val = nullptr;
+    h->bcsr_cb = 0;
   } else if (fmt == SMAT_FMT_SPLIT) {
     for (int32_t **p : {&h->split_lchunk, &h->split_lrows, &h->split_crow, &h->split_cstart, &h->split_cend,
                         &h->split_srow, &h->split_scol, &h->split_empty}) {
@@ -709,6 +710,17 @@ smat_status_t build_format(smat_s *h, int fmt, cudaStream_t s) {
       TRY(dev_alloc(&p, (size_t)h->bcsr_nb * 4)); h->bcsr_col = (int32_t *)p;
       TRY(dev_alloc(&p, (size_t)(h->bcsr_nb * bb) * h->esz)); h->bcsr_val = p;
       TRY(launch_to_bcsr(h, h->bcsr_brp64, s));
+      h->bcsr_cb = 0;
+      if (h->bcsr_mb > 0 && h->bcsr_nb > 0 && h->bcsr_nb % h->bcsr_mb == 0) {
+        DevBuf flag(s);
+        TRY(flag.alloc(4));
+        TRY(cudaMemsetAsync(flag.p, 0, 4, s));
+        TRY(launch_bcsr_uniform(h, h->bcsr_nb / h->bcsr_mb, flag.as<int>(), s));
+        int f = 1;
+        TRY(cudaMemcpyAsync(&f, flag.p, 4, cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        if (f == 0) h->bcsr_cb = (int32_t)(h->bcsr_nb / h->bcsr_mb);
+      }
     }
     undo.armed = false;
     return SMAT_OK;

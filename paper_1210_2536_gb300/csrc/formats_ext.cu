@@ -443,13 +443,16 @@ constexpr int BCSR_R2 = SMAT_BCSR_R2;  // block rows per lane group
 // the loads of all R2 blocks of a step are in flight at once.  Measured on
 // GB300 (block-diagonal 8x8, 7-point, uniform; FP64 and FP32): R2 = 1 is
 // fastest, the extra registers of R2 = 2 or 4 cost more occupancy than the
-// loads in flight gain.
+// loads in flight gain.  When every block row holds the same number cb of
+// blocks, block row I's blocks are I*cb ... I*cb + cb - 1 and the block-row
+// pointers are not read: the value loads start at once and x waits for one
+// load (the block column) instead of two.
 template <typename V, int BS, int R2, int MODE>
 __global__ void __launch_bounds__(256) bcsr_kernel(const int32_t *__restrict__ browptr, const int32_t *__restrict__ bcol,
                                                    const V *__restrict__ bval, const typename Compute<V>::T *__restrict__ x,
                                                    Epi<typename Compute<V>::T, MODE> ep,
                                                    typename Compute<V>::T *__restrict__ y, long long m, long long n,
-                                                   long long mb) {
+                                                   long long mb, int cb) {
   griddep_wait();
   typedef typename Compute<V>::T T;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,8 +463,13 @@ __global__ void __launch_bounds__(256) bcsr_kernel(const int32_t *__restrict__ b
 #pragma unroll
   for (int q = 0; q < R2; ++q) {
     const bool in = I0 + q < mb;
-    k[q] = in ? __ldg(browptr + I0 + q) : 0;
-    kend[q] = in ? __ldg(browptr + I0 + q + 1) : 0;
+    if (cb > 0) {
+      k[q] = in ? (int)((I0 + q) * cb) : 0;
+      kend[q] = in ? k[q] + cb : 0;
+    } else {
+      k[q] = in ? __ldg(browptr + I0 + q) : 0;
+      kend[q] = in ? __ldg(browptr + I0 + q + 1) : 0;
+    }
     steps = max(steps, kend[q] - k[q]);
   }
   T acc[R2];
@@ -511,11 +519,11 @@ cudaError_t ext_mode(const smat_s *h, int variant, typename Compute<V>::T alpha,
   const int g = grid_for((mb + BCSR_R2 - 1) / BCSR_R2 * h->bcsr_b, 256, INT_MAX);
   switch (h->bcsr_b) {
     case 2: (void)launch_pdl(bcsr_kernel<V, 2, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
-                                                                 ep, y, h->m, h->n, mb); break;
+                                                                 ep, y, h->m, h->n, mb, h->bcsr_cb); break;
     case 4: (void)launch_pdl(bcsr_kernel<V, 4, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
-                                                                 ep, y, h->m, h->n, mb); break;
+                                                                 ep, y, h->m, h->n, mb, h->bcsr_cb); break;
     default: (void)launch_pdl(bcsr_kernel<V, 8, BCSR_R2, MODE>, dim3(g), dim3(256), 0, s, h->bcsr_rowptr, h->bcsr_col, (const V *)h->bcsr_val, x,
-                                                                  ep, y, h->m, h->n, mb); break;
+                                                                  ep, y, h->m, h->n, mb, h->bcsr_cb); break;
   }
   return cudaGetLastError();
 }
@@ -630,6 +638,17 @@ cudaError_t launch_to_bcsr(const smat_s *h, const long long *brp, cudaStream_t s
     case 4: return to_bcsr_b<4>(h, brp, s);
     default: return to_bcsr_b<8>(h, brp, s);
   }
+}
+
+__global__ void bcsr_uniform_kernel(const long long *__restrict__ brp, long long mb, long long c, int *__restrict__ flag) {
+  for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < mb; I += (long long)gridDim.x * blockDim.x)
+    if (brp[I + 1] - brp[I] != c) *flag = 1;
+}
+
+cudaError_t launch_bcsr_uniform(const smat_s *h, long long c, int *flag, cudaStream_t s) {
+  if (h->bcsr_mb <= 0) return cudaSuccess;
+  bcsr_uniform_kernel<<<grid_for(h->bcsr_mb, 256, 152 * 8), 256, 0, s>>>(h->bcsr_brp64, h->bcsr_mb, c, flag);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_counts(const smat_s *h, long long *cl, long long *cc, long long *cs, long long *ce,

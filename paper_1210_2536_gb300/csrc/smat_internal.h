@@ -110,6 +110,7 @@ struct smat_s {
   int32_t bcsr_b = 0;
   int64_t bcsr_mb = 0, bcsr_nb = 0;
   long long *bcsr_brp64 = nullptr;
+  int32_t bcsr_cb = 0;  // blocks in every block row when all block rows hold the same count, else 0
   int32_t *bcsr_rowptr = nullptr, *bcsr_col = nullptr;
   void *bcsr_val = nullptr;
   // SPLIT: rows of >= SPLIT_L entries in chunks of <= SPLIT_CK, short rows as COO
@@ -191,6 +192,9 @@ cudaError_t launch_split_counts(const smat_s *h, long long *cl, long long *cc, l
 cudaError_t launch_split_fill(const smat_s *h, const long long *pl, const long long *pc, const long long *ps,
                               const long long *pe, cudaStream_t s);
 cudaError_t launch_to_bcsr(const smat_s *h, const long long *brp, cudaStream_t s);
+// Sets *flag (zeroed by the caller) when a block row of the built layout holds
+// a block count other than c.
+cudaError_t launch_bcsr_uniform(const smat_s *h, long long c, int *flag, cudaStream_t s);
 // SELL / BCSR products (HYB runs through the ELL and COO kernels of spmv.cu).
 cudaError_t launch_spmv_ext(const smat_s *h, int variant, const void *alpha, const void *x,
                             const void *beta, void *y, cudaStream_t s);

@@ -167,6 +167,61 @@ def test_ext_misaligned_vectors_are_safe(dtype, mk):
     M.close()
 
 
+def _csr_from_coo(m, n, rows, cols, seed, name):
+    from paper_1210_2536_gb300.synth import CSR
+    order = np.lexsort((cols, rows))
+    rows, cols = np.asarray(rows)[order], np.asarray(cols)[order]
+    rowptr = np.zeros(m + 1, np.int32)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    val = np.random.default_rng(seed).standard_normal(len(cols))
+    return CSR(m, n, rowptr, cols.astype(np.int32), val, name=name)
+
+
+def _uneven_blocks(m, b, seed):
+    # even block rows hold two dense b x b blocks (their own and one far away),
+    # odd block rows none: as many blocks as block rows, but not one per row
+    rows, cols = [], []
+    mb = (m + b - 1) // b
+    for I in range(0, mb, 2):
+        J2 = (I + mb // 2) % mb
+        for J in (I, J2):
+            for r in range(I * b, min(m, I * b + b)):
+                for c in range(J * b, min(m, J * b + b)):
+                    rows.append(r)
+                    cols.append(c)
+    return _csr_from_coo(m, m, rows, cols, seed, f"uneven_blocks_{m}")
+
+
+def _blockdiag_plus_one(m, b, seed):
+    A = synth.blockdiag(m, b, seed)
+    rows = np.repeat(np.arange(m), np.diff(A.rowptr))
+    return _csr_from_coo(m, m, np.append(rows, 5), np.append(A.colidx, m - 1), seed, f"blockdiag_plus_one_{m}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("mk", [lambda: synth.blockdiag(20000, 8, 4), lambda: synth.blockdiag(999, 8, 2),
+                                lambda: _uneven_blocks(4000, 8, 5), lambda: _blockdiag_plus_one(4000, 8, 6)],
+                         ids=["uniform", "uniform_ragged", "uneven_same_count", "one_extra_block"])
+def test_bcsr_uniform_and_uneven_block_rows(dtype, mk):
+    # block rows that all hold the same number of blocks skip the block-row
+    # pointers; a layout whose block count divides evenly among the block
+    # rows without every row holding that count, and one that does not
+    # divide, read them; all match the oracle
+    A = mk()
+    M, vals64 = make(A, dtype)
+    x = vec(synth.uniform(3, 1, A.n), dtype)
+    y0 = vec(synth.uniform(3, 2, A.m), dtype)
+    assert _convert(M, smat.SMAT_FMT_BCSR), A.name
+    for alpha, beta in [(1.0, 0.0), (-2.0, 0.5)]:
+        ref, scale = reference(A, vals64, x, alpha, beta, y0 if beta != 0 else None)
+        y = torch.from_numpy(y0.copy()).to(DEV)
+        M.spmv(torch.from_numpy(x).to(DEV), y, alpha, beta, variant=smat.SMAT_V_BCSR)
+        torch.cuda.synchronize()
+        assert_close_rows(y.cpu().numpy().astype(np.float64), ref, scale, TOL[dtype], f"{A.name} {dtype} a={alpha} b={beta}")
+    M.close()
+
+
 def test_ext_formats_in_the_search():
     # exhaustive mode times every admissible variant, the further formats too
     A = synth.blockdiag(200000, 8, 1)
