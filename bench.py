@@ -496,11 +496,12 @@ def run_products(args, ctx):
 
     # ---- timed region: K steps of all products through their plans ----
     K, W = args.steps, args.warmup
-    # per-product events on every 4th step (at most 100 steps): an event
+    # per-product events on every 8th step (at most 50 steps): an event
     # between two kernels costs idle GPU time (the step's eight products ran
-    # in 0.512 ms without events, 0.57 ms with a pair around each), which the
-    # steps without them do not pay
-    stride = max(4, K // 100)
+    # in 0.512 ms without events, 0.57 ms with a pair around each), and such
+    # a step runs its products one after another (0.50 ms against 0.47 ms
+    # side by side), which the steps without them do not pay
+    stride = max(8, K // 50)
     sampled = list(range(stride // 2, K, stride)) or [0]
     # one event between consecutive products: product j runs between events
     # j and j + 1 of its step
