@@ -574,46 +574,114 @@ def run_products(args, ctx):
         r.pop("_d")
         r.pop("alg_bytes")
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- end to end: inputs from pinned host memory, results back to it ----
+    # Pipelined steps (the figure reported): each storage type's x of all
+    # products sit in one pinned host buffer and one device buffer, their y
+    # likewise, so that each direction is one copy per storage type; two sets
+    # of device buffers alternate between steps, and copies in, the products
+    # (side by side through smat_spmv_many) and copies out run on three
+    # streams, so that one set's transfers overlap the other set's products.
+    # A step's copies in wait until the products two steps back have read
+    # that set's x, its products until that set's previous copies out have
+    # read y, its copies out until its products are done; the timed region
+    # ends when every y is on the host.
+    def packed(sizes):
+        offs, o = [], 0
+        for k in sizes:
+            offs.append(o)
+            o += (k + 31) // 32 * 32            # every vector 128-byte aligned or more
+        return offs, o
+    tdts = sorted({p["x"].dtype for p in prods}, key=str)
+    grp = {t: [j for j, p in enumerate(prods) if p["x"].dtype == t] for t in tdts}
+    xoff, yoff, xtot, ytot = {}, {}, {}, {}
+    for t, js in grp.items():
+        xo, xtot[t] = packed([prods[j]["A"].n for j in js])
+        yo, ytot[t] = packed([prods[j]["A"].m for j in js])
+        xoff.update(zip(js, xo))
+        yoff.update(zip(js, yo))
+    xh_pack = {t: torch.zeros(xtot[t], dtype=t).pin_memory() for t in tdts}
+    for j, p in enumerate(prods):
+        xh_pack[p["x"].dtype][xoff[j]:xoff[j] + p["A"].n] = p["x"].cpu()
+    yh_pack = [{t: torch.zeros(ytot[t], dtype=t).pin_memory() for t in tdts} for _ in range(2)]
+    Xd = [{t: torch.zeros(xtot[t], dtype=t, device=dev) for t in tdts} for _ in range(2)]
+    Yd = [{t: torch.zeros(ytot[t], dtype=t, device=dev) for t in tdts} for _ in range(2)]
+    xv = [[Xd[q][p["x"].dtype][xoff[j]:xoff[j] + p["A"].n] for j, p in enumerate(prods)] for q in range(2)]
+    yv = [[Yd[q][p["x"].dtype][yoff[j]:yoff[j] + p["A"].m] for j, p in enumerate(prods)] for q in range(2)]
+    h2d = sum(b.numel() * b.element_size() for b in xh_pack.values())
+    d2h = sum(b.numel() * b.element_size() for b in yh_pack[0].values())
+    mats = [p["M"] for p in prods]
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    run_done = [torch.cuda.Event(), torch.cuda.Event()]
+    out_done = [torch.cuda.Event(), torch.cuda.Event()]
+    x_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    for q in range(2):
+        run_done[q].record(s_run)
+        out_done[q].record(s_out)
+    n_e2e = [0]
+
+    def e2e_pipelined():
+        q = n_e2e[0] % 2
+        n_e2e[0] += 1
+        s_in.wait_event(run_done[q])
+        with torch.cuda.stream(s_in):
+            for t in tdts:
+                Xd[q][t].copy_(xh_pack[t], non_blocking=True)
+        x_ready[q].record(s_in)
+        s_run.wait_event(x_ready[q])
+        s_run.wait_event(out_done[q])
+        if args.concurrent:
+            smat.spmv_many(mats, xv[q], yv[q], stream=s_run)
+        else:
+            for M, x, y in zip(mats, xv[q], yv[q]):
+                M.spmv(x, y, stream=s_run)
+        run_done[q].record(s_run)
+        s_out.wait_event(run_done[q])
+        with torch.cuda.stream(s_out):
+            for t in tdts:
+                yh_pack[q][t].copy_(Yd[q][t], non_blocking=True)
+        out_done[q].record(s_out)
+
+    e2e_pipelined()
+    e2e_pipelined()
+    torch.cuda.synchronize()
+    # the products that came back equal the ones timed above (same x)
+    for q in range(2):
+        for j, p in enumerate(prods):
+            ref = p["y"].cpu()
+            got = yh_pack[q][p["x"].dtype][yoff[j]:yoff[j] + p["A"].m]
+            err = (got - ref).abs().max().item() if p["A"].m else 0.0
+            if not err <= 1e-12 * max(ref.abs().max().item() if p["A"].m else 0.0, 1e-300):
+                raise RuntimeError(f"end-to-end product of {p['A'].name} {p['dt']} differs from the timed one ({err:g})")
+
+    # Every step synchronised (reported beside it): smat_spmv_host_async per
+    # product from its own pinned x and y, the library's host-buffer call
+    # (copy in, product, copy out on the handle's staging buffers), a stream
+    # per product, issued in e2e_issue_order's order.
     pinned = []
     for p in prods:
-        xh = p["x"].cpu().pin_memory()
-        yh = torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory()
-        pinned.append((xh, yh))
-    h2d = sum(xh.numel() * xh.element_size() for xh, _ in pinned)
-    d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
-    # each product's copy in, kernel and copy out go to a stream of its own, so
-    # no product's copy in waits behind another's copy out and the transfers
-    # of one product overlap the kernels of the others; issued in
-    # e2e_issue_order's order.  Steps are pipelined: the next step's copies in
-    # are issued without waiting for this step's copies out (the host link is
-    # full duplex), each product's stream keeping its own buffers in order;
-    # the timed region ends when every stream is done (all y on the host).
-    # The same steps synchronised one by one are reported beside it.
+        pinned.append((p["x"].cpu().pin_memory(), torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory()))
     order = e2e_issue_order([p["pick_ms"] for p in prods])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
 
-    def e2e_step(sync):
+    def e2e_synced():
         for j in order:
             xh, yh = pinned[j]
             prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
-        if sync:
-            for st in streams:
-                st.synchronize()
+        for st in streams:
+            st.synchronize()
 
-    e2e_step(True)
-    E = max(1, args.e2e_steps)
+    e2e_synced()
+    E = max(2, args.e2e_steps)
     e2e_rates = {}
-    for mode in ("pipelined", "synced"):
+    for mode, fn in (("pipelined", e2e_pipelined), ("synced", e2e_synced)):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(E):
-            e2e_step(mode == "synced")
-        for st in streams:
-            st.synchronize()
+            fn()
+        torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         e2e_rates[mode] = weak_scaling_throughput(flops_step * E, e2e_s, world) / 1e9
     e2e_value = e2e_rates["pipelined"]
@@ -653,10 +721,14 @@ def run_products(args, ctx):
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": E,
-                    "how": "smat_spmv_host_async per product from pinned host x/y, a stream per product, issued "
-                           "shortest first with the two longest at the second and middle places; steps pipelined "
-                           "(all streams synced at the end of the timed region)",
-                    "synced_per_step": round(e2e_rates["synced"], 3)},
+                    "how": "each storage type's x of all products copied from one pinned host buffer as one "
+                           "transfer, the products side by side (smat_spmv_many), the y copied back as one "
+                           "transfer per storage type; two sets of device buffers alternate between steps; "
+                           "copies in, products and copies out on three streams ordered by events, steps "
+                           "pipelined and synced at the end",
+                    "synced_per_step": round(e2e_rates["synced"], 3),
+                    "synced_how": "smat_spmv_host_async per product from its own pinned x/y (the library's "
+                                  "host-buffer call), a stream per product, every step synchronised"},
             "cpu_baseline": cpu,
             "per_matrix": per,
         }
