@@ -575,7 +575,8 @@ def run_products(args, ctx):
         r.pop("alg_bytes")
 
     # ---- end to end: inputs from pinned host memory, results back to it ----
-    # Pipelined steps (the figure reported): each storage type's x of all
+    # Beside the host-buffer calls below, the device-pointer calls with the
+    # transfers arranged by the caller ("packed"): each storage type's x of all
     # products sit in one pinned host buffer and one device buffer, their y
     # likewise, so that each direction is one copy per storage type; two sets
     # of device buffers alternate between steps, and copies in, the products
@@ -607,8 +608,6 @@ def run_products(args, ctx):
     Yd = [{t: torch.zeros(ytot[t], dtype=t, device=dev) for t in tdts} for _ in range(2)]
     xv = [[Xd[q][p["x"].dtype][xoff[j]:xoff[j] + p["A"].n] for j, p in enumerate(prods)] for q in range(2)]
     yv = [[Yd[q][p["x"].dtype][yoff[j]:yoff[j] + p["A"].m] for j, p in enumerate(prods)] for q in range(2)]
-    h2d = sum(b.numel() * b.element_size() for b in xh_pack.values())
-    d2h = sum(b.numel() * b.element_size() for b in yh_pack[0].values())
     mats = [p["M"] for p in prods]
     s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     run_done = [torch.cuda.Event(), torch.cuda.Event()]
@@ -653,29 +652,40 @@ def run_products(args, ctx):
             if not err <= 1e-12 * max(ref.abs().max().item() if p["A"].m else 0.0, 1e-300):
                 raise RuntimeError(f"end-to-end product of {p['A'].name} {p['dt']} differs from the timed one ({err:g})")
 
-    # Every step synchronised (reported beside it): smat_spmv_host_async per
-    # product from its own pinned x and y, the library's host-buffer call
-    # (copy in, product, copy out on the handle's staging buffers), a stream
-    # per product, issued in e2e_issue_order's order.
+    # Through the C ABI with host buffers (the figure reported as e2e):
+    # smat_spmv_host_async per product from its own pinned x and y (copy in,
+    # product, copy out on the handle's staging buffers), each product's calls
+    # on a stream of its own so that no product's copy in waits behind
+    # another's copy out and the transfers of one product overlap the kernels
+    # of the others; issued in e2e_issue_order's order.  Steps are pipelined
+    # (the next step's copies in do not wait for this step's copies out; each
+    # product's stream keeps its own staging buffers in order) and the timed
+    # region ends when every stream is done; the same steps synchronised one
+    # by one are reported beside it.
     pinned = []
     for p in prods:
         pinned.append((p["x"].cpu().pin_memory(), torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory()))
+    h2d = sum(xh.numel() * xh.element_size() for xh, _ in pinned)
+    d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
     order = e2e_issue_order([p["pick_ms"] for p in prods])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
     for p, (xh, yh) in zip(prods, pinned):
         p["M"].spmv_host(xh, yh)
 
-    def e2e_synced():
-        for j in order:
-            xh, yh = pinned[j]
-            prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
-        for st in streams:
-            st.synchronize()
+    def e2e_host(sync):
+        def f():
+            for j in order:
+                xh, yh = pinned[j]
+                prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
+            if sync:
+                for st in streams:
+                    st.synchronize()
+        return f
 
-    e2e_synced()
+    e2e_host(True)()
     E = max(2, args.e2e_steps)
     e2e_rates = {}
-    for mode, fn in (("pipelined", e2e_pipelined), ("synced", e2e_synced)):
+    for mode, fn in (("pipelined", e2e_host(False)), ("synced", e2e_host(True)), ("packed", e2e_pipelined)):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -721,14 +731,17 @@ def run_products(args, ctx):
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": E,
-                    "how": "each storage type's x of all products copied from one pinned host buffer as one "
-                           "transfer, the products side by side (smat_spmv_many), the y copied back as one "
-                           "transfer per storage type; two sets of device buffers alternate between steps; "
-                           "copies in, products and copies out on three streams ordered by events, steps "
-                           "pipelined and synced at the end",
+                    "how": "smat_spmv_host_async (the C ABI's host-buffer call) per product from pinned host "
+                           "x/y, a stream per product, issued shortest first with the two longest at the second "
+                           "and middle places; steps pipelined (all streams synced at the end of the timed region)",
                     "synced_per_step": round(e2e_rates["synced"], 3),
-                    "synced_how": "smat_spmv_host_async per product from its own pinned x/y (the library's "
-                                  "host-buffer call), a stream per product, every step synchronised"},
+                    "packed_device_api": {
+                        "value": round(e2e_rates["packed"], 3),
+                        "how": "the device-pointer calls with the transfers arranged by the caller: each storage "
+                               "type's x of all products copied from one pinned host buffer as one transfer, the "
+                               "products side by side (smat_spmv_many), the y copied back as one transfer per "
+                               "storage type; two sets of device buffers alternate between steps; copies in, "
+                               "products and copies out on three streams; same bytes per step"}},
             "cpu_baseline": cpu,
             "per_matrix": per,
         }
