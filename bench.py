@@ -653,39 +653,47 @@ def run_products(args, ctx):
                 raise RuntimeError(f"end-to-end product of {p['A'].name} {p['dt']} differs from the timed one ({err:g})")
 
     # Through the C ABI with host buffers (the figure reported as e2e):
-    # smat_spmv_host_async per product from its own pinned x and y (copy in,
-    # product, copy out on the handle's staging buffers), each product's calls
-    # on a stream of its own so that no product's copy in waits behind
-    # another's copy out and the transfers of one product overlap the kernels
-    # of the others; issued in e2e_issue_order's order.  Steps are pipelined
-    # (the next step's copies in do not wait for this step's copies out; each
-    # product's stream keeps its own staging buffers in order) and the timed
-    # region ends when every stream is done; the same steps synchronised one
-    # by one are reported beside it.
+    # smat_spmv_host_pipelined per product from its own pinned x and y: each
+    # handle copies in, computes and copies out on streams of its own with two
+    # staging sets used in turn, so one step's transfers overlap the previous
+    # step's products and the products of different handles overlap each
+    # other; the current stream waits for every copy out, and the timed region
+    # ends when it is done (all y on the host).  Issued in e2e_issue_order's
+    # order; two pinned y buffers per product alternate between steps, so two
+    # steps in flight never write the same host buffer.  Reported beside it:
+    # smat_spmv_host_async per product on a stream of its own (the handle's
+    # single staging set), every step synchronised.
     pinned = []
     for p in prods:
-        pinned.append((p["x"].cpu().pin_memory(), torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory()))
+        pinned.append((p["x"].cpu().pin_memory(),
+                       [torch.zeros(p["A"].m, dtype=p["x"].dtype).pin_memory() for _ in range(2)]))
     h2d = sum(xh.numel() * xh.element_size() for xh, _ in pinned)
-    d2h = sum(yh.numel() * yh.element_size() for _, yh in pinned)
+    d2h = sum(yh[0].numel() * yh[0].element_size() for _, yh in pinned)
     order = e2e_issue_order([p["pick_ms"] for p in prods])
     streams = [torch.cuda.Stream() for _ in range(len(prods))]
-    for p, (xh, yh) in zip(prods, pinned):
-        p["M"].spmv_host(xh, yh)
+    n_host = [0]
 
-    def e2e_host(sync):
-        def f():
-            for j in order:
-                xh, yh = pinned[j]
-                prods[j]["M"].spmv_host_async(xh, yh, stream=streams[j])
-            if sync:
-                for st in streams:
-                    st.synchronize()
-        return f
+    def e2e_host_pipelined():
+        q = n_host[0] % 2
+        n_host[0] += 1
+        for j in order:
+            xh, yh = pinned[j]
+            prods[j]["M"].spmv_host_pipelined(xh, yh[q])
 
-    e2e_host(True)()
+    def e2e_host_synced():
+        for j in order:
+            xh, yh = pinned[j]
+            prods[j]["M"].spmv_host_async(xh, yh[0], stream=streams[j])
+        for st in streams:
+            st.synchronize()
+
+    e2e_host_pipelined()
+    e2e_host_pipelined()
+    e2e_host_synced()
+    torch.cuda.synchronize()
     E = max(2, args.e2e_steps)
     e2e_rates = {}
-    for mode, fn in (("pipelined", e2e_host(False)), ("synced", e2e_host(True)), ("packed", e2e_pipelined)):
+    for mode, fn in (("pipelined", e2e_host_pipelined), ("synced", e2e_host_synced), ("packed", e2e_pipelined)):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -731,10 +739,12 @@ def run_products(args, ctx):
             "clocks": ck,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": E,
-                    "how": "smat_spmv_host_async (the C ABI's host-buffer call) per product from pinned host "
-                           "x/y, a stream per product, issued shortest first with the two longest at the second "
-                           "and middle places; steps pipelined (all streams synced at the end of the timed region)",
+                    "how": "smat_spmv_host_pipelined (the C ABI's host-buffer call on the handle's own streams "
+                           "and two staging sets) per product from pinned host x/y, issued shortest first with the "
+                           "two longest at the second and middle places; steps pipelined, the current stream "
+                           "waiting for every copy out, synced at the end of the timed region",
                     "synced_per_step": round(e2e_rates["synced"], 3),
+                    "synced_how": "smat_spmv_host_async per product on a stream of its own, every step synchronised",
                     "packed_device_api": {
                         "value": round(e2e_rates["packed"], 3),
                         "how": "the device-pointer calls with the transfers arranged by the caller: each storage "

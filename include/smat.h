@@ -293,6 +293,25 @@ smat_status_t smat_spmv_launches(smat_handle_t h, smat_variant_t v, int32_t *lau
 smat_status_t smat_spmv_host_async(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
                                    void *y_host, void *stream);
 
+/* Host-buffer products in a pipeline.  The same product as
+ * smat_spmv_host_async, but the handle keeps two staging sets, used by
+ * consecutive calls in turn, and copies and computes on three streams of its
+ * own: a call's copy in waits only until the product two calls back has read
+ * its staging set, so one call's transfers overlap the previous call's
+ * product (and, across handles, other handles' products).  Ordering:
+ *  - x_host (and y_host when beta != 0) is read by a copy that is NOT ordered
+ *    after earlier work on `stream`: it must hold its values when the call is
+ *    made, and stay unchanged until `stream` has finished;
+ *  - y_host is written by a copy that `stream` waits for: it is valid once
+ *    `stream` has finished (e.g. cudaStreamSynchronize);
+ *  - calls on one handle must not overlap on the host.
+ * x_host and y_host should be pinned.  Returns SMAT_ERR_UNSUPPORTED when
+ * `stream` is capturing a graph (the copies do not run on it), or when the
+ * plan is not built.  The staging sets and streams are freed by smat_destroy,
+ * which waits for them first. */
+smat_status_t smat_spmv_host_pipelined(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
+                                       void *y_host, void *stream);
+
 /* Feature parameters (computes them on `stream` = NULL if not yet done). */
 smat_status_t smat_get_features(smat_handle_t h, smat_features_t *out);
 

@@ -103,6 +103,7 @@ _SIGS = {
     "smat_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _I32]),
     "smat_get_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_spmv_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_spmv_host_pipelined": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_launches": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
@@ -217,6 +218,10 @@ def smat_spmv_host(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
 
 def smat_spmv_host_async(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
     return lib().smat_spmv_host_async(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
+
+
+def smat_spmv_host_pipelined(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream=0):
+    return lib().smat_spmv_host_pipelined(h, alpha_ptr, x_ptr, beta_ptr, y_ptr, stream)
 
 
 def smat_spmv_launches(h, v) -> int:
@@ -615,6 +620,15 @@ class SpMatrix:
         a, b = self._scalars(alpha, beta)
         _check(smat_spmv_host_async(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
                                     _stream_ptr(stream)), "smat_spmv_host_async")
+        return y
+
+    def spmv_host_pipelined(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        """The host-buffer product on the handle's own streams and alternating
+        staging sets (smat_spmv_host_pipelined); y is valid once `stream` has
+        finished.  x (and y when beta != 0) must hold their values now."""
+        a, b = self._scalars(alpha, beta)
+        _check(smat_spmv_host_pipelined(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
+                                        _stream_ptr(stream)), "smat_spmv_host_pipelined")
         return y
 
     def features(self) -> dict:

@@ -1112,7 +1112,16 @@ smat_status_t smat_destroy(smat_handle_t h) {
   free_format(h, SMAT_FMT_ELL); free_format(h, SMAT_FMT_DIA); free_format(h, SMAT_FMT_COO);
   free_ext_layouts(h);
   dev_free(h->carry); dev_free(h->stage_x); dev_free(h->stage_y); dev_free(h->merge_coords);
+  if (h->pst[0]) {
+    for (cudaStream_t st : h->pst) cudaStreamSynchronize(st);
+    for (int q = 0; q < 2; ++q) {
+      cudaEventDestroy(h->pev_x[q]); cudaEventDestroy(h->pev_run[q]); cudaEventDestroy(h->pev_out[q]);
+      dev_free(h->pstage_x[q]); dev_free(h->pstage_y[q]);
+    }
+  }
   free_stream_scratch(h);
+  if (h->pst[0])
+    for (cudaStream_t st : h->pst) cudaStreamDestroy(st);
   delete h;
   return SMAT_OK;
 }
@@ -1374,6 +1383,63 @@ smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_h
   TRY(launch_spmv(h, h->variant, alpha, h->stage_x, beta, h->stage_y, s));
   if (h->m > 0) TRY(cudaMemcpyAsync(y_host, h->stage_y, (size_t)h->m * ts, cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
+  return SMAT_OK;
+}
+
+// Host-buffer products in a pipeline: the handle keeps two staging sets and
+// three streams of its own.  Call k uses set k % 2: its copy in waits only
+// for the product of call k - 2 (which read that set's x), its product for
+// its copy in and for the copy out of call k - 2 (which read that set's y),
+// its copy out for its product; the caller's stream waits for the copy out.
+// So consecutive calls overlap one call's transfers with another's product,
+// and products of different handles overlap each other.
+smat_status_t smat_spmv_host_pipelined(smat_handle_t h, const void *alpha, const void *x_host, const void *beta,
+                                       void *y_host, void *stream) {
+  TRYS(check_handle(h));
+  if (!alpha || !beta || (h->m > 0 && !y_host) || (h->n > 0 && !x_host)) return SMAT_ERR_INVALID_ARG;
+  if (!variant_ready(h, h->variant)) return SMAT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return SMAT_ERR_UNSUPPORTED;  // its streams are not the caller's
+  if (!h->pst[0]) {
+    cudaStream_t st[3] = {};
+    cudaEvent_t ev[6] = {};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (cudaStream_t x : st) if (x) cudaStreamDestroy(x);
+      for (cudaEvent_t x : ev) if (x) cudaEventDestroy(x);
+      return st_of(e);
+    }
+    for (int k = 0; k < 3; ++k) h->pst[k] = st[k];
+    for (int q = 0; q < 2; ++q) { h->pev_x[q] = ev[q]; h->pev_run[q] = ev[2 + q]; h->pev_out[q] = ev[4 + q]; }
+  }
+  const int q = (int)(h->pcalls & 1);
+  const size_t ts = (size_t)tsize(h);
+  if (!h->pstage_x[q] && h->n > 0) TRY(dev_alloc(&h->pstage_x[q], (size_t)h->n * ts));
+  if (!h->pstage_y[q] && h->m > 0) TRY(dev_alloc(&h->pstage_y[q], (size_t)h->m * ts));
+  const bool beta_zero = h->dtype == SMAT_F64 ? *(const double *)beta == 0.0 : *(const float *)beta == 0.0f;
+  cudaStream_t in = h->pst[0], run = h->pst[1], out = h->pst[2];
+  if (h->pused[q]) {
+    TRY(cudaStreamWaitEvent(in, h->pev_run[q], 0));
+    if (!beta_zero) TRY(cudaStreamWaitEvent(in, h->pev_out[q], 0));
+  }
+  if (h->n > 0) TRY(cudaMemcpyAsync(h->pstage_x[q], x_host, (size_t)h->n * ts, cudaMemcpyHostToDevice, in));
+  if (!beta_zero && h->m > 0)
+    TRY(cudaMemcpyAsync(h->pstage_y[q], y_host, (size_t)h->m * ts, cudaMemcpyHostToDevice, in));
+  TRY(cudaEventRecord(h->pev_x[q], in));
+  TRY(cudaStreamWaitEvent(run, h->pev_x[q], 0));
+  if (h->pused[q]) TRY(cudaStreamWaitEvent(run, h->pev_out[q], 0));
+  TRY(launch_spmv(h, h->variant, alpha, h->pstage_x[q], beta, h->pstage_y[q], run));
+  TRY(cudaEventRecord(h->pev_run[q], run));
+  TRY(cudaStreamWaitEvent(out, h->pev_run[q], 0));
+  if (h->m > 0) TRY(cudaMemcpyAsync(y_host, h->pstage_y[q], (size_t)h->m * ts, cudaMemcpyDeviceToHost, out));
+  TRY(cudaEventRecord(h->pev_out[q], out));
+  TRY(cudaStreamWaitEvent(s, h->pev_out[q], 0));
+  h->pused[q] = true;
+  ++h->pcalls;
   return SMAT_OK;
 }
 

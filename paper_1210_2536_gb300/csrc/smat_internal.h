@@ -145,6 +145,14 @@ struct smat_s {
 
   // host-buffer staging for smat_spmv_host
   void *stage_x = nullptr, *stage_y = nullptr;
+  // smat_spmv_host_pipelined: two staging sets used in turn, the handle's own
+  // copy-in, compute and copy-out streams, and per set the events that order
+  // a set's next use after its previous one
+  void *pstage_x[2] = {}, *pstage_y[2] = {};
+  cudaStream_t pst[3] = {};
+  cudaEvent_t pev_x[2] = {}, pev_run[2] = {}, pev_out[2] = {};
+  bool pused[2] = {};
+  long long pcalls = 0;
 
   // plan
   int32_t variant = SMAT_V_CSR_SCALAR;
