@@ -9,6 +9,10 @@
  * the product go to the file named by argv[1] for a row-by-row check.
  * Part 3: device CSR with a row whose columns are not increasing must be
  * refused with SMAT_ERR_INVALID_CSR.
+ * Part 4: on the part-1 handle, three smat_spmv_host_pipelined calls with
+ * different pinned x (the handle's two staging sets in turn, y = A*x and
+ * y = 0.5*A*x - y), then one synchronisation of the default stream; each y
+ * must equal the synchronous smat_spmv_host result bit for bit.
  * Exit code = first failing status (0 = ok). */
 #include <stdio.h>
 #include <stdlib.h>
@@ -121,6 +125,31 @@ static int part3(void) {
   return st == SMAT_ERR_INVALID_CSR && !h ? 0 : 104;
 }
 
+static int part4(smat_handle_t h, int m) {
+  double *xs = NULL, *ys = NULL;
+  if (cudaMallocHost((void **)&xs, sizeof(double) * 3 * (size_t)m) != cudaSuccess) return 105;
+  if (cudaMallocHost((void **)&ys, sizeof(double) * 3 * (size_t)m) != cudaSuccess) return 105;
+  double *ref = malloc(sizeof(double) * (size_t)m);
+  const double alphas[3] = {1.0, 0.5, -2.0}, betas[3] = {0.0, -1.0, 0.0};
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < m; ++i) {
+      xs[(size_t)c * m + i] = (double)((i * (c + 3)) % 11) - 5.0 + 0.25 * c;
+      ys[(size_t)c * m + i] = (double)(i % 3);
+    }
+  for (int c = 0; c < 3; ++c)
+    CHECK(smat_spmv_host_pipelined(h, &alphas[c], xs + (size_t)c * m, &betas[c], ys + (size_t)c * m, NULL));
+  CUDA_CHECK(cudaStreamSynchronize(NULL));
+  int bad = 0;
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < m; ++i) ref[i] = (double)(i % 3);
+    CHECK(smat_spmv_host(h, &alphas[c], xs + (size_t)c * m, &betas[c], ref, NULL));
+    for (int i = 0; i < m; ++i) bad += ref[i] != ys[(size_t)c * m + i];
+  }
+  printf("part4 mismatches %d\n", bad);
+  cudaFreeHost(xs); cudaFreeHost(ys); free(ref);
+  return bad ? 106 : 0;
+}
+
 int main(int argc, char **argv) {
   const int g = 32, m = g * g;
   int32_t *rowptr = malloc(sizeof(int32_t) * (m + 1));
@@ -156,6 +185,8 @@ int main(int argc, char **argv) {
   CHECK(smat_spmv_host(h, &alpha, x, &beta, y, NULL));
   printf("nnz %lld ndiags %lld variant %d\n", (long long)f.nnz, (long long)f.ndiags, variant);
   printf("y %.17g %.17g %.17g %.17g\n", y[0], y[1], y[g], y[m - 1]);
+  const int r4 = argc > 1 ? part4(h, m) : 0;
+  if (r4) return r4;
   CHECK(smat_destroy(h));
   free(rowptr); free(col); free(val); free(x); free(y);
   if (argc > 1) {

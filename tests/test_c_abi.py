@@ -45,6 +45,10 @@ def test_c_program_matches_oracle(tmp_path):
     assert r.returncode == 0, (r.returncode, r.stderr, r.stdout)
     lines = r.stdout.split("\n")
     assert lines[0].startswith("nnz 4992 ndiags 5")
+    # part 4 (printed right after part 1's y): pipelined host-buffer calls
+    # equal the synchronous host-buffer call bit for bit
+    assert lines[2] == "part4 mismatches 0"
+    del lines[2]
     got = np.array([float(t) for t in lines[1].split()[1:]])
     A = synth.stencil2d5(32)
     x = (np.arange(A.n) % 7) - 3.0
