@@ -114,3 +114,32 @@ def test_refused_while_capturing_and_argument_errors():
     ref = M.spmv(torch.from_numpy(x.numpy()).to(DEV)).cpu().numpy()
     assert np.allclose(y.numpy(), ref, rtol=1e-12, atol=0)
     M.close()
+
+
+@pytest.mark.parametrize("shape", [(3, 0), (0, 5), (50, 40)], ids=["no_columns", "no_rows", "all_rows_empty"])
+def test_degenerate_matrices_pipelined_and_side_by_side(shape):
+    # nnz = 0: y = beta*y through the pipelined host call and through
+    # smat_spmv_many beside a regular product
+    m, n = shape
+    A = synth.CSR(m, n, np.zeros(m + 1, np.int32), np.zeros(0, np.int32), np.zeros(0), name=f"empty_{m}x{n}")
+    M, _ = _handle(A, "f64")
+    x = _pinned(np.ones(n))
+    ys_h = [_pinned(np.full(m, 3.0 + k)) for k in range(3)]
+    s = torch.cuda.Stream()
+    for y in ys_h:                        # both staging sets, then the first again
+        M.spmv_host_pipelined(x, y, 1.0, 0.5, stream=s)
+    s.synchronize()
+    for k, y in enumerate(ys_h):
+        assert np.array_equal(y.numpy(), np.full(m, 0.5 * (3.0 + k)))
+    B = synth.stencil2d5(16)
+    MB, vB = _handle(B, "f64")
+    xb = synth.uniform(4, 1, B.n)
+    xs = [torch.ones(n, dtype=torch.float64, device=DEV), torch.from_numpy(xb).to(DEV)]
+    ys = [torch.full((m,), 2.0, dtype=torch.float64, device=DEV), torch.zeros(B.m, dtype=torch.float64, device=DEV)]
+    smat.spmv_many([M, MB], xs, ys, [1.0, 1.0], [-1.0, 0.0])
+    torch.cuda.synchronize()
+    assert torch.equal(ys[0].cpu(), torch.full((m,), -2.0, dtype=torch.float64))
+    ref, scale = reference(B, vB, xb, 1.0, 0.0, None)
+    assert_close_rows(ys[1].cpu().numpy(), ref, scale, TOL["f64"], "regular beside an empty one")
+    M.close()
+    MB.close()
