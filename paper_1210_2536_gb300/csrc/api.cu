@@ -1093,11 +1093,13 @@ smat_status_t smat_create(smat_handle_t *out, int64_t m, int64_t n, int64_t nnz,
     if ((e = cudaMemcpy(h->val, vals, (size_t)nnz * h->esz, cudaMemcpyDefault)) != cudaSuccess) return fail(st_of(e));
   }
   // K1: structural validation on the device, reported through a flag.
+  // One block: the flag, then one bit per stored entry for the row starts.
   void *flag = nullptr;
-  if ((e = dev_alloc(&flag, sizeof(int))) != cudaSuccess) return fail(st_of(e));
+  const size_t vbytes = 16 + validate_starts_words(nnz) * 4;
+  if ((e = dev_alloc(&flag, vbytes)) != cudaSuccess) return fail(st_of(e));
   int hf = 0;
-  e = cudaMemset(flag, 0, sizeof(int));
-  if (e == cudaSuccess) e = launch_validate(h, (int *)flag, 0);
+  e = cudaMemset(flag, 0, vbytes);
+  if (e == cudaSuccess) e = launch_validate(h, (int *)flag, (unsigned *)((char *)flag + 16), 0);
   if (e == cudaSuccess) e = cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost);
   dev_free(flag);
   if (e != cudaSuccess) return fail(st_of(e));

@@ -8,6 +8,7 @@
 //                 every diagonal d = j - i                  (one read of colidx)
 //   diag_reduce : Ndiags, number of "true" diagonals and the occupied offsets
 // The floating-point features are finished on the host from these integers.
+#include <algorithm>
 #include <climits>
 
 #include "smat_internal.h"
@@ -45,40 +46,61 @@ __device__ __forceinline__ int row_lane_of(int start_of_my_row, long long k) {
 }
 
 // ---------------------------------------------------------------------------
-// K1: validation.  A warp checks 32 consecutive rows; every index it reads is
-// clamped into the arrays, so malformed input cannot send it out of bounds.
+// K1: validation, in two balanced passes.  Per row: the row pointer must not
+// fall, and the row's first entry is marked in a bitmap over the stored
+// entries.  Per entry (4 per thread, one 16-byte load): the column must lie
+// in [0, n), and must be below the next entry's unless a row starts there.
+// Work is spread by rows and by entries, so a few very long rows do not hold
+// one warp while the others idle.  Every index read is clamped into the
+// arrays, so malformed input cannot send either pass out of bounds.
 // ---------------------------------------------------------------------------
-__global__ void validate_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                long long m, long long n, long long nnz, int *flag) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+__global__ void validate_rows_kernel(const int32_t *__restrict__ rowptr, long long m, long long nnz,
+                                     unsigned *__restrict__ starts, int *flag) {
   int err = 0;
-  if (warp == 0 && lane == 0) {
-    if (rowptr[0] != 0 || (long long)rowptr[m] != nnz) err |= ERRF_ROWPTR;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (rowptr[0] != 0 || (long long)rowptr[m] != nnz)) err |= ERRF_ROWPTR;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long s = rowptr[r], e = rowptr[r + 1];
+    if (e < s) err |= ERRF_ROWPTR;
+    if (s >= 0 && s < nnz) atomicOr(&starts[s >> 5], 1u << (s & 31));
   }
-  for (long long r0 = warp * 32; r0 < m; r0 += nwarps * 32) {
-    long long r = r0 + lane;
-    long long s = 0, e = 0;
-    if (r < m) {
-      s = rowptr[r];
-      e = rowptr[r + 1];
-      if (e < s) err |= ERRF_ROWPTR;
+  err = __reduce_or_sync(FULL, err);
+  if ((threadIdx.x & 31) == 0 && err) atomicOr(flag, err);
+}
+
+__global__ void validate_cols_kernel(const int32_t *__restrict__ col, long long nnz, long long n,
+                                     const unsigned *__restrict__ starts, int *flag) {
+  int err = 0;
+  const long long chunks = (nnz + 3) / 4;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < chunks;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long k0 = 4 * t;
+    int c[5];
+    if (k0 + 4 <= nnz) {
+      const int4 v = __ldcs(reinterpret_cast<const int4 *>(col) + t);
+      c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) c[i] = k0 + i < nnz ? col[k0 + i] : 0;
     }
-    s = s < 0 ? 0 : (s > nnz ? nnz : s);
-    e = e < s ? s : (e > nnz ? nnz : e);
-    int rows = (int)min(32LL, m - r0);
-    for (int q = 0; q < rows; ++q) {
-      long long qs = __shfl_sync(FULL, s, q), qe = __shfl_sync(FULL, e, q);
-      for (long long k = qs + lane; k < qe; k += 32) {
-        int c = col[k];
-        if (c < 0 || (long long)c >= n) err |= ERRF_COL_RANGE;
-        if (k + 1 < qe && col[k + 1] <= c) err |= ERRF_COL_ORDER;
+    c[4] = k0 + 4 < nnz ? __ldg(col + k0 + 4) : 0;
+    // entries k0 + 1 .. k0 + 4 sit in word k0 >> 5, or k0 + 4 in the next one
+    const unsigned w0 = starts[k0 >> 5];
+    const unsigned w1 = ((k0 + 4) & 31) == 0 ? starts[(k0 + 4) >> 5] : w0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long k = k0 + i;
+      if (k >= nnz) break;
+      if (c[i] < 0 || (long long)c[i] >= n) err |= ERRF_COL_RANGE;
+      const long long k1 = k + 1;
+      if (k1 < nnz) {
+        const unsigned w = (k1 >> 5) == (k0 >> 5) ? w0 : w1;
+        if (!((w >> (k1 & 31)) & 1u) && c[i + 1] <= c[i]) err |= ERRF_COL_ORDER;
       }
     }
   }
   err = __reduce_or_sync(FULL, err);
-  if (lane == 0 && err) atomicOr(flag, err);
+  if ((threadIdx.x & 31) == 0 && err) atomicOr(flag, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +158,10 @@ constexpr int HT_PROBES = 8;
 constexpr int HIST_SH = 1024;      // privatised histogram bins
 constexpr int EMPTY_KEY = INT_MIN;
 
-__device__ __forceinline__ void ht_add(int *keys, int *cnts, int *g_cnt, long long m, int d, int c) {
+// Adds c to diagonal d's count in the CTA's table; when its probes find no
+// slot, to the global count, and marks the table full so that the CTA's
+// later entries go to the global counts directly (random-column matrices).
+__device__ __forceinline__ void ht_add(int *keys, int *cnts, int *g_cnt, long long m, int d, int c, int *full) {
   unsigned h = ((unsigned)d * 2654435761u) >> (32 - 11);
 #pragma unroll 1
   for (int p = 0; p < HT_PROBES; ++p) {
@@ -147,6 +172,7 @@ __device__ __forceinline__ void ht_add(int *keys, int *cnts, int *g_cnt, long lo
     }
     h = (h + 1) & (HT - 1);
   }
+  *full = 1;
   atomicAdd(&g_cnt[(long long)d + m - 1], c);
 }
 
@@ -154,6 +180,8 @@ __global__ void __launch_bounds__(256) hist_diag_kernel(const int32_t *__restric
                                                         const int32_t *__restrict__ col, long long m,
                                                         int *hist, long long hist_len, int *g_cnt) {
   __shared__ int keys[HT], cnts[HT], sh_hist[HIST_SH];
+  __shared__ int ht_full;
+  if (threadIdx.x == 0) ht_full = 0;
   for (int t = threadIdx.x; t < HT; t += blockDim.x) { keys[t] = EMPTY_KEY; cnts[t] = 0; }
   for (int t = threadIdx.x; t < HIST_SH; t += blockDim.x) sh_hist[t] = 0;
   __syncthreads();
@@ -183,11 +211,17 @@ __global__ void __launch_bounds__(256) hist_diag_kernel(const int32_t *__restric
       long long k = base + lane;
       bool active = k < ge;
       int L = row_lane_of(s, k);
+      // one decision for the whole warp (lane 0's view of the flag)
+      const int full = __shfl_sync(FULL, *(volatile int *)&ht_full, 0);
+      if (full) {
+        if (active) atomicAdd(&g_cnt[(long long)(col[k] - (int)(r0 + L)) + m - 1], 1);
+        continue;
+      }
       unsigned act = __ballot_sync(FULL, active);
       if (active) {
         int d = col[k] - (int)(r0 + L);
         unsigned peers = __match_any_sync(act, d);
-        if (lane == __ffs(peers) - 1) ht_add(keys, cnts, g_cnt, m, d, __popc(peers));
+        if (lane == __ffs(peers) - 1) ht_add(keys, cnts, g_cnt, m, d, __popc(peers), &ht_full);
       }
     }
   }
@@ -200,23 +234,45 @@ __global__ void __launch_bounds__(256) hist_diag_kernel(const int32_t *__restric
 
 // ---------------------------------------------------------------------------
 // K3b: occupied / "true" diagonals, plus the occupied offsets (unordered; the
-// host sorts them) up to `cap` of them.  counts = {Ndiags, Ntrue, appended}.
+// host sorts them) up to `cap` of them.  counts = {Ndiags, Ntrue, appended};
+// "appended" is exact while it stays at most cap, and otherwise only ends
+// above cap.
 // ---------------------------------------------------------------------------
 __global__ void diag_reduce_kernel(const int *__restrict__ cnt, long long m, long long n, int tau_num,
                                    int tau_den, unsigned long long *counts, int32_t *offsets,
                                    long long cap) {
   long long nd = m + n - 1;
   unsigned long long occ = 0, tru = 0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nd;
-       t += (long long)gridDim.x * blockDim.x) {
-    int c = cnt[t];
+  const int lane = threadIdx.x & 31;
+  // the trip count is the same for the whole warp, so the ballot below sees
+  // every lane: one append per warp and pass instead of one per diagonal
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nd; base += (long long)gridDim.x * blockDim.x) {
+    const long long t = base + threadIdx.x;
+    const int c = t < nd ? cnt[t] : 0;
+    const long long d = t - (m - 1);
     if (c > 0) {
-      long long d = t - (m - 1);
       long long len = d >= 0 ? min(m, n - d) : min(m + d, n);
       ++occ;
       if ((long long)tau_den * c > (long long)tau_num * len) ++tru;
-      unsigned long long idx = atomicAdd(&counts[2], 1ull);
-      if ((long long)idx < cap) offsets[idx] = (int32_t)d;
+    }
+    const unsigned b = __ballot_sync(FULL, c > 0);
+    if (b) {
+      // once the count seen is above cap the host drops the offsets anyway
+      // (it keeps them only when the final count is at most cap), so later
+      // warps stop appending; the count still ends above cap
+      const int leader = __ffs(b) - 1;
+      unsigned long long idx0 = 0;
+      int skip = 0;
+      if (lane == leader) {
+        if (*(volatile unsigned long long *)&counts[2] > (unsigned long long)cap) skip = 1;
+        else idx0 = atomicAdd(&counts[2], (unsigned long long)__popc(b));
+      }
+      skip = __shfl_sync(FULL, skip, leader);
+      idx0 = __shfl_sync(FULL, idx0, leader);
+      if (!skip && c > 0) {
+        const unsigned long long idx = idx0 + __popc(b & ((1u << lane) - 1u));
+        if ((long long)idx < cap) offsets[idx] = (int32_t)d;
+      }
     }
   }
   occ = warp_sum(occ);
@@ -236,9 +292,15 @@ int grid_for(long long work, int block, int max_blocks) {
 
 }  // namespace
 
-cudaError_t launch_validate(const smat_s *h, int *d_flag, cudaStream_t s) {
-  int g = grid_for((h->m + 31) / 32 * 32, 256, 152 * 16);
-  validate_kernel<<<g, 256, 0, s>>>(h->rowptr, h->colidx, h->m, h->n, h->nnz, d_flag);
+size_t validate_starts_words(int64_t nnz) { return (size_t)(nnz / 32 + 2); }
+
+cudaError_t launch_validate(const smat_s *h, int *d_flag, unsigned *d_starts, cudaStream_t s) {
+  validate_rows_kernel<<<grid_for(std::max<int64_t>(h->m, 1), 256, 152 * 16), 256, 0, s>>>(h->rowptr, h->m, h->nnz,
+                                                                                          d_starts, d_flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || h->nnz == 0) return e;
+  validate_cols_kernel<<<grid_for((h->nnz + 3) / 4, 256, 152 * 16), 256, 0, s>>>(h->colidx, h->nnz, h->n, d_starts,
+                                                                               d_flag);
   return cudaGetLastError();
 }
 

@@ -165,7 +165,10 @@ struct smat_s {
 namespace smat {
 
 // ---- launchers (return cudaError_t of the launch) ----
-cudaError_t launch_validate(const smat_s *h, int *d_flag, cudaStream_t s);
+// Validation writes its error flags to d_flag and uses d_starts, zeroed
+// words of one bit per stored entry (validate_starts_words of them).
+size_t validate_starts_words(int64_t nnz);
+cudaError_t launch_validate(const smat_s *h, int *d_flag, unsigned *d_starts, cudaStream_t s);
 cudaError_t launch_row_stats(const int32_t *rowptr, int64_t m, RowStats *d_stats, cudaStream_t s);
 cudaError_t launch_hist_diag(const int32_t *rowptr, const int32_t *colidx, int64_t m,
                              int *d_hist, int64_t hist_len, int *d_diag_cnt, cudaStream_t s);
