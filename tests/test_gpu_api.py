@@ -262,3 +262,50 @@ def test_trial_racing_keeps_the_pick_and_saves_time():
     assert np.array_equal(raced > 0, ran)
     assert raced[pick_raced] <= 1.02 * raced[ran].min()
     M.close()
+
+
+def _random_rows(m, n, lens, seed):
+    rng = np.random.default_rng(seed)
+    rp = np.zeros(m + 1, np.int32)
+    rp[1:] = np.cumsum(lens)
+    ci = np.concatenate([np.sort(rng.choice(n, size=int(k), replace=False)) for k in lens]).astype(np.int32)
+    return rp, ci
+
+
+def test_validation_at_chunk_and_word_boundaries():
+    # validation reads the columns 4 at a time and marks row starts in a
+    # bitmap of 32-entry words: an order violation placed exactly at those
+    # boundaries (and inside a long row, and at the last entries) is caught,
+    # and rows starting at them, whose first column is below the previous
+    # row's last, are accepted
+    m, n = 3000, 5000
+    rng = np.random.default_rng(21)
+    lens = rng.integers(0, 12, size=m)
+    lens[1500] = 2500                      # one long row
+    rp, ci = _random_rows(m, n, lens, 22)
+    nnz = len(ci)
+    st, h = _create(m, n, rp, ci, np.ones(nnz))
+    assert st == smat.SMAT_OK
+    smat.smat_destroy(h)
+    row_of = np.repeat(np.arange(m), np.diff(rp))
+    picks = [3, 4, 7, 31, 32, 63, 64, 127, 128, int(rp[1500]) + 1000, int(rp[1500]) + 2047, nnz - 2]
+    tried = 0
+    for k0 in picks:
+        # the nearest k >= k0 whose next entry is in the same row
+        k = next((j for j in range(k0, nnz - 1) if row_of[j] == row_of[j + 1]), None)
+        if k is None:
+            continue
+        bad = ci.copy()
+        bad[k], bad[k + 1] = bad[k + 1], bad[k]
+        st, h = _create(m, n, rp, bad, np.ones(nnz))
+        assert st == smat.SMAT_ERR_INVALID_CSR and not h, (k0, k)
+        tried += 1
+    assert tried >= len(picks) - 1
+    # rows that start on word boundaries with a smaller first column
+    lens2 = np.full(64, 32, np.int64)
+    rp2 = np.zeros(65, np.int32)
+    rp2[1:] = np.cumsum(lens2)
+    ci2 = np.concatenate([np.arange(2600 - 40 * r, 2632 - 40 * r) for r in range(64)]).astype(np.int32)
+    st, h = _create(64, 5000, rp2, ci2, np.ones(len(ci2)))
+    assert st == smat.SMAT_OK
+    smat.smat_destroy(h)
