@@ -519,6 +519,20 @@ __global__ void __launch_bounds__(NT, SMAT_COO_MINB) coo_kernel(const int32_t *_
 #define SMAT_COO_CH 1
 #endif
 constexpr int COO_NT = SMAT_COO_NT, COO_CH = SMAT_COO_CH, COO_IPT = 8 * SMAT_COO_CH;
+// SPLIT's short rows in tiles of one warp (32 threads x 8 entries) whose
+// carries are resolved with shuffles alone, or (0) in the COO kernel's
+// 256-thread tiles with a block-wide carry scan.
+#ifndef SMAT_SPLIT_WARP_TILES
+#define SMAT_SPLIT_WARP_TILES 1
+#endif
+constexpr bool SPLIT_WARP_TILES = SMAT_SPLIT_WARP_TILES != 0;
+constexpr long long SPLIT_TILE = SPLIT_WARP_TILES ? 32LL * 8 : (long long)COO_NT * COO_IPT;
+// The same choice for COO products (and HYB's COO tail).
+#ifndef SMAT_COO_WARP_TILES
+#define SMAT_COO_WARP_TILES 1
+#endif
+constexpr bool COO_WARP_TILES = SMAT_COO_WARP_TILES != 0;
+constexpr long long COO_TILE = COO_WARP_TILES ? 32LL * 8 : (long long)COO_NT * COO_IPT;
 
 // ---------------------------------------------------------------------------
 // SPLIT, long rows (at least SPLIT_L = 1024 entries; measured on power-law
@@ -576,6 +590,83 @@ __device__ __forceinline__ void split_chunk(long long c, const int32_t *__restri
 // blocks [nc, nc + tiles) are COO tiles of the short rows (the two sets
 // write disjoint rows).  One launch instead of two keeps the GPU full across
 // what was the boundary between them.
+// Within one warp whose 32 lanes' chunks form a tile: the inclusive
+// segmented sum of the lanes' open partial sums c, segments starting at the
+// lanes where a row ended (their c opens the next row).  A lane with a row
+// end gets the sum at the lane before it: the partials of the row its first
+// row end closes.  *open is the sum at lane 31, the row left open at the
+// tile's end.  Shuffles only; fixed order.
+template <typename T>
+__device__ __forceinline__ T warp_carries(bool h, T c, T *open) {
+  const int lane = threadIdx.x & 31;
+  int f = h ? 1 : 0;
+  T v = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T vu = __shfl_up_sync(FULL, v, o);
+    const int fu = __shfl_up_sync(FULL, f, o);
+    if (lane >= o) {
+      if (!f) v = vu + v;
+      f |= fu;
+    }
+  }
+  *open = __shfl_sync(FULL, v, 31);
+  const T prev = __shfl_up_sync(FULL, v, 1);
+  return lane == 0 ? (T)0 : prev;
+}
+
+// A COO tile of one warp: lane l owns the 8 stored entries at b0 + 8 l; rows
+// ending inside a lane's entries are written as in the block tiles, the
+// first one after the warp's carries, and the row open at the tile's end is
+// handed to the fix-up as (carry_row, carry_val)[tile].
+template <typename V, typename T, int MODE>
+__device__ __forceinline__ void coo_warp_tile(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+                                              const V *__restrict__ val, const T *__restrict__ x,
+                                              const Epi<T, MODE> &ep, T *__restrict__ y, long long nnz,
+                                              int32_t *carry_row, T *carry_val, long long tile) {
+  constexpr int IPT = 8;
+  const int lane = threadIdx.x & 31;
+  const long long b0 = tile * (32LL * IPT);
+  if (b0 >= nnz) return;  // the whole warp
+  const long long k0 = b0 + (long long)lane * IPT;
+  const int valid = k0 >= nnz ? 0 : (int)min((long long)IPT, nnz - k0);
+  const bool full = valid == IPT;
+  int r[IPT], c[IPT];
+  T v[IPT];
+  load_i32_run<IPT>(col + k0, full, valid, c, 0);
+  load_val_run<V, IPT>(val + k0, full, valid, v);
+  load_i32_run<IPT>(row + k0, full, valid, r, -1);
+  // the row after a lane's entries is the next lane's first row (a lane past
+  // the end holds -1); lane 31 loads it
+  int r_next = __shfl_down_sync(FULL, r[0], 1);
+  if (lane == 31) r_next = (k0 + IPT < nnz) ? __ldg(row + k0 + IPT) : -1;
+  T acc = 0, first_acc = 0;
+  int first_row = -1;
+  if (valid > 0) coo_chunk<T, IPT, MODE>(r, c, v, r_next, valid, x, ep, y, acc, first_row, first_acc);
+  T open;
+  const T incoming = warp_carries<T>(first_row >= 0, acc, &open);
+  if (first_row >= 0) y[first_row] = ep(incoming + first_acc, y, (long long)first_row);
+  if (lane == 31) {
+    const long long kl = min(b0 + 32LL * IPT, nnz) - 1;
+    const bool opn = kl + 1 < nnz && __ldg(row + kl + 1) == __ldg(row + kl);
+    carry_row[tile] = opn ? __ldg(row + kl) : -1;
+    carry_val[tile] = opn ? open : (T)0;
+  }
+}
+
+// COO products in warp tiles (coo_warp_tile), 8 tiles per 256-thread CTA.
+template <typename V, typename T, int MODE>
+__global__ void __launch_bounds__(COO_NT, SMAT_COO_MINB) coo_warp_kernel(const int32_t *__restrict__ row,
+                                                                     const int32_t *__restrict__ col,
+                                                                     const V *__restrict__ val,
+                                                                     const T *__restrict__ x, Epi<T, MODE> ep,
+                                                                     T *__restrict__ y, long long nnz,
+                                                                     int32_t *carry_row, T *carry_val) {
+  griddep_wait();
+  coo_warp_tile<V, T, MODE>(row, col, val, x, ep, y, nnz, carry_row, carry_val,
+                            (long long)blockIdx.x * (COO_NT / 32) + (threadIdx.x >> 5));
+}
+
 template <typename V, typename T, int MODE>
 __global__ void __launch_bounds__(COO_NT, SMAT_COO_MINB) split_main_kernel(
     const int32_t *__restrict__ cstart, const int32_t *__restrict__ cend, const int32_t *__restrict__ col,
@@ -586,6 +677,9 @@ __global__ void __launch_bounds__(COO_NT, SMAT_COO_MINB) split_main_kernel(
   static_assert(COO_NT == 256, "the chunk path assumes 256 threads");
   if ((long long)blockIdx.x < nc)
     split_chunk<V, T>(blockIdx.x, cstart, cend, col, val, x, part);
+  else if (SPLIT_WARP_TILES)
+    coo_warp_tile<V, T, MODE>(srow, scol, sval, x, ep, y, ns, carry_row, carry_val,
+                              ((long long)blockIdx.x - nc) * (COO_NT / 32) + (threadIdx.x >> 5));
   else
     coo_tile<V, T, COO_NT, COO_CH, MODE>(srow, scol, sval, x, ep, y, ns, carry_row, carry_val,
                                          (long long)blockIdx.x - nc);
@@ -722,10 +816,14 @@ constexpr int MERGE_NT = 256, MERGE_IPT = 8;
 template <typename V, typename T, int MODE>
 cudaError_t launch_coo(const Scratch &sc, const int32_t *row, const int32_t *col, const V *val, const T *x,
                        const Epi<T, MODE> &ep, T *y, long long nnz, cudaStream_t s) {
-  const long long tiles = (nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  const long long tiles = (nnz + COO_TILE - 1) / COO_TILE;
   int32_t *crow = (int32_t *)sc.carry;
   T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
-  (void)launch_pdl(coo_kernel<V, T, COO_NT, COO_CH, MODE>, dim3((unsigned)tiles), dim3(COO_NT), 0, s, row, col, val, x, ep, y, nnz, crow, cval);
+  if (COO_WARP_TILES)
+    (void)launch_pdl(coo_warp_kernel<V, T, MODE>, dim3((unsigned)((tiles + COO_NT / 32 - 1) / (COO_NT / 32))), dim3(COO_NT), 0,
+        s, row, col, val, x, ep, y, nnz, crow, cval);
+  else
+    (void)launch_pdl(coo_kernel<V, T, COO_NT, COO_CH, MODE>, dim3((unsigned)tiles), dim3(COO_NT), 0, s, row, col, val, x, ep, y, nnz, crow, cval);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (tiles > 1) (void)launch_pdl(carry_fixup_kernel<T, MODE>, dim3(grid_for(tiles, 256, 152 * 8)), dim3(256), 0, s, crow, cval, tiles, ep, y);
@@ -861,11 +959,12 @@ cudaError_t spmv_mode(const smat_s *h, const Scratch &sc, int variant, typename 
       // short ones in one grid, then one pass for the long rows' sums, the
       // tiles' carries and the empty rows
       const long long nc = h->split_nc, ns = h->split_ns;
-      const long long tiles = (ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+      const long long tiles = (ns + SPLIT_TILE - 1) / SPLIT_TILE;
+      const long long tile_ctas = SPLIT_WARP_TILES ? (tiles + COO_NT / 32 - 1) / (COO_NT / 32) : tiles;
       int32_t *crow = (int32_t *)sc.carry;
       T *cval = (T *)((char *)sc.carry + ((tiles * 4 + 15) / 16) * 16);
-      if (nc + tiles > 0) {
-        (void)launch_pdl(split_main_kernel<V, T, MODE>, dim3((unsigned)(nc + tiles)), dim3(COO_NT), 0, s,
+      if (nc + tile_ctas > 0) {
+        (void)launch_pdl(split_main_kernel<V, T, MODE>, dim3((unsigned)(nc + tile_ctas)), dim3(COO_NT), 0, s,
             h->split_cstart, h->split_cend, h->colidx, val, (T *)sc.part, nc, h->split_srow, h->split_scol,
             (const V *)h->split_sval, ns, x, ep, y, crow, cval);
         cudaError_t e = cudaGetLastError();
@@ -910,9 +1009,9 @@ cudaError_t launch_merge_partition(const int32_t *rowptr, long long m, long long
 size_t carry_bytes_needed(const smat_s *h, int variant) {
   long long tiles = 0;
   if (variant == SMAT_V_CSR_MERGE) tiles = (h->m + h->nnz + MERGE_NT * MERGE_IPT - 1) / (MERGE_NT * MERGE_IPT);
-  else if (variant == SMAT_V_COO) tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-  else if (variant == SMAT_V_HYB) tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
-  else if (variant == SMAT_V_SPLIT) tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+  else if (variant == SMAT_V_COO) tiles = (h->nnz + COO_TILE - 1) / COO_TILE;
+  else if (variant == SMAT_V_HYB) tiles = (h->hyb_ncoo + COO_TILE - 1) / COO_TILE;
+  else if (variant == SMAT_V_SPLIT) tiles = (h->split_ns + SPLIT_TILE - 1) / SPLIT_TILE;
   else return 0;
   size_t tsz = h->dtype == SMAT_F64 ? 8 : 4;
   return (size_t)((tiles * 4 + 15) / 16) * 16 + (size_t)tiles * tsz;
@@ -925,15 +1024,15 @@ int spmv_launch_count(const smat_s *h, int variant) {
     return 1 + (tiles > 1);
   }
   if (variant == SMAT_V_COO) {
-    long long tiles = (h->nnz + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    long long tiles = (h->nnz + COO_TILE - 1) / COO_TILE;
     return (h->coo_nempty > 0) + (h->nnz > 0) + (tiles > 1);
   }
   if (variant == SMAT_V_HYB) {
-    long long tiles = (h->hyb_ncoo + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    long long tiles = (h->hyb_ncoo + COO_TILE - 1) / COO_TILE;
     return 1 + (h->hyb_ncoo > 0) + (tiles > 1);
   }
   if (variant == SMAT_V_SPLIT) {  // the main grid, then the closing pass when it has rows to do
-    const long long tiles = (h->split_ns + COO_NT * COO_IPT - 1) / (COO_NT * COO_IPT);
+    const long long tiles = (h->split_ns + SPLIT_TILE - 1) / SPLIT_TILE;
     const long long nl = h->split_nc > 0 ? h->split_nl : 0, nt = tiles > 1 ? tiles : 0;
     return (h->split_nc + tiles > 0) + (nl + nt + h->split_ne > 0);
   }
