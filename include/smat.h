@@ -177,10 +177,13 @@ typedef struct {
   float trial_tie;         /* trials: candidates whose median is within this
                               fraction of the fastest count as equally fast
                               (Sec. 7.3 counts near-equal performance as a
-                              hit) and the lowest variant id among them is the
-                              pick, so that plans of matrices whose variants
-                              all run alike are reproducible; 0 breaks only
-                              exact ties that way; default 0.02               */
+                              hit); among them the pick is the one whose
+                              format moves the fewest matrix bytes
+                              (smat_variant_bytes), then the lowest variant
+                              id, so that plans of matrices whose variants all
+                              run alike are reproducible; 0 breaks only exact
+                              ties that way, < 0 keeps the fastest median;
+                              default 0.02                                    */
 } smat_tune_opts_t;
 
 /* Fill *opts with the defaults above. */
@@ -278,6 +281,13 @@ smat_status_t smat_get_kernel(smat_handle_t h, smat_variant_t v, int32_t *kernel
  * finished, so y is ready on return. */
 smat_status_t smat_spmv_host(smat_handle_t h, const void *alpha, const void *x_host,
                              const void *beta, void *y_host, void *stream);
+
+/* Matrix bytes one product through variant v reads (the format's arrays; x
+ * and y, common to every variant, excluded): the quantity the execute-and-
+ * measure search breaks near-ties on.  Computes the features first if
+ * needed; SMAT_ERR_UNSUPPORTED for HYB / SELL / BCSR / SPLIT before their
+ * layout has been measured (by smat_tune or smat_convert). */
+smat_status_t smat_variant_bytes(smat_handle_t h, smat_variant_t v, double *bytes);
 
 /* Number of kernel launches one product through variant v issues on this
  * handle (merge-path and COO add a carry fix-up launch when they span more

@@ -104,6 +104,7 @@ _SIGS = {
     "smat_get_kernel": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_spmv_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smat_spmv_host_pipelined": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smat_variant_bytes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "smat_spmv_launches": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "smat_get_features": (ctypes.c_int, [_VP, ctypes.POINTER(smat_features_t)]),
     "smat_get_feature_vector": (ctypes.c_int, [_VP, _VP]),
@@ -621,6 +622,12 @@ class SpMatrix:
         _check(smat_spmv_host_async(self.h, ctypes.addressof(a), _ptr(x), ctypes.addressof(b), _ptr(y),
                                     _stream_ptr(stream)), "smat_spmv_host_async")
         return y
+
+    def variant_bytes(self, variant) -> float:
+        """Matrix bytes one product through `variant` reads (smat_variant_bytes)."""
+        b = ctypes.c_double()
+        _check(lib().smat_variant_bytes(self.h, int(variant), ctypes.byref(b)), "smat_variant_bytes")
+        return b.value
 
     def spmv_host_pipelined(self, x, y, alpha=1.0, beta=0.0, stream=None):
         """The host-buffer product on the handle's own streams and alternating

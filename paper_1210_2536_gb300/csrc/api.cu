@@ -897,13 +897,22 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     *best = SMAT_V_CSR_SCALAR;
     return SMAT_OK;
   }
-  // near-ties: the lowest variant id within trial_tie of the fastest (0:
-  // among exactly equal medians)
+  // near-ties: among the candidates within trial_tie of the fastest (0: among
+  // exactly equal medians), the one whose format moves the fewest matrix
+  // bytes (it contends least when other products run beside it), then the
+  // lowest variant id
   if (o.trial_tie >= 0.0f) {
     const float lim = best_ms * (1.0f + o.trial_tie);
     int pick = *best;
+    double pick_bytes = variant_bytes(h, pick);
     for (const auto &t : timed_here)
-      if (t.second <= lim && t.first < pick) pick = t.first;
+      if (t.second <= lim) {
+        const double b = variant_bytes(h, t.first);
+        if (b < pick_bytes || (b == pick_bytes && t.first < pick)) {
+          pick = t.first;
+          pick_bytes = b;
+        }
+      }
     if (pick != *best) {
       const int fastest = *best;
       smat_status_t ps = variant_ready(h, pick) ? SMAT_OK : prepare_variant(h, pick, s);
@@ -1442,6 +1451,15 @@ smat_status_t smat_spmv_host_pipelined(smat_handle_t h, const void *alpha, const
   TRY(cudaStreamWaitEvent(s, h->pev_out[q], 0));
   h->pused[q] = true;
   ++h->pcalls;
+  return SMAT_OK;
+}
+
+smat_status_t smat_variant_bytes(smat_handle_t h, smat_variant_t v, double *bytes) {
+  TRYS(check_handle(h));
+  if (!bytes || (int)v < 0 || (int)v >= SMAT_NUM_ALL_VARIANTS) return SMAT_ERR_INVALID_ARG;
+  if (!h->have_features) TRYS(compute_features(h, 0));
+  if (v >= SMAT_V_HYB && v <= SMAT_V_SPLIT && !h->ext_known[v - SMAT_V_HYB]) return SMAT_ERR_UNSUPPORTED;
+  *bytes = variant_bytes(h, (int)v);
   return SMAT_OK;
 }
 

@@ -183,25 +183,33 @@ def test_concurrent_products_on_one_handle():
     M.close()
 
 
-def test_exhaustive_near_ties_take_the_lowest_variant_id():
-    # trial_tie: medians within that fraction of the fastest count as equal
-    # and the lowest variant id among them is the pick
+def test_exhaustive_near_ties_take_the_fewest_bytes():
+    # trial_tie: medians within that fraction of the fastest count as equal;
+    # among them the pick moves the fewest matrix bytes, then has the lowest
+    # variant id
     A = synth.stencil2d5(64)    # every variant within a few us of the others
     M = smat.SpMatrix(A.m, A.n, A.rowptr, A.colidx, A.val, "f64")
+
+    def expected(t, tie):
+        tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
+        best = min(t[v] for v in tried)
+        return min((M.variant_bytes(v), v) for v in tried if t[v] <= (1.0 + tie) * best)[1]
+
     M.tune("exhaustive", trial_reps=5, trial_race=0.0, trial_tie=100.0)
     t = M.timings()
-    tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
-    assert M.plan()["variant"] == min(tried)
+    assert M.plan()["variant"] == expected(t, 100.0)
     for tie in (0.0, 0.02, 0.25):
         M.tune("exhaustive", trial_reps=5, trial_race=0.0, trial_tie=tie)
         t = M.timings()
-        tried = [v for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0]
-        best = min(t[v] for v in tried)
+        best = min(t[v] for v in range(smat.SMAT_NUM_ALL_VARIANTS) if t[v] > 0)
         pick = M.plan()["variant"]
         assert t[pick] <= (1.0 + tie) * best
-        assert pick == min(v for v in tried if t[v] <= (1.0 + tie) * best), (tie, pick, t)
+        assert pick == expected(t, tie), (tie, pick, t)
         y = M.spmv(torch.from_numpy(synth.uniform(0, 1, A.n)).to(DEV))   # the pick's format is in place
         assert y.shape[0] == A.m
+    # bytes agree with the formats' sizes
+    assert M.variant_bytes(smat.SMAT_V_CSR_SCALAR) == 12 * A.nnz + 4 * (A.m + 1)
+    assert M.variant_bytes(smat.SMAT_V_COO) == 16 * A.nnz
     M.close()
 
 
