@@ -478,12 +478,21 @@ def run_products(args, ctx):
         prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
                           f=M.features(), launches=M.launches()))
 
-    # plain CSR-scalar and tuned pick, each timed alone (median of 20)
+    # plain CSR-scalar and tuned pick, each timed alone (median of 20).  L2
+    # is flushed before every repetition (a write of twice its size, outside
+    # the events), as the other products evict it in the step; a short device
+    # sleep first lets the host queue the repetitions ahead of the GPU, so
+    # that no host launch latency falls between a pair of events
+    flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,
+                        device=dev)
+
     def time_variant(p, v, reps=20):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for _ in range(3):
             p["M"].spmv(p["x"], p["y"], variant=v)
+        torch.cuda._sleep(4_000_000)
         for s, e in ev:
+            flush.fill_(1)
             s.record()
             p["M"].spmv(p["x"], p["y"], variant=v)
             e.record()

@@ -111,6 +111,9 @@ def main():
                 M.spmv(x, y, variant=v)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(a.reps)]
+            # a device sleep lets the host queue the repetitions ahead of the
+            # GPU, so that no host launch latency falls between two events
+            torch.cuda._sleep(4_000_000)
             for s, e in ev:
                 if flush is not None:
                     flush.fill_(1)
