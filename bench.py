@@ -478,21 +478,23 @@ def run_products(args, ctx):
         prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
                           f=M.features(), launches=M.launches()))
 
-    # plain CSR-scalar and tuned pick, each timed alone (median of 20).  L2
-    # is flushed before every repetition (a write of twice its size, outside
-    # the events), as the other products evict it in the step; a short device
-    # sleep first lets the host queue the repetitions ahead of the GPU, so
-    # that no host launch latency falls between a pair of events
+    # plain CSR-scalar and tuned pick, each timed alone (median of 20).  With
+    # cold=True L2 is flushed before every repetition (a write of twice its
+    # size, outside the events), as the other products evict it in the step;
+    # otherwise the repetitions run back to back, as the tuner's trials do.
+    # A short device sleep first lets the host queue the repetitions ahead of
+    # the GPU, so that no host launch latency falls between a pair of events.
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,
                         device=dev)
 
-    def time_variant(p, v, reps=20):
+    def time_variant(p, v, reps=20, cold=True):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for _ in range(3):
             p["M"].spmv(p["x"], p["y"], variant=v)
         torch.cuda._sleep(4_000_000)
         for s, e in ev:
-            flush.fill_(1)
+            if cold:
+                flush.fill_(1)
             s.record()
             p["M"].spmv(p["x"], p["y"], variant=v)
             e.record()
@@ -1071,23 +1073,40 @@ def kernel_label(M, variant):
 
 
 def selector_regret(prods, time_variant):
-    """Regret of each learned pick against the fastest of the eight classes,
-    every admissible one timed alone here (median of 20): the paper's
-    accuracy and slowdown of the prediction (Sec. 7.3), live on this GPU."""
+    """Regret of each tuned pick (learned selector plus its execute-and-
+    measure fallback over the further formats) against the fastest variant
+    the library can run on that matrix: the eight classes of Sec. 5 and the
+    further formats, every one that builds timed alone here (median of 20),
+    the pick among them in the same loop.  Measured twice: with the
+    repetitions back to back as the tuner's trials run them (`warm`, the
+    conditions the selector's labels were taken under), and with L2 flushed
+    before each (`cold_l2`, the conditions of the step, whose other products
+    evict each matrix).  The paper's accuracy and slowdown of the prediction
+    (Sec. 7.3), live on this GPU."""
     import paper_1210_2536_gb300 as smat
-    rows = []
-    for p in prods:
-        adm = p["f"]["admissible"]
-        t = {v: time_variant(p, v) for v in range(smat.SMAT_NUM_VARIANTS) if (adm >> v) & 1}
-        best_v = min(t, key=t.get)
-        pick_t = p["pick_ms"]
-        rows.append({"matrix": p["A"].name, "pick": p["plan"]["name"], "best": smat.VARIANT_NAMES[best_v],
-                     "regret": round(pick_t / t[best_v] - 1.0, 4), "hit": pick_t <= 1.02 * t[best_v],
-                     "trialled": p["plan"]["trialled"]})
-    reg = sorted(r["regret"] for r in rows)
-    return {"matrices": len(rows), "mean_regret": round(sum(reg) / len(reg), 4),
-            "p90_regret": reg[min(len(reg) - 1, int(0.9 * len(reg)))],
-            "accuracy_within_2pct": round(sum(r["hit"] for r in rows) / len(rows), 4), "rows": rows}
+    further = (smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR, smat.SMAT_V_SPLIT)
+    out = {}
+    for mode, cold in (("warm", False), ("cold_l2", True)):
+        rows = []
+        for p in prods:
+            adm = p["f"]["admissible"]
+            pick = p["plan"]["variant"]
+            t = {}
+            for v in sorted({v for v in range(smat.SMAT_NUM_VARIANTS) if (adm >> v) & 1} | set(further) | {pick}):
+                try:
+                    t[v] = time_variant(p, v, cold=cold)
+                except smat.SmatError:        # a further format this matrix does not admit
+                    if v == pick:
+                        raise
+            best_v = min(t, key=t.get)
+            rows.append({"matrix": p["A"].name, "pick": p["plan"]["name"], "best": smat.VARIANT_NAMES[best_v],
+                         "regret": round(t[pick] / t[best_v] - 1.0, 4), "hit": t[pick] <= 1.02 * t[best_v],
+                         "trialled": p["plan"]["trialled"]})
+        reg = sorted(r["regret"] for r in rows)
+        out[mode] = {"matrices": len(rows), "mean_regret": round(sum(reg) / len(reg), 4),
+                     "p90_regret": reg[min(len(reg) - 1, int(0.9 * len(reg)))], "max_regret": reg[-1],
+                     "accuracy_within_2pct": round(sum(r["hit"] for r in rows) / len(rows), 4), "rows": rows}
+    return out
 
 
 def main():

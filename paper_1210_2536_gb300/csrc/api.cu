@@ -555,13 +555,18 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   TRY(cudaEventCreate(&e0));
   TRY(cudaEventCreate(&e1));
   struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
+  double enq_us = 10.0;
   auto time_it = [&](int u, int lane, float *med) -> smat_status_t {
     for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
     float ms[5];
     for (int r = 0; r < 5; ++r) {
-      TRY(cudaEventRecord(e0, s));
-      TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
-      TRY(cudaEventRecord(e1, s));
+      // queued behind a device hold, so that the events bracket the product alone
+      TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+        cudaError_t q = cudaEventRecord(e0, s);
+        if (q == cudaSuccess) q = launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s);
+        if (q == cudaSuccess) q = cudaEventRecord(e1, s);
+        return q;
+      }));
       TRY(cudaEventSynchronize(e1));
       TRY(cudaEventElapsedTime(&ms[r], e0, e1));
     }
@@ -841,6 +846,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
   } guard{ev};
   const double t_start = now_ms();
   float best_ms = 1e30f;
+  double enq_us = 10.0;  // host time to queue a block of timed repetitions
   *best = -1;
   std::vector<std::pair<int, float>> timed_here;
   for (int v : cands) {
@@ -853,13 +859,19 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     // times the best so far stops there (its median of those is kept)
     const int first = (o.trial_race > 0.0f && best_ms < 1e30f) ? std::min(reps, 3) : reps;
     int done = 0;
+    // the repetitions are queued behind a device hold, so that each pair of
+    // events brackets the product alone
     auto timed = [&](int upto) -> cudaError_t {
-      for (int r = done; r < upto; ++r) {
-        cudaError_t e = cudaEventRecord(ev[2 * r], s);
-        if (e == cudaSuccess) e = launch_spmv(h, v, a, x.p, b, y.p, s, false);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], s);
-        if (e != cudaSuccess) return e;
-      }
+      cudaError_t e = queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+        for (int r = done; r < upto; ++r) {
+          cudaError_t q = cudaEventRecord(ev[2 * r], s);
+          if (q == cudaSuccess) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
+          if (q == cudaSuccess) q = cudaEventRecord(ev[2 * r + 1], s);
+          if (q != cudaSuccess) return q;
+        }
+        return cudaSuccess;
+      });
+      if (e != cudaSuccess) return e;
       done = upto;
       return cudaStreamSynchronize(s);
     };

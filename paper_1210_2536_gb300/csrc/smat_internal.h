@@ -255,4 +255,40 @@ cudaError_t launch_spmv(const smat_s *h, int variant, const void *alpha, const v
 cudaError_t launch_mlp_forward(const float *params, const float *X, int B, float *logits,
                                cudaStream_t s);
 
+// ---- timing support (measure.cu) ----
+// Host wall clock in milliseconds (steady).
+double host_ms();
+// Holds stream s on the device for about `us` microseconds (clamped to
+// [0, 4000]): one thread polls the global nanosecond timer, with short sleeps
+// and a bounded number of polls, so it ends whatever the timer does.
+cudaError_t launch_hold(cudaStream_t s, double us);
+constexpr double HOLD_MAX_US = 4000.0;
+
+// Queues timed work behind a device hold that outlasts the host's time to
+// enqueue it, so that the GPU reaches the work only once all of it is queued
+// and no host launch latency falls between a pair of timing events (a short
+// kernel enqueued behind an idle GPU is otherwise timed together with the
+// host's latency to submit it).  enqueue() issues the work and its events
+// without synchronising; *enq_us carries the host's enqueue time from one
+// call to the next.  When the enqueue outlasted the hold, the stream is
+// drained and the same work queued again behind a hold twice as long (three
+// attempts at most).
+template <typename F>
+cudaError_t queue_ahead(cudaStream_t s, double *enq_us, F &&enqueue) {
+  for (int attempt = 0;; ++attempt) {
+    double hold = (20.0 + 1.5 * *enq_us) * (double)(1 << attempt);
+    hold = hold < HOLD_MAX_US ? hold : HOLD_MAX_US;
+    cudaError_t e = launch_hold(s, hold);
+    if (e != cudaSuccess) return e;
+    const double t0 = host_ms();
+    e = enqueue();
+    const double dt = (host_ms() - t0) * 1e3;
+    if (e != cudaSuccess) return e;
+    *enq_us = dt;
+    if (dt < hold || attempt == 2) return cudaSuccess;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+  }
+}
+
 }  // namespace smat
