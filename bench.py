@@ -31,6 +31,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -478,28 +479,41 @@ def run_products(args, ctx):
         prods.append(dict(A=A, dt=dt, M=M, x=xd, y=yd, v64=v64, plan=plan, create_ms=create_ms,
                           f=M.features(), launches=M.launches()))
 
-    # plain CSR-scalar and tuned pick, each timed alone (median of 20).  With
-    # cold=True L2 is flushed before every repetition (a write of twice its
-    # size, outside the events), as the other products evict it in the step;
-    # otherwise the repetitions run back to back, as the tuner's trials do.
-    # A short device sleep first lets the host queue the repetitions ahead of
-    # the GPU, so that no host launch latency falls between a pair of events.
+    # plain CSR-scalar and tuned pick, each timed alone: the mean of the middle
+    # half of 20 repetitions.  With cold=True L2 is flushed before every
+    # repetition (a write of twice its size, outside the events), as the other
+    # products evict it in the step, and a repetition is one product;
+    # otherwise the repetitions run back to back, as the tuner's trials do,
+    # each timing enough products (up to 32) to span about 40 us, since event
+    # timestamps on this GPU advance in steps of about 2 us.  A device sleep
+    # first lets the host queue the repetitions ahead of the GPU, so that no
+    # host launch latency falls between a pair of events.
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,
                         device=dev)
 
     def time_variant(p, v, reps=20, cold=True):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        M, x, y = p["M"], p["x"], p["y"]
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(2100 * 300)
+        w0.record()
         for _ in range(3):
-            p["M"].spmv(p["x"], p["y"], variant=v)
-        torch.cuda._sleep(4_000_000)
+            M.spmv(x, y, variant=v)
+        w1.record()
+        torch.cuda.synchronize()
+        group = 1 if cold else max(1, min(32, math.ceil(0.040 / max(w0.elapsed_time(w1) / 3, 1e-4))))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda._sleep(int(2100 * (500 + 30 * reps * group)))   # cycles: about 0.5 ms + 30 us per product
         for s, e in ev:
             if cold:
                 flush.fill_(1)
             s.record()
-            p["M"].spmv(p["x"], p["y"], variant=v)
+            for _ in range(group):
+                M.spmv(x, y, variant=v)
             e.record()
         torch.cuda.synchronize()
-        return statistics.median(s.elapsed_time(e) for s, e in ev)
+        t = sorted(s.elapsed_time(e) / group for s, e in ev)
+        q = len(t) // 4
+        return statistics.mean(t[q:len(t) - q])
 
     for p in prods:
         p["csr_ms"] = time_variant(p, smat.SMAT_V_CSR_SCALAR)
@@ -1101,7 +1115,10 @@ def selector_regret(prods, time_variant):
             best_v = min(t, key=t.get)
             rows.append({"matrix": p["A"].name, "pick": p["plan"]["name"], "best": smat.VARIANT_NAMES[best_v],
                          "regret": round(t[pick] / t[best_v] - 1.0, 4), "hit": t[pick] <= 1.02 * t[best_v],
-                         "trialled": p["plan"]["trialled"]})
+                         "trialled": p["plan"]["trialled"], "confidence": round(p["plan"]["confidence"], 3),
+                         "us": {smat.VARIANT_NAMES[v]: round(ms * 1e3, 2) for v, ms in t.items()},
+                         "tuner_us": {smat.VARIANT_NAMES[v]: round(float(ms) * 1e3, 2)
+                                      for v, ms in enumerate(p["M"].timings()) if ms > 0}})
         reg = sorted(r["regret"] for r in rows)
         out[mode] = {"matrices": len(rows), "mean_regret": round(sum(reg) / len(reg), 4),
                      "p90_regret": reg[min(len(reg) - 1, int(0.9 * len(reg)))], "max_regret": reg[-1],

@@ -527,6 +527,17 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
   return SMAT_OK;
 }
 
+// Products per timed repetition: enough back to back that a repetition spans
+// about 40 us, since this GPU's event timestamps advance in steps of about
+// 2 us (measured: the medians of single short products sit on multiples of
+// 2.05 us), too coarse to rank products of 5-20 us one launch at a time.
+int products_per_rep(float ms_per_product) {
+  const float target_ms = 0.040f;
+  if (!(ms_per_product > 0.0f)) return 1;
+  const int g = (int)std::ceil(target_ms / ms_per_product);
+  return g < 1 ? 1 : (g > 32 ? 32 : g);
+}
+
 // Kernel search for ELL / DIA (the paper's per-format implementation choice,
 // Sec. 3): time the candidate batch widths once on zero vectors, keep the
 // faster; for ELL then time the lane-striped row mapping at that width, for
@@ -556,20 +567,26 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   TRY(cudaEventCreate(&e1));
   struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
   double enq_us = 10.0;
+  // each timed block is queued behind a device hold, so that its events
+  // bracket the products alone; `group` products per block
+  auto block = [&](int u, int lane, int group, float *ms) -> smat_status_t {
+    TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+      cudaError_t q = cudaEventRecord(e0, s);
+      for (int g = 0; g < group && q == cudaSuccess; ++g) q = launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s);
+      if (q == cudaSuccess) q = cudaEventRecord(e1, s);
+      return q;
+    }));
+    TRY(cudaEventSynchronize(e1));
+    TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= (float)group;
+    return SMAT_OK;
+  };
   auto time_it = [&](int u, int lane, float *med) -> smat_status_t {
-    for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
+    float wms;
+    TRYS(block(u, lane, 2, &wms));  // warm-up, which also sizes the blocks
+    const int group = products_per_rep(wms);
     float ms[5];
-    for (int r = 0; r < 5; ++r) {
-      // queued behind a device hold, so that the events bracket the product alone
-      TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
-        cudaError_t q = cudaEventRecord(e0, s);
-        if (q == cudaSuccess) q = launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s);
-        if (q == cudaSuccess) q = cudaEventRecord(e1, s);
-        return q;
-      }));
-      TRY(cudaEventSynchronize(e1));
-      TRY(cudaEventElapsedTime(&ms[r], e0, e1));
-    }
+    for (int r = 0; r < 5; ++r) TRYS(block(u, lane, group, &ms[r]));
     std::sort(ms, ms + 5);
     *med = ms[2];
     return SMAT_OK;
@@ -838,7 +855,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
   const void *a = h->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
   const void *b = h->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
   const int reps = std::max(1, o.trial_reps);
-  std::vector<cudaEvent_t> ev((size_t)reps * 2);
+  std::vector<cudaEvent_t> ev((size_t)reps * 2 + 2);  // two per repetition, two around the warm-up
   for (auto &e : ev) TRY(cudaEventCreate(&e));
   struct EvGuard {
     std::vector<cudaEvent_t> &v;
@@ -854,18 +871,32 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     smat_status_t ps = prepare_variant(h, v, s);
     if (ps == SMAT_ERR_UNSUPPORTED || ps == SMAT_ERR_ALLOC) continue;  // skip, keep searching
     TRYS(ps);
-    for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
+    // the warm-up products, timed as one block, size the repetitions
+    int group = 1;
+    if (o.trial_warmup > 0) {
+      const size_t w0 = (size_t)reps * 2;
+      TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+        cudaError_t q = cudaEventRecord(ev[w0], s);
+        for (int w = 0; w < o.trial_warmup && q == cudaSuccess; ++w) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
+        if (q == cudaSuccess) q = cudaEventRecord(ev[w0 + 1], s);
+        return q;
+      }));
+      TRY(cudaEventSynchronize(ev[w0 + 1]));
+      float wms = 0.0f;
+      TRY(cudaEventElapsedTime(&wms, ev[w0], ev[w0 + 1]));
+      group = products_per_rep(wms / (float)o.trial_warmup);
+    }
     // racing: a candidate whose first few products already take trial_race
     // times the best so far stops there (its median of those is kept)
     const int first = (o.trial_race > 0.0f && best_ms < 1e30f) ? std::min(reps, 3) : reps;
     int done = 0;
-    // the repetitions are queued behind a device hold, so that each pair of
-    // events brackets the product alone
+    // each repetition times `group` products back to back, queued behind a
+    // device hold so that its pair of events brackets the products alone
     auto timed = [&](int upto) -> cudaError_t {
       cudaError_t e = queue_ahead(s, &enq_us, [&]() -> cudaError_t {
         for (int r = done; r < upto; ++r) {
           cudaError_t q = cudaEventRecord(ev[2 * r], s);
-          if (q == cudaSuccess) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
+          for (int g = 0; g < group && q == cudaSuccess; ++g) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
           if (q == cudaSuccess) q = cudaEventRecord(ev[2 * r + 1], s);
           if (q != cudaSuccess) return q;
         }
@@ -880,6 +911,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
       for (int r = 0; r < done; ++r) {
         cudaError_t e = cudaEventElapsedTime(&ms[(size_t)r], ev[2 * r], ev[2 * r + 1]);
         if (e != cudaSuccess) return e;
+        ms[(size_t)r] /= (float)group;
       }
       std::nth_element(ms.begin(), ms.begin() + done / 2, ms.end());
       return cudaSuccess;

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 
@@ -107,21 +108,33 @@ def main():
                 except smat.SmatError:
                     continue
                 label = f"{names[v]}:{kernel_names[v][k]}" + ("*" if k == measured else "")
-            for _ in range(a.warmup):
+            # a device sleep lets the host queue the launches ahead of the GPU,
+            # so that no host launch latency falls between two events
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda._sleep(2100 * (100 + 30 * max(a.warmup, 1)))
+            w0.record()
+            for _ in range(max(a.warmup, 1)):
                 M.spmv(x, y, variant=v)
+            w1.record()
+            torch.cuda.synchronize()
+            # warm: enough products per repetition (up to 32) to span about
+            # 40 us, since event timestamps advance in steps of about 2 us
+            group = 1 if a.cold else max(1, min(32, math.ceil(0.040 / max(w0.elapsed_time(w1) / max(a.warmup, 1),
+                                                                           1e-4))))
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(a.reps)]
-            # a device sleep lets the host queue the repetitions ahead of the
-            # GPU, so that no host launch latency falls between two events
-            torch.cuda._sleep(4_000_000)
+            torch.cuda._sleep(int(2100 * (500 + 30 * a.reps * group)))
             for s, e in ev:
                 if flush is not None:
                     flush.fill_(1)
                 s.record()
-                M.spmv(x, y, variant=v)
+                for _ in range(group):
+                    M.spmv(x, y, variant=v)
                 e.record()
             torch.cuda.synchronize()
-            ms = statistics.median(s.elapsed_time(e) for s, e in ev)
+            t = sorted(s.elapsed_time(e) / group for s, e in ev)
+            q = len(t) // 4
+            ms = statistics.mean(t[q:len(t) - q])   # mean of the middle half
             b = algorithmic_bytes(f, v, a.dtype)
             out["variants"][label] = {"ms": round(ms, 5), "gflops": round(2 * A.nnz / ms / 1e6, 1),
                                       "gbs": round(b / ms / 1e6, 1), "hbm_frac": round(b / ms / 1e6 / peak, 4)}
