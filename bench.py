@@ -481,15 +481,16 @@ def run_products(args, ctx):
 
     # plain CSR-scalar and tuned pick, each timed alone: the mean of the middle
     # half of 20 repetitions.  With cold=True L2 is flushed before every
-    # repetition (a write of twice its size, outside the events), as the other
-    # products evict it in the step, and a repetition is one product;
+    # repetition (a read of twice its size, outside the events, which leaves
+    # it holding clean lines of other data, as the other products of the step
+    # leave it), and a repetition is one product;
     # otherwise the repetitions run back to back, as the tuner's trials do,
     # each timing enough products (up to 32) to span about 40 us, since event
     # timestamps on this GPU advance in steps of about 2 us.  A device sleep
     # first lets the host queue the repetitions ahead of the GPU, so that no
     # host launch latency falls between a pair of events.
-    flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,
-                        device=dev)
+    flush = torch.ones(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,
+                       device=dev)
 
     def time_variant(p, v, reps=20, cold=True):
         M, x, y = p["M"], p["x"], p["y"]
@@ -508,7 +509,7 @@ def run_products(args, ctx):
             torch.cuda._sleep(int(2100 * hold_us))    # cycles at about 2.1 GHz
             for s, e in ev:
                 if cold:
-                    flush.fill_(1)
+                    flush.sum()
                 s.record()
                 for _ in range(group):
                     M.spmv(x, y, variant=v)

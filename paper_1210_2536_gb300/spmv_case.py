@@ -56,8 +56,8 @@ def main():
                     help="kernels behind DIA / ELL: 'measured' (the handle's choice), or 'all' to time each "
                          "(DIA: direct / staged; ELL: consecutive / lane-striped)")
     ap.add_argument("--cold", action="store_true",
-                    help="write a buffer of twice the L2 size between timed repetitions (x and the matrix "
-                         "start from HBM)")
+                    help="read a buffer of twice the L2 size between timed repetitions (x and the matrix "
+                         "start from HBM; L2 holds clean lines of other data)")
     a = ap.parse_args()
     A = make_matrix(a.matrix)
     from . import synth
@@ -88,7 +88,7 @@ def main():
     flush = None
     if a.cold:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-        flush = torch.empty(2 * l2 // 4, dtype=torch.int32, device=dev)
+        flush = torch.ones(2 * l2 // 4, dtype=torch.int32, device=dev)
     kernel_names = {smat.SMAT_V_DIA: ("direct", "staged1", "staged2"),
                     smat.SMAT_V_ELL: ("rows", "lanes")}
     for v in vs:
@@ -130,7 +130,7 @@ def main():
                 torch.cuda._sleep(int(2100 * hold_us))    # cycles at about 2.1 GHz
                 for s, e in ev:
                     if flush is not None:
-                        flush.fill_(1)
+                        flush.sum()
                     s.record()
                     for _ in range(group):
                         M.spmv(x, y, variant=v)
