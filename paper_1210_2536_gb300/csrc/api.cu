@@ -582,13 +582,15 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
     return SMAT_OK;
   };
   auto time_it = [&](int u, int lane, float *med) -> smat_status_t {
+    for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
     float wms;
-    TRYS(block(u, lane, 2, &wms));  // warm-up, which also sizes the blocks
+    TRYS(block(u, lane, 1, &wms));  // one product alone sizes the blocks
     const int group = products_per_rep(wms);
+    const int nrep = group > 1 ? 3 : 5;   // about as many products as five single ones
     float ms[5];
-    for (int r = 0; r < 5; ++r) TRYS(block(u, lane, group, &ms[r]));
-    std::sort(ms, ms + 5);
-    *med = ms[2];
+    for (int r = 0; r < nrep; ++r) TRYS(block(u, lane, group, &ms[r]));
+    std::sort(ms, ms + nrep);
+    *med = ms[nrep / 2];
     return SMAT_OK;
   };
   float best = 1e30f;
@@ -854,8 +856,8 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
   const float onef = 1.0f, zerof = 0.0f;
   const void *a = h->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
   const void *b = h->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
-  const int reps = std::max(1, o.trial_reps);
-  std::vector<cudaEvent_t> ev((size_t)reps * 2 + 2);  // two per repetition, two around the warm-up
+  const int reps_max = std::max(1, o.trial_reps);
+  std::vector<cudaEvent_t> ev((size_t)reps_max * 2 + 2);  // two per repetition, two for the sizing product
   for (auto &e : ev) TRY(cudaEventCreate(&e));
   struct EvGuard {
     std::vector<cudaEvent_t> &v;
@@ -871,21 +873,25 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     smat_status_t ps = prepare_variant(h, v, s);
     if (ps == SMAT_ERR_UNSUPPORTED || ps == SMAT_ERR_ALLOC) continue;  // skip, keep searching
     TRYS(ps);
-    // the warm-up products, timed as one block, size the repetitions
+    for (int w = 0; w < o.trial_warmup; ++w) TRY(launch_spmv(h, v, a, x.p, b, y.p, s, false));
+    // one product timed alone sizes the repetitions: `group` products each,
+    // and fewer repetitions when grouped, so that a candidate costs about
+    // trial_reps products as before (at least 3 repetitions)
     int group = 1;
-    if (o.trial_warmup > 0) {
-      const size_t w0 = (size_t)reps * 2;
+    {
+      const size_t w0 = (size_t)reps_max * 2;
       TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
         cudaError_t q = cudaEventRecord(ev[w0], s);
-        for (int w = 0; w < o.trial_warmup && q == cudaSuccess; ++w) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
+        if (q == cudaSuccess) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
         if (q == cudaSuccess) q = cudaEventRecord(ev[w0 + 1], s);
         return q;
       }));
       TRY(cudaEventSynchronize(ev[w0 + 1]));
       float wms = 0.0f;
       TRY(cudaEventElapsedTime(&wms, ev[w0], ev[w0 + 1]));
-      group = products_per_rep(wms / (float)o.trial_warmup);
+      group = products_per_rep(wms);
     }
+    const int reps = std::max(std::min(reps_max, 3), (reps_max + group - 1) / group);
     // racing: a candidate whose first few products already take trial_race
     // times the best so far stops there (its median of those is kept)
     const int first = (o.trial_race > 0.0f && best_ms < 1e30f) ? std::min(reps, 3) : reps;

@@ -271,12 +271,12 @@ constexpr double HOLD_MAX_US = 4000.0;
 // host's latency to submit it).  enqueue() issues the work and its events
 // without synchronising; *enq_us carries the host's enqueue time from one
 // call to the next.  When the enqueue outlasted the hold, the stream is
-// drained and the same work queued again behind a hold twice as long (three
-// attempts at most).
+// drained and the same work queued again behind a hold sized from the
+// enqueue just measured (three attempts at most).
 template <typename F>
 cudaError_t queue_ahead(cudaStream_t s, double *enq_us, F &&enqueue) {
   for (int attempt = 0;; ++attempt) {
-    double hold = (20.0 + 1.5 * *enq_us) * (double)(1 << attempt);
+    double hold = 20.0 + 1.5 * *enq_us;
     hold = hold < HOLD_MAX_US ? hold : HOLD_MAX_US;
     cudaError_t e = launch_hold(s, hold);
     if (e != cudaSuccess) return e;
