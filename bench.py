@@ -197,7 +197,8 @@ class Clocks:
         sm = [float(r[1]) for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+        return {"sm_mhz": statistics.median(sm), "sm_mhz_min": min(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons,
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
@@ -1106,9 +1107,13 @@ def selector_regret(prods, time_variant):
     evict each matrix).  The paper's accuracy and slowdown of the prediction
     (Sec. 7.3), live on this GPU."""
     import paper_1210_2536_gb300 as smat
+    import torch
     further = (smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR, smat.SMAT_V_SPLIT)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     out = {}
     for mode, cold in (("warm", False), ("cold_l2", True)):
+        clocks = Clocks(vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device()))
+        clocks.start()
         rows = []
         for p in prods:
             adm = p["f"]["admissible"]
@@ -1130,7 +1135,8 @@ def selector_regret(prods, time_variant):
         reg = sorted(r["regret"] for r in rows)
         out[mode] = {"matrices": len(rows), "mean_regret": round(sum(reg) / len(reg), 4),
                      "p90_regret": reg[min(len(reg) - 1, int(0.9 * len(reg)))], "max_regret": reg[-1],
-                     "accuracy_within_2pct": round(sum(r["hit"] for r in rows) / len(rows), 4), "rows": rows}
+                     "accuracy_within_2pct": round(sum(r["hit"] for r in rows) / len(rows), 4),
+                     "clocks": clocks.stop(), "rows": rows}
     return out
 
 
