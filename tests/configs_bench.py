@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import time
@@ -50,16 +51,39 @@ def _peak():
 
 
 def _time(fn, reps=20, warmup=3):
+    """Milliseconds per call of fn, back to back: the mean of the middle half
+    of `reps` repetitions, each timing enough calls (up to 32) to span about
+    40 us, since event timestamps on this GPU advance in steps of about 2 us;
+    the repetitions are queued behind a device sleep that outlasts their host
+    enqueue (re-queued behind a longer one if it did not), so that no host
+    launch latency falls between a pair of events."""
     import torch
-    for _ in range(warmup):
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(2100 * (100 + 50 * max(warmup, 1)))
+    w0.record()
+    for _ in range(max(warmup, 1)):
         fn()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for s, e in ev:
-        s.record()
-        fn()
-        e.record()
+    w1.record()
     torch.cuda.synchronize()
-    return statistics.median(s.elapsed_time(e) for s, e in ev)
+    group = max(1, min(32, math.ceil(0.040 / max(w0.elapsed_time(w1) / max(warmup, 1), 1e-4))))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    hold_us = 500 + 50 * reps * group
+    for _ in range(3):
+        t0 = time.perf_counter()
+        torch.cuda._sleep(int(2100 * min(hold_us, 200000)))     # cycles at about 2.1 GHz
+        for s, e in ev:
+            s.record()
+            for _ in range(group):
+                fn()
+            e.record()
+        host_us = (time.perf_counter() - t0) * 1e6
+        torch.cuda.synchronize()
+        if host_us < hold_us:
+            break
+        hold_us = 1.5 * host_us + 500
+    t = sorted(s.elapsed_time(e) / group for s, e in ev)
+    q = len(t) // 4
+    return statistics.mean(t[q:len(t) - q])
 
 
 def _select():
