@@ -486,8 +486,9 @@ def run_products(args, ctx):
     # it holding clean lines of other data, as the other products of the step
     # leave it), and a repetition is one product;
     # otherwise the repetitions run back to back, as the tuner's trials do,
-    # each timing enough products (up to 32) to span about 40 us, since event
-    # timestamps on this GPU advance in steps of about 2 us.  A device sleep
+    # each timing enough products (up to 32) to span about 40 us, since the
+    # event-timed duration of a single short kernel on this GPU moves in steps
+    # of about 2 us.  A device sleep
     # first lets the host queue the repetitions ahead of the GPU, so that no
     # host launch latency falls between a pair of events.
     flush = torch.ones(2 * torch.cuda.get_device_properties(dev).L2_cache_size // 4, dtype=torch.int32,

@@ -157,8 +157,9 @@ typedef struct {
   int32_t trial_reps;      /* timed products per variant: the median of that many
                               repetitions, or, for products under about 40 us,
                               of max(3, ceil(trial_reps / g)) repetitions of g
-                              back-to-back products spanning about 40 us (event
-                              timestamps advance in steps of about 2 us); each
+                              back-to-back products spanning about 40 us (the
+                              event-timed duration of one short kernel moves
+                              in steps of about 2 us); each
                               block of repetitions is queued behind a short
                               device hold so that no host launch latency falls
                               between its events                              */

@@ -528,9 +528,10 @@ smat_status_t ext_layout(smat_s *h, int v, int sigma, cudaStream_t s) {
 }
 
 // Products per timed repetition: enough back to back that a repetition spans
-// about 40 us, since this GPU's event timestamps advance in steps of about
-// 2 us (measured: the medians of single short products sit on multiples of
-// 2.05 us), too coarse to rank products of 5-20 us one launch at a time.
+// about 40 us, since on this GPU the event-timed duration of a single short
+// kernel moves in steps of about 2 us (measured: an empty kernel 3.5-3.8 us,
+// 256 KB and 4 MB reads both 5.6-5.8 us), too coarse to rank products of
+// 5-20 us one launch at a time.
 int products_per_rep(float ms_per_product) {
   const float target_ms = 0.040f;
   if (!(ms_per_product > 0.0f)) return 1;

@@ -119,7 +119,8 @@ def main():
             w1.record()
             torch.cuda.synchronize()
             # warm: enough products per repetition (up to 32) to span about
-            # 40 us, since event timestamps advance in steps of about 2 us
+            # 40 us, since the event-timed duration of a single short kernel
+            # moves in steps of about 2 us
             group = 1 if a.cold else max(1, min(32, math.ceil(0.040 / max(w0.elapsed_time(w1) / max(a.warmup, 1),
                                                                            1e-4))))
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

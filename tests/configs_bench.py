@@ -53,7 +53,8 @@ def _peak():
 def _time(fn, reps=20, warmup=3):
     """Milliseconds per call of fn, back to back: the mean of the middle half
     of `reps` repetitions, each timing enough calls (up to 32) to span about
-    40 us, since event timestamps on this GPU advance in steps of about 2 us;
+    40 us, since the event-timed duration of a single short kernel on this
+    GPU moves in steps of about 2 us;
     the repetitions are queued behind a device sleep that outlasts their host
     enqueue (re-queued behind a longer one if it did not), so that no host
     launch latency falls between a pair of events."""
