@@ -563,33 +563,42 @@ smat_status_t measure_batch_width(smat_s *h, int variant, cudaStream_t s) {
   const float onef = 1.0f, zerof = 0.0f;
   const void *a = h->dtype == SMAT_F64 ? (const void *)&one : (const void *)&onef;
   const void *b = h->dtype == SMAT_F64 ? (const void *)&zero : (const void *)&zerof;
-  cudaEvent_t e0, e1;
-  TRY(cudaEventCreate(&e0));
-  TRY(cudaEventCreate(&e1));
-  struct EvFree { cudaEvent_t a, c; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(c); } } evf{e0, e1};
-  double enq_us = 10.0;
-  // each timed block is queued behind a device hold, so that its events
-  // bracket the products alone; `group` products per block
-  auto block = [&](int u, int lane, int group, float *ms) -> smat_status_t {
-    TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
-      cudaError_t q = cudaEventRecord(e0, s);
-      for (int g = 0; g < group && q == cudaSuccess; ++g) q = launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s);
-      if (q == cudaSuccess) q = cudaEventRecord(e1, s);
+  cudaEvent_t ev[10] = {};  // two per repetition (at most 5)
+  struct EvFree {
+    cudaEvent_t *v;
+    ~EvFree() { for (int k = 0; k < 10; ++k) if (v[k]) cudaEventDestroy(v[k]); }
+  } evf{ev};
+  for (int k = 0; k < 10; ++k) TRY(cudaEventCreate(&ev[k]));
+  double enq_us = 10.0;  // host time to queue one timed product
+  // nrep repetitions of `group` products each, queued together behind a
+  // device hold so that each pair of events brackets its products alone;
+  // per-product milliseconds in ms[0..nrep)
+  auto blocks = [&](int u, int lane, int group, int nrep, float *ms) -> smat_status_t {
+    TRY(queue_ahead(s, &enq_us, group * nrep, [&]() -> cudaError_t {
+      cudaError_t q = cudaSuccess;
+      for (int r = 0; r < nrep && q == cudaSuccess; ++r) {
+        q = cudaEventRecord(ev[2 * r], s);
+        for (int g = 0; g < group && q == cudaSuccess; ++g)
+          q = launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s);
+        if (q == cudaSuccess) q = cudaEventRecord(ev[2 * r + 1], s);
+      }
       return q;
     }));
-    TRY(cudaEventSynchronize(e1));
-    TRY(cudaEventElapsedTime(ms, e0, e1));
-    *ms /= (float)group;
+    TRY(cudaEventSynchronize(ev[2 * nrep - 1]));
+    for (int r = 0; r < nrep; ++r) {
+      TRY(cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]));
+      ms[r] /= (float)group;
+    }
     return SMAT_OK;
   };
   auto time_it = [&](int u, int lane, float *med) -> smat_status_t {
     for (int w = 0; w < 2; ++w) TRY(launch_spmv_width(h, variant, u, lane, a, x.p, b, y.p, s));
     float wms;
-    TRYS(block(u, lane, 1, &wms));  // one product alone sizes the blocks
+    TRYS(blocks(u, lane, 1, 1, &wms));  // one product alone sizes the repetitions
     const int group = products_per_rep(wms);
     const int nrep = group > 1 ? 3 : 5;   // about as many products as five single ones
     float ms[5];
-    for (int r = 0; r < nrep; ++r) TRYS(block(u, lane, group, &ms[r]));
+    TRYS(blocks(u, lane, group, nrep, ms));
     std::sort(ms, ms + nrep);
     *med = ms[nrep / 2];
     return SMAT_OK;
@@ -866,7 +875,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
   } guard{ev};
   const double t_start = now_ms();
   float best_ms = 1e30f;
-  double enq_us = 10.0;  // host time to queue a block of timed repetitions
+  double enq_us = 10.0;  // host time to queue one timed product
   *best = -1;
   std::vector<std::pair<int, float>> timed_here;
   for (int v : cands) {
@@ -881,7 +890,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     int group = 1;
     {
       const size_t w0 = (size_t)reps_max * 2;
-      TRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+      TRY(queue_ahead(s, &enq_us, 1, [&]() -> cudaError_t {
         cudaError_t q = cudaEventRecord(ev[w0], s);
         if (q == cudaSuccess) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);
         if (q == cudaSuccess) q = cudaEventRecord(ev[w0 + 1], s);
@@ -900,7 +909,7 @@ smat_status_t trial(smat_s *h, const std::vector<int> &cands, const smat_tune_op
     // each repetition times `group` products back to back, queued behind a
     // device hold so that its pair of events brackets the products alone
     auto timed = [&](int upto) -> cudaError_t {
-      cudaError_t e = queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+      cudaError_t e = queue_ahead(s, &enq_us, (upto - done) * group, [&]() -> cudaError_t {
         for (int r = done; r < upto; ++r) {
           cudaError_t q = cudaEventRecord(ev[2 * r], s);
           for (int g = 0; g < group && q == cudaSuccess; ++g) q = launch_spmv(h, v, a, x.p, b, y.p, s, false);

@@ -554,7 +554,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
     for (int sc : scales)
       for (int cp : ctas) cands.push_back({sc, cp, ow});
   }
-  double enq_us = 10.0;  // host time to queue one timed repetition
+  double enq_us = 10.0;  // host time to queue one launch
   for (const Cand &cd : cands) {
     {
       const int sc = cd.sc, cp = cd.cp;
@@ -566,7 +566,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
       std::vector<float> ms((size_t)reps);
       for (int r = 0; r < reps; ++r) {
         // queued behind a device hold, so that the events bracket the graph alone
-        BTRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+        BTRY(queue_ahead(s, &enq_us, 1, [&]() -> cudaError_t {
           cudaError_t q = cudaEventRecord(e0, s);
           if (q == cudaSuccess) q = cudaGraphLaunch(b->exec, s);
           if (q == cudaSuccess) q = cudaEventRecord(e1, s);
@@ -602,7 +602,7 @@ smat_status_t smat_batch_tune(smat_batch_t b, const smat_batch_opts_t *opts, voi
     for (int w = 0; w < 2; ++w) BTRY(run_loop());
     std::vector<float> ms((size_t)reps);
     for (int r = 0; r < reps; ++r) {
-      BTRY(queue_ahead(s, &enq_us, [&]() -> cudaError_t {
+      BTRY(queue_ahead(s, &enq_us, n, [&]() -> cudaError_t {
         cudaError_t q = cudaEventRecord(e0, s);
         if (q == cudaSuccess) q = run_loop();
         if (q == cudaSuccess) q = cudaEventRecord(e1, s);

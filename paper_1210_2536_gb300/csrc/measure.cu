@@ -86,7 +86,7 @@ cudaError_t run_gather(long long n, long long nidx, int reps, double *rate) {
   const unsigned grid = (unsigned)((nt + 255) / 256);
   double enq_us = 10.0;
   for (int r = -3; r < reps && e == cudaSuccess; ++r) {  // three untimed passes first
-    e = queue_ahead(0, &enq_us, [&]() -> cudaError_t {
+    e = queue_ahead(0, &enq_us, 1, [&]() -> cudaError_t {
       cudaError_t q = cudaEventRecord(e0);
       gather_rate_kernel<T><<<grid, 256>>>((const int32_t *)pi, (const T *)px, (T *)po, nt);
       if (q == cudaSuccess) q = cudaGetLastError();
@@ -144,7 +144,7 @@ cudaError_t run_fp64(int reps, double *rate) {
   std::vector<float> ms;
   double enq_us = 10.0;
   for (int r = -3; r < reps && e == cudaSuccess; ++r) {  // three untimed passes first
-    e = queue_ahead(0, &enq_us, [&]() -> cudaError_t {
+    e = queue_ahead(0, &enq_us, 1, [&]() -> cudaError_t {
       cudaError_t q = cudaEventRecord(e0);
       fp64_fma_kernel<<<grid, 256>>>((const double *)pbc, (double *)po, iters);
       if (q == cudaSuccess) q = cudaGetLastError();

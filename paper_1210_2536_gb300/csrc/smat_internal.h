@@ -268,15 +268,16 @@ constexpr double HOLD_MAX_US = 4000.0;
 // enqueue it, so that the GPU reaches the work only once all of it is queued
 // and no host launch latency falls between a pair of timing events (a short
 // kernel enqueued behind an idle GPU is otherwise timed together with the
-// host's latency to submit it).  enqueue() issues the work and its events
-// without synchronising; *enq_us carries the host's enqueue time from one
-// call to the next.  When the enqueue outlasted the hold, the stream is
-// drained and the same work queued again behind a hold sized from the
-// enqueue just measured (three attempts at most).
+// host's latency to submit it).  enqueue() issues `units` launches with their
+// events and does not synchronise; *enq_us carries the host's enqueue time
+// per unit from one call to the next.  When the enqueue outlasted the hold,
+// the stream is drained and the same work queued again behind a hold sized
+// from the enqueue just measured (three attempts at most).
 template <typename F>
-cudaError_t queue_ahead(cudaStream_t s, double *enq_us, F &&enqueue) {
+cudaError_t queue_ahead(cudaStream_t s, double *enq_us, int units, F &&enqueue) {
+  const double n = units > 1 ? (double)units : 1.0;
   for (int attempt = 0;; ++attempt) {
-    double hold = 20.0 + 1.5 * *enq_us;
+    double hold = 20.0 + 1.5 * *enq_us * n;
     hold = hold < HOLD_MAX_US ? hold : HOLD_MAX_US;
     cudaError_t e = launch_hold(s, hold);
     if (e != cudaSuccess) return e;
@@ -284,7 +285,7 @@ cudaError_t queue_ahead(cudaStream_t s, double *enq_us, F &&enqueue) {
     e = enqueue();
     const double dt = (host_ms() - t0) * 1e3;
     if (e != cudaSuccess) return e;
-    *enq_us = dt;
+    *enq_us = dt / n;
     if (dt < hold || attempt == 2) return cudaSuccess;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
