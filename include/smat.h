@@ -156,7 +156,8 @@ typedef struct {
                               CSR bytes (default 4)                            */
   int32_t trial_reps;      /* timed products per variant: the median of that many
                               repetitions, or, for products under about 40 us,
-                              of max(3, ceil(trial_reps / g)) repetitions of g
+                              of max(min(trial_reps, 3), ceil(trial_reps / g))
+                              repetitions of g
                               back-to-back products spanning about 40 us (the
                               event-timed duration of one short kernel moves
                               in steps of about 2 us); each
