@@ -154,16 +154,16 @@ typedef struct {
                               aver_RD (Sec. 2.3: 20, i.e. >= 5% fill)          */
   double bytes_cap;        /* DIA/ELL admissible while their bytes <= this *
                               CSR bytes (default 4)                            */
-  int32_t trial_reps;      /* timed products per variant: the median of that many
-                              repetitions, or, for products under about 40 us,
-                              of max(min(trial_reps, 3), ceil(trial_reps / g))
-                              repetitions of g
-                              back-to-back products spanning about 40 us (the
-                              event-timed duration of one short kernel moves
-                              in steps of about 2 us); each
-                              block of repetitions is queued behind a short
-                              device hold so that no host launch latency falls
-                              between its events                              */
+  int32_t trial_reps;      /* timed products per variant: the median of that
+                              many repetitions of one product, or, for
+                              products under about 40 us, of
+                              max(min(trial_reps, 3), ceil(trial_reps / g))
+                              repetitions of g back-to-back products spanning
+                              about 40 us (the event-timed duration of one
+                              short kernel moves in steps of about 2 us);
+                              each block of repetitions is queued behind a
+                              short device hold so that no host launch
+                              latency falls between its events              */
   int32_t trial_warmup;    /* untimed repetitions per variant                  */
   double trial_budget_ms;  /* stop trialling further variants past this       */
   uint32_t allowed;        /* bit mask over smat_variant_t (0 = all)           */
