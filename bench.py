@@ -1100,8 +1100,8 @@ def selector_regret(prods, time_variant):
     """Regret of each tuned pick (learned selector plus its execute-and-
     measure fallback over the further formats) against the fastest variant
     the library can run on that matrix: the eight classes of Sec. 5 and the
-    further formats, every one that builds timed alone here (median of 20),
-    the pick among them in the same loop.  Measured twice: with the
+    further formats, every one that builds timed alone here (the mean of the
+    middle half of 20 repetitions), the pick among them in the same loop.  Measured twice: with the
     repetitions back to back as the tuner's trials run them (`warm`, the
     conditions the selector's labels were taken under), and with L2 flushed
     before each (`cold_l2`, the conditions of the step, whose other products
@@ -1111,9 +1111,10 @@ def selector_regret(prods, time_variant):
     import torch
     further = (smat.SMAT_V_HYB, smat.SMAT_V_SELL, smat.SMAT_V_BCSR, smat.SMAT_V_SPLIT)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    dev_idx = torch.cuda.current_device() if torch.cuda.is_available() else 0
     out = {}
     for mode, cold in (("warm", False), ("cold_l2", True)):
-        clocks = Clocks(vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device()))
+        clocks = Clocks(vis.split(",")[dev_idx] if vis else str(dev_idx))
         clocks.start()
         rows = []
         for p in prods:

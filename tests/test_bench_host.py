@@ -1,5 +1,5 @@
-"""Host-side logic of bench.py: the end-to-end issue order and the DRAM
-traffic record lookup."""
+"""Host-side logic of bench.py: the end-to-end issue order, the DRAM
+traffic record lookup and the live selector-regret bookkeeping."""
 import itertools
 import os
 import sys
@@ -68,3 +68,61 @@ def test_configuration_harness_loads_and_lists_its_workloads():
                          capture_output=True, text=True, check=True).stdout
     for name in ("poisson64", "batched_hierarchy", "galerkin", "segments", "precision", "all"):
         assert name in out
+
+
+def test_selector_regret_over_the_whole_plan_space():
+    # the live regret loop with a fake timer: every admissible class and every
+    # further format that builds is timed, the pick always (even outside the
+    # classes' mask), each mode separately; regret = t(pick) / t(best) - 1
+    import numpy as np
+    import paper_1210_2536_gb300 as smat
+
+    class _A:
+        def __init__(self, name):
+            self.name = name
+
+    class _M:
+        def timings(self):
+            t = np.full(smat.SMAT_NUM_ALL_VARIANTS, -1.0, np.float32)
+            t[smat.SMAT_V_CSR_VEC32] = 0.009
+            return t
+
+    V = smat
+    warm_times = {  # product 0: CSR-vector-32 picked, COO faster; product 1: SPLIT picked and fastest
+        0: {V.SMAT_V_CSR_SCALAR: 0.030, V.SMAT_V_CSR_VEC32: 0.010, V.SMAT_V_COO: 0.008, V.SMAT_V_SELL: 0.020},
+        1: {V.SMAT_V_CSR_SCALAR: 0.200, V.SMAT_V_COO: 0.060, V.SMAT_V_SPLIT: 0.050},
+    }
+    cold_times = {0: dict(warm_times[0]), 1: dict(warm_times[1])}
+    cold_times[0][V.SMAT_V_COO] = 0.012      # cold: the pick is the fastest after all
+    cold_times[1][V.SMAT_V_COO] = 0.040      # cold: COO beats the pick by 25 %
+    prods = [
+        {"A": _A("m0"), "M": _M(), "f": {"admissible": (1 << V.SMAT_V_CSR_SCALAR) | (1 << V.SMAT_V_CSR_VEC32)
+                                         | (1 << V.SMAT_V_COO)},
+         "plan": {"variant": V.SMAT_V_CSR_VEC32, "name": "csr_vec32", "trialled": 1, "confidence": 0.61}},
+        {"A": _A("m1"), "M": _M(), "f": {"admissible": (1 << V.SMAT_V_CSR_SCALAR) | (1 << V.SMAT_V_COO)},
+         "plan": {"variant": V.SMAT_V_SPLIT, "name": "split", "trialled": 1, "confidence": 1.0}},
+    ]
+    calls = []
+
+    def fake_time(p, v, cold=True):
+        i = prods.index(p)
+        calls.append((i, v, cold))
+        table = (cold_times if cold else warm_times)[i]
+        if v not in table:
+            raise smat.SmatError(smat.SMAT_ERR_UNSUPPORTED, "build")
+        return table[v]
+
+    out = bench.selector_regret(prods, fake_time)
+    w, c = out["warm"], out["cold_l2"]
+    assert [r["regret"] for r in w["rows"]] == [0.25, 0.0]
+    assert [r["best"] for r in w["rows"]] == ["coo", "split"]
+    assert [r["hit"] for r in w["rows"]] == [False, True]
+    assert [r["regret"] for r in c["rows"]] == [0.0, 0.25]
+    assert w["mean_regret"] == 0.125 and w["max_regret"] == 0.25 and w["accuracy_within_2pct"] == 0.5
+    assert w["rows"][0]["us"] == {"csr_scalar": 30.0, "csr_vec32": 10.0, "coo": 8.0, "sell": 20.0}
+    assert w["rows"][0]["tuner_us"] == {"csr_vec32": 9.0}
+    # the classes outside a matrix's mask are not timed, every further format is
+    # tried, and the pick is timed even when it is a further format
+    timed = {(i, v) for i, v, cold_ in calls if not cold_}
+    assert (1, V.SMAT_V_CSR_VEC32) not in timed and (1, V.SMAT_V_SPLIT) in timed
+    assert all((i, f) in timed for i in (0, 1) for f in (V.SMAT_V_HYB, V.SMAT_V_SELL, V.SMAT_V_BCSR, V.SMAT_V_SPLIT))
