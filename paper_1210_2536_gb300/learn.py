@@ -6,6 +6,7 @@ paper's rules.
 
   python -m paper_1210_2536_gb300.learn label --out ds.jsonl [--count 2400]
   python -m paper_1210_2536_gb300.learn train --data ds.jsonl --model m.bin --report r.json
+  python -m paper_1210_2536_gb300.learn influence --data ds.jsonl --out influence.json
 
 Dataset line (JSON): id, kind, params, m, n, nnz, features (12 selector
 inputs), admissible mask, timings_ms[8] (-1 = not admissible), rules pick.
@@ -249,6 +250,101 @@ def evaluate(P, recs, conf=0.6, topk=3):
     return out
 
 
+# ---------------------------------------------------------------------------
+# Parameter influence (Sec. 4 and its figures on Ndiags and max_RD, ER_DIA
+# and ER_ELL, NTdiags_ratio and var_RD): the matrices of the labelled set
+# binned by one parameter at a time, and in each bin how many of those that
+# admit the format the parameter steers are GOOD for it, i.e. that format's
+# time lies within 2 % of the fastest of the eight classes (the rest are
+# BAD).  The paper reads its thresholds off such counts; the same counts on
+# this GPU show where those thresholds still hold.  Each bin also counts the
+# matrices of at least LARGE_NNZ stored entries apart: below that a product
+# takes a few microseconds and most classes tie within the 2 %.
+# ---------------------------------------------------------------------------
+
+LARGE_NNZ = 1_000_000
+
+INF = float("inf")
+# (parameter, variant it steers, bin edges, the paper's reading)
+INFLUENCE = [
+    ("ndiags", 6, [1, 25, 100, 500, INF], "nearly every matrix with Ndiags < 25 is good for DIA, few above 500"),
+    ("er_dia", 6, [0.0, 0.2, 0.4, 0.6, 0.8, INF], "DIA wins when ER_DIA > 60 %"),
+    ("ntdiags_ratio", 6, [0.0, 0.2, 0.4, 0.6, 0.8, INF], "DIA benefits when NTdiags_ratio > 40 %"),
+    ("max_rd", 5, [0, 5, 10, 50, INF], "ELL is most often best when max_RD < 5"),
+    ("er_ell", 5, [0.0, 0.5, 0.7, 0.9, INF], "ELL may benefit only when ER_ELL > 90 %"),
+    ("var_rd", 5, [0.0, 0.5, 2.0, 10.0, INF], "ELL benefits only when var_RD < 0.5"),
+    ("r", 7, [-INF, 1.0, 4.0, INF], "COO for small-world matrices, R in [1, 4)"),
+]
+VARIANT_SHORT = ["csr_scalar", "csr_vec4", "csr_vec8", "csr_vec32", "csr_merge", "ell", "dia", "coo"]
+
+
+def parameter_value(rec, name):
+    """The raw feature `name` of a dataset record (NTdiags_ratio = true
+    diagonals / Ndiags, 0 without diagonals; R is None where undefined)."""
+    raw = rec["raw"]
+    if name == "ntdiags_ratio":
+        return raw["ntdiags"] / raw["ndiags"] if raw["ndiags"] > 0 else 0.0
+    if name == "r":
+        return raw["r"] if raw["r_valid"] else None
+    return raw[name]
+
+
+def is_good(rec, v, tie=TIE):
+    """Variant v admissible and within `tie` of the fastest admissible class."""
+    t = rec["timings_ms"]
+    if not (rec["admissible"] >> v) & 1 or not t[v] > 0:
+        return None
+    best = min(x for j, x in enumerate(t) if (rec["admissible"] >> j) & 1 and x > 0)
+    return t[v] <= tie * best
+
+
+def influence(recs):
+    out = {"matrices": len(recs), "tie": round(TIE - 1.0, 4), "large_nnz": LARGE_NNZ, "parameters": []}
+    for name, v, edges, reading in INFLUENCE:
+        bins = [{"lo": None if edges[k] == -INF else edges[k], "hi": None if edges[k + 1] == INF else edges[k + 1],
+                 "n": 0, "good": 0, "n_large": 0, "good_large": 0} for k in range(len(edges) - 1)]
+        undefined = {"n": 0, "good": 0, "n_large": 0, "good_large": 0}
+        for r in recs:
+            g = is_good(r, v)
+            if g is None:
+                continue
+            x = parameter_value(r, name)
+            if x is None:
+                slot = undefined
+            else:
+                slot = next(b for k, b in enumerate(bins) if edges[k] <= x < edges[k + 1])
+            slot["n"] += 1
+            slot["good"] += int(g)
+            if r["nnz"] >= LARGE_NNZ:
+                slot["n_large"] += 1
+                slot["good_large"] += int(g)
+        for b in bins + [undefined]:
+            b["good_share"] = round(b["good"] / b["n"], 4) if b["n"] else None
+            b["good_share_large"] = round(b["good_large"] / b["n_large"], 4) if b["n_large"] else None
+        entry = {"parameter": name, "format": VARIANT_SHORT[v], "paper": reading, "bins": bins}
+        if name == "r":
+            entry["undefined"] = undefined
+        out["parameters"].append(entry)
+    return out
+
+
+def influence_table(rep):
+    """The report as markdown: one row per parameter bin."""
+    lines = ["| parameter | format | bin | admissible | good | good share | admissible, nnz ≥ 10⁶ | good | good share |",
+             "|---|---|---|---|---|---|---|---|---|"]
+    for p in rep["parameters"]:
+        rows = [(f"[{b['lo'] if b['lo'] is not None else '-inf'}, {b['hi'] if b['hi'] is not None else 'inf'})", b)
+                for b in p["bins"]]
+        if "undefined" in p:
+            rows.append(("undefined", p["undefined"]))
+        for label, b in rows:
+            share = f"{100 * b['good_share']:.0f} %" if b["good_share"] is not None else "—"
+            large = f"{100 * b['good_share_large']:.0f} %" if b["good_share_large"] is not None else "—"
+            lines.append(f"| {p['parameter']} | {p['format']} | {label} | {b['n']} | {b['good']} | {share} | "
+                         f"{b['n_large']} | {b['good_large']} | {large} |")
+    return "\n".join(lines)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -264,7 +360,15 @@ def main():
     t.add_argument("--epochs", type=int, default=400)
     t.add_argument("--lr", type=float, default=3e-3)
     t.add_argument("--seed", type=int, default=0)
+    f = sub.add_parser("influence")
+    f.add_argument("--data", required=True)
+    f.add_argument("--out", required=True)
     args = ap.parse_args()
+    if args.cmd == "influence":     # bookkeeping over the labelled set only: no GPU, no build
+        rep = influence(load(args.data))
+        json.dump(rep, open(args.out, "w"), indent=1)
+        print(influence_table(rep))
+        return
     import __graft_entry__
     __graft_entry__.build()
     import paper_1210_2536_gb300 as smat
