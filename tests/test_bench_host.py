@@ -126,3 +126,19 @@ def test_selector_regret_over_the_whole_plan_space():
     timed = {(i, v) for i, v, cold_ in calls if not cold_}
     assert (1, V.SMAT_V_CSR_VEC32) not in timed and (1, V.SMAT_V_SPLIT) in timed
     assert all((i, f) in timed for i in (0, 1) for f in (V.SMAT_V_HYB, V.SMAT_V_SELL, V.SMAT_V_BCSR, V.SMAT_V_SPLIT))
+
+
+def test_reference_arm_prints_its_line_on_the_host():
+    # the reference arm is the oracle on the host cores: it needs no GPU, and
+    # its one JSON line carries the keys the bench contract asks of it
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--scale", "0.05"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 1
+    assert line["metric"] and line["unit"] == "GFLOP/s" and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
